@@ -1,0 +1,301 @@
+"""Benchmark: PCF Learned Sort on GB300 (one JSON line on rank 0).
+
+Workload (one step): sort four arrays of n = 10^8 float64 keys, one per
+distribution (Normal(0,1), LogNormal(0,1), Exponential(1), a 5-Gaussian
+mixture), keys only, through pcf_sort_keys (pristine device input ->
+device output; inputs are 800 MB each, larger than the 129 MB L2).
+
+  value        sorted Gkeys/s over the K timed steps (device-resident inputs)
+  e2e          the same through pcf_sort_keys_host: pinned host buffer ->
+               device -> sort -> host, copies inside the timed region
+  roofline     the dominant kernel's algorithmic bytes per launch / its mean
+               launch time (CUDA events on the sort's stream), vs the
+               measured copy bandwidth
+  cpu_baseline the CPU oracle, single-threaded, on a bounded sample
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): the sort does not shard; each rank sorts its own
+replica of the workload ("weak" scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2405_07122_gb300 import workloads as W  # noqa: E402
+
+N = 10**8
+DISTS = [("normal", 1), ("lognormal", 2), ("exponential", 3), ("mixture", 4)]
+METRIC = "sorted Gkeys/s"
+WORKLOAD = "plain PCF sort, 4 arrays x 10^8 float64 keys (Normal, LogNormal, Exponential, 5-Gaussian mixture), keys only"
+CPU_SAMPLE_N = 25 * 10**6
+
+# algorithmic bytes per key of each kernel (keys only)
+KERNEL_BYTES = {
+    "range": 8,        # read the key
+    "hist1_scan": 8,   # read the key (the bucket table hits L2)
+    "scatter1": 18,    # read the key, write the key and its 2-byte low digit
+    "hist2_scan": 2,   # read the low digit
+    "scatter2": 18,    # read key + digit, write the key
+    "leaf": 16,        # read and write each key finished on chip
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_gkeys(keys_list):
+    """Single-threaded oracle on the first CPU_SAMPLE_N keys of each array."""
+    import oracle
+    total, secs = 0, 0.0
+    for x in keys_list:
+        s = np.ascontiguousarray(x[:CPU_SAMPLE_N])
+        t0 = time.perf_counter()
+        oracle.sort(s)
+        secs += time.perf_counter() - t0
+        total += s.size
+    return total / secs / 1e9, total, secs
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    keys = [W.f64_keys(d, CPU_SAMPLE_N, seed) for d, seed in DISTS]
+    import oracle
+    oracle.lib()
+    times = []
+    for step in range(args.warmup + args.steps):
+        total, secs = 0, 0.0
+        for x in keys:
+            t0 = time.perf_counter()
+            oracle.sort(x)
+            secs += time.perf_counter() - t0
+            total += x.size
+        if step >= args.warmup:
+            times.append(secs)
+    v = total / (sum(times) / len(times)) / 1e9
+    sample = "first %d keys of each of the 4 distributions (n=%d per array, seeds as the GPU arm)" % (
+        CPU_SAMPLE_N, CPU_SAMPLE_N)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gkeys/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (CPU oracle on a bounded sample)",
+                       "n_per_array": CPU_SAMPLE_N, "arrays_per_step": 4},
+            "cpu_baseline": {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "Gkeys/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N, help="keys per array (default 10^8)")
+    args = ap.parse_args()
+    global N
+    N = args.n
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_07122_gb300 import pcfsort
+
+    host_keys = [W.f64_keys(d, N, seed) for d, seed in DISTS]
+    ins = [torch.from_numpy(x).to(dev) for x in host_keys]
+    outs = [torch.empty_like(t) for t in ins]
+    ctx = pcfsort.Context(local)
+    ctx.reserve(N)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(timing=False):
+        st = {k: 0.0 for k in pcfsort.STAGES}
+        launches = 0
+        for t, o in zip(ins, outs):
+            ctx.sort_keys(t, o, key_type="f64", seed=0, stream=stream)
+            s = ctx.last_stats()
+            launches += s["kernel_launches"]
+            if timing:
+                for k, v in ctx.stage_ms().items():
+                    st[k] += v
+        return st, launches
+
+    for _ in range(args.warmup):
+        step()
+    # correctness guard on the timed configuration (full check is in tests)
+    for o in outs:
+        b = o.view(torch.int64)
+        low63 = torch.tensor(2**63 - 1, dtype=torch.int64, device=dev)
+        ok = torch.where(b < 0, b ^ low63, b)
+        assert bool((ok[1:] >= ok[:-1]).all()), "output not sorted"
+
+    ctx.enable_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stages = {k: 0.0 for k in pcfsort.STAGES}
+    launches = 0
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, nl = step(timing=True)
+            launches += nl
+            for k in stages:
+                stages[k] += st[k]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ctx.enable_timing(False)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    keys_per_step = 4 * N * world
+    value = keys_per_step * args.steps / (ms / 1e3) / 1e9
+
+    # end to end: pinned host buffer -> device -> sort -> host, per array
+    pinned = [torch.from_numpy(x.copy()).pin_memory() for x in host_keys]
+    for p, x in zip(pinned, host_keys):
+        p.copy_(torch.from_numpy(x))
+        ctx.sort_keys_host(p, key_type="f64", stream=stream)
+    torch.cuda.synchronize(dev)
+    e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        for p in pinned:
+            ctx.sort_keys_host(p, key_type="f64", stream=stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e = keys_per_step * e_steps / e2e_s / 1e9
+
+    peak, peak_kind = peaks()
+    per_launch = {}
+    for k, b in KERNEL_BYTES.items():
+        ms_k = stages[k] / (args.steps * 4)
+        if ms_k > 0:
+            per_launch[k] = (ms_k, b)
+    dom = max(per_launch, key=lambda k: per_launch[k][0])
+    dom_ms, dom_b = per_launch[dom]
+    # keys processed by one launch of the dominant kernel: all N (global
+    # passes; the leaf kernel sees every key of this workload too)
+    achieved = dom_b * N / (dom_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_per_array": N, "arrays_per_step": 4,
+                   "l2": "inputs larger than L2 (800 MB per array, L2 129 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e, "unit": "Gkeys/s", "h2d_bytes_per_step": 8 * 4 * N,
+                "d2h_bytes_per_step": 8 * 4 * N},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "bytes_per_key": dom_b},
+        "stage_ms_per_array": {k: v / (args.steps * 4) for k, v in stages.items()},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, total, secs = cpu_oracle_gkeys(host_keys)
+        line["cpu_baseline"] = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                                "sample": "first %d keys of each of the 4 arrays (%d keys, %.1f s)"
+                                          % (CPU_SAMPLE_N, total, secs)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

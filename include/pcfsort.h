@@ -1,0 +1,159 @@
+/*
+ * pcfsort.h -- C ABI of the GB300 (sm_103a) PCF Learned Sort library.
+ *
+ * The library sorts 64-bit keys on one GPU with PCF Learned Sort
+ * (Sato & Matsui, "PCF Learned Sort: a Learning Augmented Sort Algorithm
+ * with O(n log log n) Expected Complexity", TMLR 2025):
+ *   Algorithm 1 (Learned-Sort): inputs shorter than tau go to a standard
+ *   sort; otherwise a CDF model is trained, every key is appended to bucket
+ *   floor(F(x) gamma) + 1 of gamma + 1 buckets, buckets of size >= delta are
+ *   sorted by the standard sort and the others recursively, and the sorted
+ *   buckets are concatenated.
+ *   Sec. 3.3 (PCF model): alpha sampled keys are counted into beta
+ *   equal-width bins i(x) = floor((x - x_min) beta / (x_max - x_min)) + 1,
+ *   b_i = |{j : i(a_j) <= i}| and F(x) = b_{i(x)} / alpha.
+ *   Theorem pcf-nlogn / Sec. 4: alpha = beta = gamma = delta = floor(n^{3/4}),
+ *   tau = 100 (the default policy).
+ *
+ * The output is the unique ascending order of the keys (IEEE-754 total
+ * order for binary64 keys, so -0 sorts before +0; unsigned order for u64
+ * keys); the pair sorts are stable (equal keys keep their input order).
+ * Results do not depend on the seed, the policy or the tuning.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers of the context's device; h_*
+ *     pointers are HOST pointers.  The caller owns all key and value buffers.
+ *     d_in may equal d_out (in-place sort); otherwise the ranges must not
+ *     overlap.  Keys are 8-byte aligned, values 4-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Calls are issued on `stream` and return when the sort is complete on
+ *     the device, except where stated.  A context serialises its own calls;
+ *     use one context per host thread.
+ *   - Errors are returned, never raised: no call aborts, traps or exits.
+ *     On PCF_ERR_INVALID_KEY (a NaN key) the output buffers are not written.
+ *     n = 0 and n = 1 succeed without device work other than a copy.
+ *   - Maximum n per array (and per batched call in total): 2^32 - 1 keys.
+ */
+#ifndef PCFSORT_H
+#define PCFSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PCF_KEY_F64 = 0, /* IEEE-754 binary64, ordered by the total order, NaN rejected */
+  PCF_KEY_U64 = 1  /* unsigned 64-bit integers                                     */
+} pcf_key_type;
+
+typedef enum {
+  PCF_OK = 0,
+  PCF_ERR_INVALID_ARG = 1, /* bad pointer, size, key type, policy or tuning            */
+  PCF_ERR_INVALID_KEY = 2, /* a NaN key (the paper's keys are real numbers)            */
+  PCF_ERR_OOM = 3,         /* device or pinned-host allocation failed                  */
+  PCF_ERR_CUDA = 4,        /* a CUDA runtime call failed (see pcf_last_cuda_error)     */
+  PCF_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (no trap is used)     */
+  PCF_ERR_INTERNAL = 6     /* an internal consistency check failed                     */
+} pcf_status;
+
+/* Parameters of Algorithm 1: alpha = floor(n^(a_num/den)), beta = ...(b_num),
+ * gamma = ...(c_num), delta = ...(d_num), recomputed for every (sub)array
+ * from its own n; tau is the small-input threshold.  Supported: den in 1..4,
+ * 1 <= a_num, b_num, c_num <= den, 1 <= d_num < den (0 < d < 1, as
+ * Lemma nlogn requires), tau >= 2.  Default: {3,3,3,3,4,100}. */
+typedef struct {
+  uint32_t a_num, b_num, c_num, d_num, den;
+  uint64_t tau;
+} pcf_policy;
+
+/* Implementation knobs.  They change speed only, never the result or the
+ * model: max_digit_bits = widest bucket-id digit scattered per global pass
+ * (4..11); tile_log2 = log2 of keys per scatter tile (11..13); leaf_cap =
+ * the largest bucket finished inside shared memory by one warp (64..1024,
+ * power of two).  Zero fields keep the current value. */
+typedef struct {
+  uint32_t max_digit_bits;
+  uint32_t tile_log2;
+  uint32_t leaf_cap;
+} pcf_tuning;
+
+typedef struct pcf_ctx pcf_ctx;
+
+/* Per-call counters (filled by the last sort on the context). */
+typedef struct {
+  uint64_t levels;           /* global bucketing levels run                     */
+  uint64_t global_passes;    /* digit scatter passes over device memory         */
+  uint64_t leaf_buckets;     /* buckets finished in shared memory               */
+  uint64_t fallback_buckets; /* buckets sent to the standard sort (|c| >= delta or degenerate) */
+  uint64_t fallback_keys;
+  uint64_t bytes_moved;      /* bytes read + written by the global passes (model) */
+  uint64_t kernel_launches;  /* this library's kernel launches in the call       */
+} pcf_call_stats;
+
+/* Creates a context on `device`.  The context owns its workspace (grown on
+ * demand, kept until destroy), a status word and a pinned host staging area. */
+pcf_status pcf_ctx_create(pcf_ctx** out, int device);
+/* Frees everything the context owns.  NULL is accepted. */
+pcf_status pcf_ctx_destroy(pcf_ctx* ctx);
+/* Replaces the policy (copied).  PCF_ERR_INVALID_ARG if unsupported. */
+pcf_status pcf_ctx_set_policy(pcf_ctx* ctx, const pcf_policy* policy);
+/* Replaces non-zero tuning fields (copied). */
+pcf_status pcf_ctx_set_tuning(pcf_ctx* ctx, const pcf_tuning* tuning);
+pcf_status pcf_ctx_get_tuning(const pcf_ctx* ctx, pcf_tuning* out);
+/* Pre-allocates workspace for sorts of up to n_total keys (pairs != 0: with
+ * values) so that later calls allocate nothing. */
+pcf_status pcf_ctx_reserve(pcf_ctx* ctx, uint64_t n_total, int pairs);
+/* Counters of the last sort on this context. */
+pcf_status pcf_ctx_last_stats(const pcf_ctx* ctx, pcf_call_stats* out);
+
+/* Sorts n keys (Algorithm 1, PCF model of Sec. 3.3) from d_in into d_out. */
+pcf_status pcf_sort_keys(pcf_ctx* ctx, const void* d_in, void* d_out, uint64_t n,
+                         pcf_key_type kt, uint64_t seed, void* stream);
+
+/* Stable key-value sort: d_vals_out[i] is the value that travelled with
+ * d_keys_out[i]; equal keys keep their input order. */
+pcf_status pcf_sort_pairs(pcf_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
+                          void* d_keys_out, uint32_t* d_vals_out, uint64_t n,
+                          pcf_key_type kt, uint64_t seed, void* stream);
+
+/* Sorts S independent arrays in one batched pass.  Segment s is keys
+ * [h_offsets[s], h_offsets[s+1]) of the key buffers (h_offsets: S+1
+ * non-decreasing HOST values, h_offsets[0] = 0) and is sorted exactly as
+ * pcf_sort_keys / pcf_sort_pairs would sort it with seed + s.  d_vals_* may
+ * be NULL (keys only).  In-place when d_keys_in == d_keys_out. */
+pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
+                              void* d_keys_out, uint32_t* d_vals_out,
+                              const uint64_t* h_offsets, uint32_t S, pcf_key_type kt,
+                              uint64_t seed, void* stream);
+
+/* End-to-end form on HOST buffers: copies h_keys (n keys, ideally pinned)
+ * to the device, sorts, and copies the result back into h_keys. */
+pcf_status pcf_sort_keys_host(pcf_ctx* ctx, void* h_keys, uint64_t n, pcf_key_type kt,
+                              uint64_t seed, void* stream);
+
+/* Stage timing of the last sort (milliseconds between CUDA events recorded
+ * on the sort's stream) when enabled with pcf_ctx_enable_timing(ctx, 1):
+ * [0] range (k_range + k_model), [1] sample + PCF table (k_sample),
+ * [2] pass-1 histogram + scan, [3] pass-1 scatter (k_scatter1),
+ * [4] pass-2 groups + histogram + scans, [5] pass-2 scatter (k_scatter2),
+ * [6] buckets finished on chip (k_buckets + k_leaf), [7] standard-sort
+ * fallback.  Events only; the call synchronises at its end either way. */
+pcf_status pcf_ctx_enable_timing(pcf_ctx* ctx, int on);
+pcf_status pcf_ctx_stage_ms(const pcf_ctx* ctx, float out[8]);
+
+/* Text of a status code (static storage). */
+const char* pcf_status_string(pcf_status s);
+/* The last CUDA error string seen by this context ("" if none). */
+const char* pcf_last_cuda_error(const pcf_ctx* ctx);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+uint32_t pcf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCFSORT_H */

@@ -1,0 +1,822 @@
+// pcf_host.cu -- host driver and C ABI of the PCF Learned Sort library.
+//
+// Algorithm 1 of Sato & Matsui (TMLR 2025) is run level by level: every
+// (sub)array too large for one warp's shared memory is bucketed by a global
+// level (range -> PCF model -> bucket ids -> two stable digit scatters), its
+// buckets are finished on chip when they fit, recursed at the next level
+// when they do not, and sent to the standard sort when |c| >= delta.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pcfsort.h"
+#include "pcf_internal.h"
+
+
+using namespace pcf;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+struct HostBuf {  // pinned staging
+  void* p = nullptr;
+  size_t cap = 0;
+  ~HostBuf() {
+    if (p) cudaFreeHost(p);
+  }
+};
+
+}  // namespace
+
+struct pcf_ctx {
+  int device = 0;
+  int num_sms = 0;
+  Policy policy{3, 3, 3, 3, 4, 0, 100};
+  pcf_tuning tuning{10, 15, 512};
+  std::string last_err;
+  pcf_call_stats stats{};
+  bool timing = false;
+  float stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // workspace
+  DevBuf tmp_k, tmp_v, tmp_aux, host_keys;
+  DevBuf segs, bases, tpool, done, cmat1, cmat2, sw, groups, gtiles, gcent, gtot;
+  DevBuf leaf, next, fb, lout, status, misc, fb_items, fb_bases, fb_lohi, small_items;
+  HostBuf h_stage, h_lout, h_status, h_items;
+};
+
+namespace {
+
+pcf_status cuda_fail(pcf_ctx* c, cudaError_t e) {
+  c->last_err = cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PCF_ERR_OOM : PCF_ERR_CUDA;
+}
+
+#define CK(expr)                                    \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
+  } while (0)
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return cudaSuccess;
+  if (b.p) {
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  size_t want = bytes + bytes / 4;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      return e;
+    }
+    want = bytes;
+  }
+  b.cap = want;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_host(HostBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return cudaSuccess;
+  if (b.p) cudaFreeHost(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = bytes + bytes / 4;
+  cudaError_t e = cudaMallocHost(&b.p, want);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return e;
+  }
+  b.cap = want;
+  return cudaSuccess;
+}
+
+template <typename T>
+T* as(DevBuf& b) {
+  return (T*)b.p;
+}
+
+bool policy_ok(const Policy& P) {
+  if (P.den < 1 || P.den > 4) return false;
+  if (P.a_num < 1 || P.a_num > P.den || P.b_num < 1 || P.b_num > P.den) return false;
+  if (P.c_num < 1 || P.c_num > P.den) return false;
+  if (P.d_num < 1 || P.d_num >= P.den) return false;
+  if (P.tau < 2 || P.tau > 65535) return false;
+  return true;
+}
+
+uint32_t bits_of(uint32_t v) {  // number of bits to hold values 0..v
+  uint32_t b = 0;
+  while (b < 32 && (v >> b) != 0) ++b;
+  return b;
+}
+
+struct InSeg {
+  uint64_t off, n, start, seed;
+  uint32_t depth;
+};
+
+struct Plan {
+  std::vector<Seg> segs;
+  std::vector<uint32_t> range_base, k1_base, tile1_base;
+  std::vector<uint64_t> group_base, bucket_base;
+  uint64_t tpool = 0, cmat1 = 0, cmat2_bound = 0, tiles2_bound = 0, n_groups = 0, n_buckets = 0;
+  uint32_t dmax1 = 1, dmax2 = 1;
+};
+
+void plan_level(const Policy& P, const pcf_tuning& tu, const std::vector<InSeg>& in, Plan& pl) {
+  const uint32_t tile_keys = 1u << tu.tile_log2;
+  const uint32_t S = (uint32_t)in.size();
+  pl.segs.resize(S);
+  pl.range_base.assign(S + 1, 0);
+  pl.k1_base.assign(S + 1, 0);
+  pl.tile1_base.assign(S + 1, 0);
+  pl.group_base.assign(S + 1, 0);
+  pl.bucket_base.assign(S + 1, 0);
+  pl.tpool = pl.cmat1 = pl.cmat2_bound = pl.tiles2_bound = 0;
+  pl.dmax1 = pl.dmax2 = 1;
+  for (uint32_t s = 0; s < S; ++s) {
+    Seg g;
+    memset(&g, 0, sizeof g);
+    g.off = in[s].off;
+    g.n = in[s].n;
+    g.start = in[s].start;
+    g.seed = in[s].seed;
+    g.depth = in[s].depth;
+    Params pr = params_of(P, g.n);
+    g.alpha = pr.alpha;
+    g.beta = pr.beta;
+    g.gamma = pr.gamma;
+    g.delta = pr.delta;
+    const uint32_t jb = std::max(1u, bits_of(pr.gamma));
+    uint32_t b1 = (jb + 1) / 2;
+    b1 = std::min(b1, std::min(tu.max_digit_bits, kMaxDigitBits));
+    if (jb - b1 > kMaxDigitBits) b1 = jb - kMaxDigitBits;
+    g.b1 = b1;
+    g.b2 = jb - b1;
+    g.T_off = pl.tpool;
+    pl.tpool += (uint64_t)pr.beta + 1;
+    g.tiles1 = (uint32_t)((g.n + tile_keys - 1) / tile_keys);
+    g.cbase1 = pl.cmat1;
+    pl.cmat1 += (uint64_t)g.tiles1 << g.b1;
+    g.group_base = pl.group_base[s];
+    g.bucket_base = pl.bucket_base[s];
+    g.ord_lo = ~0ull;
+    g.ord_hi = 0;
+    g.status = SEG_BUCKET;
+    pl.segs[s] = g;
+    pl.range_base[s + 1] = pl.range_base[s] + (uint32_t)((g.n + kRangeTile - 1) / kRangeTile);
+    pl.k1_base[s + 1] = pl.k1_base[s] + (pr.alpha + kSamplesPerCta - 1) / kSamplesPerCta;
+    pl.tile1_base[s + 1] = pl.tile1_base[s] + g.tiles1;
+    pl.group_base[s + 1] = pl.group_base[s] + (1ull << g.b1);
+    pl.bucket_base[s + 1] = pl.bucket_base[s] + (uint64_t)pr.gamma + 1;
+    const uint64_t t2 = g.tiles1 + (1ull << g.b1);
+    pl.tiles2_bound += t2;
+    pl.cmat2_bound += t2 << g.b2;
+    pl.dmax1 = std::max(pl.dmax1, 1u << g.b1);
+    pl.dmax2 = std::max(pl.dmax2, 1u << g.b2);
+  }
+  pl.n_groups = pl.group_base[S];
+  pl.n_buckets = pl.bucket_base[S];
+}
+
+struct LeafGeom {
+  uint32_t tmax, gmax, warps, grid;
+};
+
+LeafGeom leaf_geom(pcf_ctx* ctx, bool pairs) {
+  LeafGeom g;
+  const uint32_t cap = ctx->tuning.leaf_cap;
+  uint32_t tmax = 2, gmax = 2;
+  for (uint64_t n = 2; n <= cap; ++n) {
+    if (n < ctx->policy.tau) continue;
+    Params pr = params_of(ctx->policy, n);
+    tmax = std::max(tmax, pr.beta + 1);
+    gmax = std::max(gmax, pr.gamma + 1);
+  }
+  g.tmax = (tmax + 3) & ~3u;
+  g.gmax = (gmax + 3) & ~3u;
+  const size_t per = leaf_smem_per_warp(cap, pairs, g.tmax, g.gmax);
+  uint32_t warps = 8;
+  while (warps > 1 && per * warps > 110 * 1024) warps /= 2;
+  g.warps = warps;
+  const size_t cta = per * warps;
+  uint32_t per_sm = (uint32_t)std::max<size_t>(1, (227 * 1024) / (cta + 1024));
+  per_sm = std::min(per_sm, 2048u / (32 * warps));
+  g.grid = (uint32_t)ctx->num_sms * per_sm;
+  return g;
+}
+
+struct Timer {
+  pcf_ctx* ctx;
+  cudaStream_t st;
+  cudaEvent_t ev[64];
+  int n = 0;
+  int stage_of[64];
+  Timer(pcf_ctx* c, cudaStream_t s) : ctx(c), st(s) {
+    if (ctx->timing)
+      for (int i = 0; i < 64; ++i) cudaEventCreate(&ev[i]);
+  }
+  void mark(int stage) {
+    if (!ctx->timing || n >= 64) return;
+    stage_of[n] = stage;
+    cudaEventRecord(ev[n++], st);
+  }
+  ~Timer() {
+    if (!ctx->timing) return;
+    if (n > 0) cudaEventSynchronize(ev[n - 1]);
+    for (int i = 1; i < n; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      if (stage_of[i] >= 0 && stage_of[i] < 8) ctx->stage_ms[stage_of[i]] += ms;
+    }
+    for (int i = 0; i < 64; ++i) cudaEventDestroy(ev[i]);
+  }
+};
+
+constexpr uint64_t kSpinLimit = 1ull << 24;
+
+// The whole sort of a batch of arrays.  Level-0 segments are the caller's
+// arrays; keys flow src -> tmp (pass 1) -> out (pass 2); leaf buckets are
+// finished in place in out; fallback buckets are merge-sorted in out.
+pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, uint64_t* out_k,
+                    uint32_t* out_v, const std::vector<InSeg>& user, uint32_t kt, bool pairs,
+                    cudaStream_t st, uint32_t scan_withhold = 0xFFFFFFFFu,
+                    uint64_t spin_limit = kSpinLimit) {
+  ctx->stats = pcf_call_stats{};
+  for (int i = 0; i < 8; ++i) ctx->stage_ms[i] = 0;
+  uint64_t n_total = 0;
+  for (auto& s : user) n_total = std::max(n_total, s.off + s.n);
+  if (n_total == 0) return PCF_OK;
+  CK(cudaSetDevice(ctx->device));
+  LaunchCfg lc;
+  lc.stream = st;
+  lc.kt = kt;
+  lc.pairs = pairs;
+  lc.launches = &ctx->stats.kernel_launches;
+  CK(ensure(ctx->status, 64));
+  lc.status = as<uint32_t>(ctx->status);
+  CK(cudaMemsetAsync(lc.status, 0, 4, st));
+  CK(ensure_host(ctx->h_status, 64));
+  CK(ensure_host(ctx->h_lout, sizeof(LevelOut)));
+  CK(ensure(ctx->lout, sizeof(LevelOut) + 64));
+  CK(ensure(ctx->misc, 256));
+  const uint32_t tile_keys = 1u << ctx->tuning.tile_log2;
+  const uint32_t cap = ctx->tuning.leaf_cap;
+  const LeafGeom lg = leaf_geom(ctx, pairs);
+  Timer tm(ctx, st);
+  tm.mark(-1);
+
+  // NaN check of everything first; every writer below is skipped on NaN by
+  // the host before launch.
+  std::vector<InSeg> small, big;
+  for (auto& s : user) {
+    if (s.n == 0) continue;
+    if (s.n <= cap) small.push_back(s);
+    else big.push_back(s);
+  }
+  if (kt == KEY_F64) {
+    // range + NaN of the small segments in one launch (big ones: level 0)
+    std::vector<InSeg> all = small;
+    if (!all.empty()) {
+      Plan pl;
+      plan_level(ctx->policy, ctx->tuning, all, pl);
+      const uint32_t S = (uint32_t)all.size();
+      size_t need = S * sizeof(Seg) + (S + 1) * 4;
+      CK(ensure_host(ctx->h_stage, need));
+      CK(ensure(ctx->segs, need));
+      memcpy(ctx->h_stage.p, pl.segs.data(), S * sizeof(Seg));
+      memcpy((char*)ctx->h_stage.p + S * sizeof(Seg), pl.range_base.data(), (S + 1) * 4);
+      CK(cudaMemcpyAsync(ctx->segs.p, ctx->h_stage.p, need, cudaMemcpyHostToDevice, st));
+      CK(launch_range(lc, as<Seg>(ctx->segs), S,
+                      (const uint32_t*)((char*)ctx->segs.p + S * sizeof(Seg)), pl.range_base[S],
+                      in_k, true));
+    }
+  }
+
+  // ---- level 0 of the small arrays: straight to the shared-memory kernel,
+  // launched once the NaN check of every key has passed
+  auto launch_small = [&]() -> pcf_status {
+    if (small.empty()) return PCF_OK;
+    const uint32_t S = (uint32_t)small.size();
+    std::vector<WorkItem> items(S);
+    for (uint32_t i = 0; i < S; ++i) {
+      items[i].off = small[i].off;
+      items[i].start = small[i].start;
+      items[i].seed = small[i].seed;
+      items[i].n = (uint32_t)small[i].n;
+      items[i].depth = small[i].depth;
+    }
+    const size_t need = S * sizeof(WorkItem) + 64;
+    CK(ensure(ctx->small_items, need));
+    CK(ensure_host(ctx->h_items, need));
+    memcpy(ctx->h_items.p, items.data(), S * sizeof(WorkItem));
+    uint32_t* cnt = (uint32_t*)((char*)ctx->h_items.p + S * sizeof(WorkItem));
+    cnt[0] = S;
+    cnt[1] = 0;
+    CK(cudaMemcpyAsync(ctx->small_items.p, ctx->h_items.p, S * sizeof(WorkItem) + 8,
+                       cudaMemcpyHostToDevice, st));
+    const uint32_t* dcnt = (const uint32_t*)((char*)ctx->small_items.p + S * sizeof(WorkItem));
+    CK(launch_leaf(lc, as<WorkItem>(ctx->small_items), dcnt, (uint32_t*)dcnt + 1, in_k, out_k,
+                   in_v, out_v, ctx->policy, cap, lg.tmax, lg.gmax, lg.warps,
+                   std::min<uint32_t>(lg.grid, (S + lg.warps - 1) / lg.warps)));
+    ctx->stats.leaf_buckets += S;
+    return PCF_OK;
+  };
+  if (big.empty()) {
+    if (kt == KEY_F64) {
+      CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+    }
+    pcf_status r = launch_small();
+    if (r != PCF_OK) return r;
+    tm.mark(6);
+  }
+
+  // ---- global levels
+  std::vector<InSeg> level = big;
+  const uint64_t* src = in_k;
+  const uint32_t* src_v = in_v;
+  bool first = true;
+  while (!level.empty()) {
+    Plan pl;
+    plan_level(ctx->policy, ctx->tuning, level, pl);
+    const uint32_t S = (uint32_t)level.size();
+    uint64_t n_level = 0;
+    for (auto& s : level) n_level += s.n;
+    ctx->stats.levels += 1;
+    // upload plan: segs | range_base | k1_base | tile1_base | group_base | bucket_base
+    const size_t o_seg = 0, o_rb = o_seg + S * sizeof(Seg), o_k1 = o_rb + (S + 1) * 4,
+                 o_t1 = o_k1 + (S + 1) * 4, o_gb = ((o_t1 + (S + 1) * 4) + 7) & ~(size_t)7,
+                 o_bb = o_gb + (S + 1) * 8, need = o_bb + (S + 1) * 8;
+    CK(ensure_host(ctx->h_stage, need));
+    CK(ensure(ctx->segs, need));
+    char* hs = (char*)ctx->h_stage.p;
+    memcpy(hs + o_seg, pl.segs.data(), S * sizeof(Seg));
+    memcpy(hs + o_rb, pl.range_base.data(), (S + 1) * 4);
+    memcpy(hs + o_k1, pl.k1_base.data(), (S + 1) * 4);
+    memcpy(hs + o_t1, pl.tile1_base.data(), (S + 1) * 4);
+    memcpy(hs + o_gb, pl.group_base.data(), (S + 1) * 8);
+    memcpy(hs + o_bb, pl.bucket_base.data(), (S + 1) * 8);
+    CK(cudaMemcpyAsync(ctx->segs.p, hs, need, cudaMemcpyHostToDevice, st));
+    char* ds = (char*)ctx->segs.p;
+    Seg* d_segs = (Seg*)(ds + o_seg);
+    const uint32_t* d_rb = (const uint32_t*)(ds + o_rb);
+    const uint32_t* d_k1 = (const uint32_t*)(ds + o_k1);
+    const uint32_t* d_t1 = (const uint32_t*)(ds + o_t1);
+    const uint64_t* d_gb = (const uint64_t*)(ds + o_gb);
+    const uint64_t* d_bb = (const uint64_t*)(ds + o_bb);
+
+    // range, model
+    CK(launch_range(lc, d_segs, S, d_rb, pl.range_base[S], src, first && kt == KEY_F64));
+    if (first && kt == KEY_F64) {
+      CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+    }
+    if (first) {
+      pcf_status r = launch_small();
+      if (r != PCF_OK) return r;
+    }
+    CK(launch_model(lc, d_segs, S));
+    tm.mark(0);
+    if (first && src != out_k)
+      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], src, out_k, src_v, out_v));
+    // lists
+    const uint64_t max_items = std::max<uint64_t>(pl.n_buckets, S) + 16;
+    CK(ensure(ctx->leaf, max_items * sizeof(WorkItem)));
+    CK(ensure(ctx->next, max_items * sizeof(WorkItem)));
+    CK(ensure(ctx->fb, max_items * sizeof(FbItem)));
+    LevelOut* d_lo = as<LevelOut>(ctx->lout);
+    CK(cudaMemsetAsync(d_lo, 0, sizeof(LevelOut), st));
+    CK(launch_seg_status_lists(lc, d_segs, S, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
+    // sample + PCF
+    CK(ensure(ctx->tpool, pl.tpool * 4));
+    CK(ensure(ctx->done, S * 4));
+    CK(cudaMemsetAsync(ctx->tpool.p, 0, pl.tpool * 4, st));
+    CK(cudaMemsetAsync(ctx->done.p, 0, S * 4, st));
+    CK(launch_sample(lc, d_segs, S, d_k1, pl.k1_base[S], src, as<uint32_t>(ctx->tpool),
+                     as<uint32_t>(ctx->done), ctx->policy));
+    tm.mark(1);
+    // pass 1
+    CK(ensure(ctx->tmp_k, n_total * 8));
+    CK(ensure(ctx->tmp_aux, n_total * 2));
+    if (pairs) CK(ensure(ctx->tmp_v, n_total * 4));
+    KeyBufs kb;
+    kb.src = src;
+    kb.src_v = src_v;
+    kb.tmp = as<uint64_t>(ctx->tmp_k);
+    kb.tmp_v = pairs ? as<uint32_t>(ctx->tmp_v) : nullptr;
+    kb.tmp_aux = as<uint16_t>(ctx->tmp_aux);
+    kb.out = out_k;
+    kb.out_v = out_v;
+    const uint64_t sw_need = ((std::max(pl.cmat1, pl.cmat2_bound) + kScanTile - 1) / kScanTile +
+                              (pl.n_groups + kScanTile - 1) / kScanTile + 8) * 8;
+    CK(ensure(ctx->sw, sw_need));
+    CK(ensure(ctx->cmat1, pl.cmat1 * 4));
+    CK(cudaMemsetAsync(ctx->cmat1.p, 0, pl.cmat1 * 4, st));
+    uint32_t* tile_counter = as<uint32_t>(ctx->misc);
+    uint64_t* totals = (uint64_t*)((char*)ctx->misc.p + 64);
+    CK(launch_hist1(lc, d_segs, S, d_t1, pl.tile1_base[S], tile_keys, src,
+                    as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1));
+    CK(launch_scan(lc, as<uint32_t>(ctx->cmat1), pl.cmat1, nullptr, as<uint64_t>(ctx->sw),
+                   tile_counter, scan_withhold, spin_limit, nullptr));
+    tm.mark(2);
+    CK(launch_scatter1(lc, d_segs, S, d_t1, pl.tile1_base[S], tile_keys, kb,
+                       as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1));
+    tm.mark(3);
+    // pass 2
+    CK(ensure(ctx->groups, pl.n_groups * sizeof(Group)));
+    CK(ensure(ctx->gtiles, pl.n_groups * 4));
+    CK(ensure(ctx->gcent, pl.n_groups * 4));
+    CK(launch_groups(lc, d_segs, S, d_gb, pl.n_groups, as<uint32_t>(ctx->cmat1), tile_keys,
+                     as<Group>(ctx->groups), as<uint32_t>(ctx->gtiles), as<uint32_t>(ctx->gcent)));
+    CK(launch_scan(lc, as<uint32_t>(ctx->gtiles), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
+                   tile_counter, 0xFFFFFFFFu, spin_limit, &totals[0]));
+    CK(launch_scan(lc, as<uint32_t>(ctx->gcent), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
+                   tile_counter, 0xFFFFFFFFu, spin_limit, &totals[1]));
+    CK(launch_group_bases(lc, as<Group>(ctx->groups), pl.n_groups, as<uint32_t>(ctx->gcent)));
+    CK(ensure(ctx->cmat2, pl.cmat2_bound * 4));
+    CK(cudaMemsetAsync(ctx->cmat2.p, 0, pl.cmat2_bound * 4, st));
+    CK(launch_hist2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
+                    as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound, tile_keys,
+                    kb.tmp_aux, as<uint32_t>(ctx->cmat2), pl.dmax2));
+    CK(launch_scan(lc, as<uint32_t>(ctx->cmat2), pl.cmat2_bound, &totals[1],
+                   as<uint64_t>(ctx->sw), tile_counter, 0xFFFFFFFFu, spin_limit, nullptr));
+    tm.mark(4);
+    CK(launch_scatter2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
+                       as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound,
+                       tile_keys, kb, as<uint32_t>(ctx->cmat2), pl.dmax2));
+    tm.mark(5);
+    ctx->stats.global_passes += 2;
+    ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 /*hist1*/ + 8 + 10 /*scatter1*/ +
+                                         2 /*hist2*/ + 10 + 8 /*scatter2*/) +
+                              (pairs ? n_level * 16 : 0);
+    // buckets
+    CK(launch_buckets(lc, d_segs, S, pl.n_buckets, d_bb, as<Group>(ctx->groups),
+                      as<uint32_t>(ctx->cmat2), cap, as<WorkItem>(ctx->leaf),
+                      as<WorkItem>(ctx->next), as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
+    CK(launch_leaf(lc, as<WorkItem>(ctx->leaf), &d_lo->n_leaf, &d_lo->leaf_cursor, out_k, out_k,
+                   out_v, out_v, ctx->policy, cap, lg.tmax, lg.gmax, lg.warps, lg.grid));
+    tm.mark(6);
+    CK(cudaMemcpyAsync(ctx->h_lout.p, d_lo, sizeof(LevelOut), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const LevelOut lo = *(LevelOut*)ctx->h_lout.p;
+    const uint32_t stw = *(uint32_t*)ctx->h_status.p;
+    if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
+    if (stw & STATUS_INTERNAL) return PCF_ERR_INTERNAL;
+    ctx->stats.leaf_buckets += lo.n_leaf;
+    // standard sort of the large failure-guard / degenerate buckets
+    std::vector<InSeg> nextl;
+    if (lo.n_fb) {
+      const uint32_t nf = lo.n_fb;
+      std::vector<FbItem> items(nf);
+      CK(cudaMemcpy(items.data(), ctx->fb.p, nf * sizeof(FbItem), cudaMemcpyDeviceToHost));
+      std::vector<uint32_t> rb(nf + 1, 0), mb(nf + 1, 0);
+      uint64_t max_n = 0;
+      for (uint32_t i = 0; i < nf; ++i) {
+        rb[i + 1] = rb[i] + (uint32_t)((items[i].n + kRangeTile - 1) / kRangeTile);
+        mb[i + 1] = mb[i] + (uint32_t)((items[i].n + kMergeTile - 1) / kMergeTile);
+        max_n = std::max<uint64_t>(max_n, items[i].n);
+        ctx->stats.fallback_keys += items[i].n;
+      }
+      ctx->stats.fallback_buckets += nf;
+      const size_t need2 = (nf + 1) * 8 + 64;
+      CK(ensure(ctx->fb_bases, need2));
+      CK(ensure(ctx->fb_lohi, nf * 16 + 16));
+      std::vector<uint64_t> lohi(2 * nf);
+      for (uint32_t i = 0; i < nf; ++i) {
+        lohi[2 * i] = ~0ull;
+        lohi[2 * i + 1] = 0;
+      }
+      CK(cudaMemcpyAsync(ctx->fb_bases.p, rb.data(), (nf + 1) * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync((char*)ctx->fb_bases.p + (nf + 1) * 4, mb.data(), (nf + 1) * 4,
+                         cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(ctx->fb_lohi.p, lohi.data(), nf * 16, cudaMemcpyHostToDevice, st));
+      CK(launch_fb_range(lc, as<FbItem>(ctx->fb), nf, as<uint32_t>(ctx->fb_bases), rb[nf], out_k,
+                         as<uint64_t>(ctx->fb_lohi)));
+      CK(launch_fb_sort(lc, as<FbItem>(ctx->fb), nf,
+                        (const uint32_t*)((char*)ctx->fb_bases.p + (nf + 1) * 4), mb[nf], max_n,
+                        as<uint64_t>(ctx->fb_lohi), out_k, as<uint64_t>(ctx->tmp_k), out_v,
+                        pairs ? as<uint32_t>(ctx->tmp_v) : nullptr));
+      CK(cudaStreamSynchronize(st));
+      tm.mark(7);
+    }
+    if (lo.n_next) {
+      std::vector<WorkItem> items(lo.n_next);
+      CK(cudaMemcpy(items.data(), ctx->next.p, lo.n_next * sizeof(WorkItem),
+                    cudaMemcpyDeviceToHost));
+      nextl.reserve(lo.n_next);
+      for (auto& it : items) nextl.push_back(InSeg{it.off, it.n, it.start, it.seed, it.depth});
+      std::sort(nextl.begin(), nextl.end(),
+                [](const InSeg& a, const InSeg& b) { return a.off < b.off; });
+    }
+    level.swap(nextl);
+    src = out_k;
+    src_v = out_v;
+    first = false;
+  }
+  CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t stw = *(uint32_t*)ctx->h_status.p;
+  if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+  if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
+  if (stw & STATUS_INTERNAL) return PCF_ERR_INTERNAL;
+  return PCF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+uint32_t pcf_version(void) { return 100; }
+
+const char* pcf_status_string(pcf_status s) {
+  switch (s) {
+    case PCF_OK: return "ok";
+    case PCF_ERR_INVALID_ARG: return "invalid argument";
+    case PCF_ERR_INVALID_KEY: return "invalid key (NaN)";
+    case PCF_ERR_OOM: return "out of memory";
+    case PCF_ERR_CUDA: return "CUDA error";
+    case PCF_ERR_TIMEOUT: return "device wait timed out";
+    case PCF_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+pcf_status pcf_ctx_create(pcf_ctx** out, int device) {
+  if (!out) return PCF_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return PCF_ERR_INVALID_ARG;
+  }
+  pcf_ctx* c = new (std::nothrow) pcf_ctx();
+  if (!c) return PCF_ERR_OOM;
+  c->device = device;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return PCF_ERR_CUDA;
+  }
+  *out = c;
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_destroy(pcf_ctx* ctx) {
+  if (!ctx) return PCF_OK;
+  cudaSetDevice(ctx->device);
+  delete ctx;
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_set_policy(pcf_ctx* ctx, const pcf_policy* p) {
+  if (!ctx || !p) return PCF_ERR_INVALID_ARG;
+  Policy P{p->a_num, p->b_num, p->c_num, p->d_num, p->den, 0, p->tau};
+  if (!policy_ok(P)) return PCF_ERR_INVALID_ARG;
+  ctx->policy = P;
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_set_tuning(pcf_ctx* ctx, const pcf_tuning* t) {
+  if (!ctx || !t) return PCF_ERR_INVALID_ARG;
+  pcf_tuning n = ctx->tuning;
+  if (t->max_digit_bits) n.max_digit_bits = t->max_digit_bits;
+  if (t->tile_log2) n.tile_log2 = t->tile_log2;
+  if (t->leaf_cap) n.leaf_cap = t->leaf_cap;
+  if (n.max_digit_bits < 4 || n.max_digit_bits > 11) return PCF_ERR_INVALID_ARG;
+  if (n.tile_log2 < 12 || n.tile_log2 > 18) return PCF_ERR_INVALID_ARG;
+  if (n.leaf_cap < 64 || n.leaf_cap > 1024 || (n.leaf_cap & (n.leaf_cap - 1))) return PCF_ERR_INVALID_ARG;
+  ctx->tuning = n;
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_get_tuning(const pcf_ctx* ctx, pcf_tuning* out) {
+  if (!ctx || !out) return PCF_ERR_INVALID_ARG;
+  *out = ctx->tuning;
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_reserve(pcf_ctx* ctx, uint64_t n_total, int pairs) {
+  if (!ctx) return PCF_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(ensure(ctx->tmp_k, n_total * 8));
+  CK(ensure(ctx->tmp_aux, n_total * 2));
+  if (pairs) CK(ensure(ctx->tmp_v, n_total * 4));
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_last_stats(const pcf_ctx* ctx, pcf_call_stats* out) {
+  if (!ctx || !out) return PCF_ERR_INVALID_ARG;
+  *out = ctx->stats;
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_enable_timing(pcf_ctx* ctx, int on) {
+  if (!ctx) return PCF_ERR_INVALID_ARG;
+  ctx->timing = on != 0;
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_stage_ms(const pcf_ctx* ctx, float out[8]) {
+  if (!ctx || !out) return PCF_ERR_INVALID_ARG;
+  for (int i = 0; i < 8; ++i) out[i] = ctx->stage_ms[i];
+  return PCF_OK;
+}
+
+const char* pcf_last_cuda_error(const pcf_ctx* ctx) { return ctx ? ctx->last_err.c_str() : ""; }
+
+static bool overlap(const void* a, const void* b, uint64_t bytes) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x != y && x < y + bytes && y < x + bytes;
+}
+
+static pcf_status sort_common(pcf_ctx* ctx, const void* kin, const uint32_t* vin, void* kout,
+                              uint32_t* vout, const std::vector<InSeg>& segs, uint64_t n,
+                              pcf_key_type kt, bool pairs, void* stream) {
+  if (!ctx) return PCF_ERR_INVALID_ARG;
+  if (kt != PCF_KEY_F64 && kt != PCF_KEY_U64) return PCF_ERR_INVALID_ARG;
+  if (n > 0xFFFFFFFFull) return PCF_ERR_INVALID_ARG;
+  if (n == 0) return PCF_OK;
+  if (!kin || !kout || (pairs && (!vin || !vout))) return PCF_ERR_INVALID_ARG;
+  if (((uintptr_t)kin & 7) || ((uintptr_t)kout & 7)) return PCF_ERR_INVALID_ARG;
+  if (pairs && (((uintptr_t)vin & 3) || ((uintptr_t)vout & 3))) return PCF_ERR_INVALID_ARG;
+  if (overlap(kin, kout, n * 8)) return PCF_ERR_INVALID_ARG;
+  if (pairs && overlap(vin, vout, n * 4)) return PCF_ERR_INVALID_ARG;
+  if (!policy_ok(ctx->policy)) return PCF_ERR_INVALID_ARG;
+  return run_sort(ctx, (const uint64_t*)kin, vin, (uint64_t*)kout, vout, segs, (uint32_t)kt,
+                  pairs, (cudaStream_t)stream);
+}
+
+pcf_status pcf_sort_keys(pcf_ctx* ctx, const void* d_in, void* d_out, uint64_t n, pcf_key_type kt,
+                         uint64_t seed, void* stream) {
+  std::vector<InSeg> segs{InSeg{0, n, 0, seed, 0}};
+  // offsets in the kernels are relative to the buffer base
+  return sort_common(ctx, d_in, nullptr, d_out, nullptr, segs, n, kt, false, stream);
+}
+
+pcf_status pcf_sort_pairs(pcf_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
+                          void* d_keys_out, uint32_t* d_vals_out, uint64_t n, pcf_key_type kt,
+                          uint64_t seed, void* stream) {
+  std::vector<InSeg> segs{InSeg{0, n, 0, seed, 0}};
+  return sort_common(ctx, d_keys_in, d_vals_in, d_keys_out, d_vals_out, segs, n, kt, true,
+                     stream);
+}
+
+pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
+                              void* d_keys_out, uint32_t* d_vals_out, const uint64_t* h_offsets,
+                              uint32_t S, pcf_key_type kt, uint64_t seed, void* stream) {
+  if (!ctx || (!h_offsets && S)) return PCF_ERR_INVALID_ARG;
+  if (S == 0) return PCF_OK;
+  if (h_offsets[0] != 0) return PCF_ERR_INVALID_ARG;
+  std::vector<InSeg> segs;
+  segs.reserve(S);
+  for (uint32_t s = 0; s < S; ++s) {
+    if (h_offsets[s + 1] < h_offsets[s]) return PCF_ERR_INVALID_ARG;
+    segs.push_back(InSeg{h_offsets[s], h_offsets[s + 1] - h_offsets[s], 0, seed + s, 0});
+  }
+  const bool pairs = d_vals_in != nullptr || d_vals_out != nullptr;
+  return sort_common(ctx, d_keys_in, d_vals_in, d_keys_out, d_vals_out, segs, h_offsets[S], kt,
+                     pairs, stream);
+}
+
+pcf_status pcf_sort_keys_host(pcf_ctx* ctx, void* h_keys, uint64_t n, pcf_key_type kt,
+                              uint64_t seed, void* stream) {
+  if (!ctx || (!h_keys && n)) return PCF_ERR_INVALID_ARG;
+  if (n == 0) return PCF_OK;
+  if (n > 0xFFFFFFFFull) return PCF_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(ensure(ctx->host_keys, n * 8));
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(ctx->host_keys.p, h_keys, n * 8, cudaMemcpyHostToDevice, st));
+  std::vector<InSeg> segs{InSeg{0, n, 0, seed, 0}};
+  pcf_status s = sort_common(ctx, ctx->host_keys.p, nullptr, ctx->host_keys.p, nullptr, segs, n,
+                             kt, false, stream);
+  if (s != PCF_OK) return s;
+  CK(cudaMemcpyAsync(h_keys, ctx->host_keys.p, n * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PCF_OK;
+}
+
+// ---- self-test hooks (used by the test suite) ----
+
+// Host copy of the kernels' bin function, for CPU checks of the fast path.
+// Returns 1 (and writes nothing) if the range [lo, hi] is degenerate.
+int pcf_debug_bins_host(uint32_t kt, uint64_t lo_bits, uint64_t hi_bits, uint32_t beta,
+                        const uint64_t* xs, uint64_t m, uint32_t* out, uint8_t* fast_decided) {
+  BinModel M;
+  if (make_bin_model(kt, lo_bits, hi_bits, beta, &M)) return 1;
+  for (uint64_t i = 0; i < m; ++i) {
+    out[i] = bin_of(M, xs[i]);
+    if (fast_decided) fast_decided[i] = bin_fast_decides(M, xs[i]) ? 1 : 0;
+  }
+  return 0;
+}
+
+// Host copy of floor(n^{p/q}) and of the sample index stream.
+uint64_t pcf_debug_root_floor(uint64_t n, uint32_t p, uint32_t q) { return root_floor(n, p, q); }
+uint64_t pcf_debug_sample_index(uint64_t seed, uint64_t depth, uint64_t start, uint64_t n,
+                                uint64_t j) {
+  return sample_index(sample_state(seed, depth, start, n), j, n);
+}
+
+// Runs the decoupled-lookback scan on d_data[0..n) in place.  withhold_tile:
+// a tile that never publishes (timeout test), or UINT32_MAX.
+pcf_status pcf_debug_scan(pcf_ctx* ctx, uint32_t* d_data, uint64_t n, uint32_t withhold_tile,
+                          uint64_t spin_limit, void* stream) {
+  if (!ctx || (!d_data && n)) return PCF_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device));
+  CK(ensure(ctx->status, 64));
+  CK(ensure(ctx->misc, 256));
+  CK(ensure(ctx->sw, ((n + kScanTile - 1) / kScanTile + 8) * 8));
+  CK(ensure_host(ctx->h_status, 64));
+  LaunchCfg lc;
+  lc.stream = st;
+  lc.kt = 0;
+  lc.pairs = false;
+  lc.launches = nullptr;
+  lc.status = as<uint32_t>(ctx->status);
+  CK(cudaMemsetAsync(lc.status, 0, 4, st));
+  CK(launch_scan(lc, d_data, n, nullptr, as<uint64_t>(ctx->sw), as<uint32_t>(ctx->misc),
+                 withhold_tile, spin_limit ? spin_limit : kSpinLimit, nullptr));
+  CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t w = *(uint32_t*)ctx->h_status.p;
+  if (w & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
+  return PCF_OK;
+}
+
+// Level-0 model of one array on the device (for intermediate parity): the
+// range bits, alpha..delta, status, and T (beta + 1 u32) copied to h_T.
+pcf_status pcf_debug_level0(pcf_ctx* ctx, const void* d_keys, uint64_t n, pcf_key_type kt,
+                            uint64_t seed, uint64_t* h_params8, uint32_t* h_T, uint64_t T_cap) {
+  if (!ctx || !d_keys || n < 2 || !h_params8) return PCF_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<InSeg> in{InSeg{0, n, 0, seed, 0}};
+  Plan pl;
+  plan_level(ctx->policy, ctx->tuning, in, pl);
+  const uint32_t S = 1;
+  CK(ensure(ctx->status, 64));
+  CK(ensure(ctx->segs, sizeof(Seg) + 64));
+  CK(ensure(ctx->bases, 64));
+  CK(ensure(ctx->tpool, pl.tpool * 4));
+  CK(ensure(ctx->done, 16));
+  LaunchCfg lc;
+  lc.stream = 0;
+  lc.kt = kt;
+  lc.pairs = false;
+  lc.launches = nullptr;
+  lc.status = as<uint32_t>(ctx->status);
+  CK(cudaMemset(lc.status, 0, 4));
+  CK(cudaMemcpy(ctx->segs.p, pl.segs.data(), sizeof(Seg), cudaMemcpyHostToDevice));
+  uint32_t bases[4] = {0, pl.range_base[1], 0, pl.k1_base[1]};
+  CK(cudaMemcpy(ctx->bases.p, bases, 16, cudaMemcpyHostToDevice));
+  CK(cudaMemset(ctx->tpool.p, 0, pl.tpool * 4));
+  CK(cudaMemset(ctx->done.p, 0, 4));
+  CK(launch_range(lc, as<Seg>(ctx->segs), S, as<uint32_t>(ctx->bases), pl.range_base[1],
+                  (const uint64_t*)d_keys, kt == PCF_KEY_F64));
+  CK(launch_model(lc, as<Seg>(ctx->segs), S));
+  CK(launch_sample(lc, as<Seg>(ctx->segs), S, as<uint32_t>(ctx->bases) + 2, pl.k1_base[1],
+                   (const uint64_t*)d_keys, as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->done),
+                   ctx->policy));
+  Seg g;
+  CK(cudaMemcpy(&g, ctx->segs.p, sizeof(Seg), cudaMemcpyDeviceToHost));
+  h_params8[0] = g.alpha;
+  h_params8[1] = g.beta;
+  h_params8[2] = g.gamma;
+  h_params8[3] = g.delta;
+  h_params8[4] = bits_of_ord(g.ord_lo, kt);
+  h_params8[5] = bits_of_ord(g.ord_hi, kt);
+  h_params8[6] = g.status;
+  h_params8[7] = 0;
+  if (h_T && g.status == SEG_BUCKET) {
+    if (T_cap < (uint64_t)g.beta + 1) return PCF_ERR_INVALID_ARG;
+    CK(cudaMemcpy(h_T, ctx->tpool.p, ((size_t)g.beta + 1) * 4, cudaMemcpyDeviceToHost));
+  }
+  return PCF_OK;
+}
+
+}  // extern "C"

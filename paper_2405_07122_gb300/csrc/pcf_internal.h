@@ -1,0 +1,165 @@
+// pcf_internal.h -- work descriptors shared by the kernels and the host
+// driver of the PCF Learned Sort library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pcf_common.cuh"
+
+namespace pcf {
+
+// Status bits written by kernels into the context's device status word.
+enum : uint32_t {
+  STATUS_NAN = 1u,       // a NaN key was seen (binary64 keys)
+  STATUS_TIMEOUT = 2u,   // a bounded wait gave up
+  STATUS_INTERNAL = 4u,  // an internal capacity check failed
+};
+
+enum : uint32_t { SEG_BUCKET = 0, SEG_SINGLE = 1, SEG_DEGEN = 2 };
+
+// One (sub)array bucketed by a global level (Algorithm 1, one call of
+// Learned-Sort with its own model).  Host-planned fields first.
+struct Seg {
+  uint64_t off;     // offset of its first key in the key buffers
+  uint64_t n;       // number of keys
+  uint64_t start;   // offset inside the caller's array (keys the sample stream)
+  uint64_t seed;    // the caller's seed for this array
+  uint32_t depth;   // recursion depth (0 = the caller's array)
+  uint32_t status;  // SEG_* (set on the device from the range)
+  uint32_t alpha, beta, gamma, delta;
+  uint32_t b1, b2;  // bucket-id bits scattered by pass 1 / pass 2 (b1 + b2 = bits of gamma)
+  uint64_t T_off;   // its table (beta + 1 u32) in the table pool
+  uint64_t cbase1;  // its pass-1 count block (2^b1 x tiles1) in the pass-1 matrix
+  uint64_t key_prefix;  // sum of n over the earlier segments of the level
+  uint32_t tiles1;      // count tiles of pass 1
+  uint32_t pad0;
+  uint64_t group_base;  // index of its first pass-1 group
+  uint64_t bucket_base; // index of its first bucket (gamma + 1 of them)
+  uint64_t ord_lo, ord_hi;  // range (total-order keys), reduced on the device
+  BinModel bm;
+};
+
+// A pass-2 segment: the keys of one pass-1 digit of one Seg.
+struct Group {
+  uint64_t off;         // key offset of its first key
+  uint64_t key_prefix;  // compacted offset (sum of sizes of earlier groups)
+  uint64_t cbase;       // its count block (2^b2 x tiles) in the pass-2 matrix
+  uint32_t n;
+  uint32_t tiles;
+  uint32_t seg;
+  uint32_t pad;
+};
+
+// A bucket finished in shared memory, or a (sub)array queued for the next
+// global level: Learned-Sort(keys [off, off+n)) at `depth`.
+struct WorkItem {
+  uint64_t off;
+  uint64_t start;
+  uint64_t seed;
+  uint32_t n;
+  uint32_t depth;
+};
+
+// A bucket for the standard sort (failure guard |c| >= delta, or a
+// degenerate range).
+struct FbItem {
+  uint64_t off;
+  uint64_t n;
+};
+
+// Counters written by k_buckets.
+struct LevelOut {
+  uint32_t n_leaf;
+  uint32_t n_next;
+  uint32_t n_fb;
+  uint32_t pad;
+  uint64_t leaf_keys, next_keys, fb_keys;
+  uint32_t max_fb_n;  // largest standard-sort bucket (sizes the merge passes)
+  uint32_t leaf_cursor; // work counter of the leaf kernel
+};
+
+struct KeyBufs {
+  const uint64_t* src;  // where the level reads
+  uint64_t* tmp;        // pass-1 target
+  uint64_t* out;        // pass-2 target / final
+  const uint32_t* src_v;
+  uint32_t* tmp_v;
+  uint32_t* out_v;
+  uint16_t* tmp_aux;    // low bucket-id digit carried from pass 1 to pass 2
+};
+
+// ---- kernel launchers (pcf_kernels.cu) ----
+struct LaunchCfg {
+  cudaStream_t stream;
+  uint32_t kt;
+  bool pairs;
+  uint32_t* status;  // device status word
+  uint64_t* launches;  // host counter of kernel launches (may be null)
+};
+
+inline void count_launch(const LaunchCfg& c, uint64_t k = 1) {
+  if (c.launches) *c.launches += k;
+}
+
+// Tile sizes (keys).
+constexpr uint32_t kRangeTile = 16384;
+constexpr uint32_t kSamplesPerCta = 4096;
+constexpr uint32_t kScatterSub = 4096;  // keys staged in shared memory at once
+constexpr uint32_t kScanTile = 4096;    // entries per decoupled-lookback tile
+constexpr uint32_t kMergeTile = 2048;   // keys per block-sorted run
+constexpr uint32_t kMaxDigitBits = 12;
+
+cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* range_base,
+                         uint32_t n_tiles, const uint64_t* keys, bool check_nan);
+cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S);
+cudaError_t launch_sample(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
+                          uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool,
+                          uint32_t* done, Policy P);
+cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
+                         uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
+                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax);
+cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const uint64_t* n_dev,
+                        uint64_t* status_words, uint32_t* tile_counter, uint32_t withhold,
+                        uint64_t spin_limit, uint64_t* total_out);
+cudaError_t launch_scatter1(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                            const uint32_t* tile_base, uint32_t n_tiles, uint32_t tile_keys,
+                            const KeyBufs& kb, const uint32_t* tpool, const uint32_t* cmat,
+                            uint32_t dmax);
+cudaError_t launch_groups(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                          const uint64_t* group_base_dev, uint64_t n_groups, const uint32_t* cmat1,
+                          uint32_t tile_keys, Group* groups, uint32_t* g_tiles,
+                          uint32_t* g_centries);
+cudaError_t launch_group_bases(const LaunchCfg& c, Group* groups, uint64_t n_groups,
+                               const uint32_t* g_centries_scan);
+cudaError_t launch_hist2(const LaunchCfg& c, const Group* groups, uint32_t n_groups,
+                         const Seg* segs, const uint32_t* g_tile_scan, const uint64_t* total_tiles,
+                         uint32_t n_tiles_bound, uint32_t tile_keys, const uint16_t* aux,
+                         uint32_t* cmat2, uint32_t dmax);
+cudaError_t launch_scatter2(const LaunchCfg& c, const Group* groups, uint32_t n_groups,
+                            const Seg* segs, const uint32_t* g_tile_scan,
+                            const uint64_t* total_tiles, uint32_t n_tiles_bound,
+                            uint32_t tile_keys, const KeyBufs& kb, const uint32_t* cmat2,
+                            uint32_t dmax);
+cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint64_t n_buckets,
+                           const uint64_t* bucket_base, const Group* groups,
+                           const uint32_t* cmat2, uint32_t leaf_cap, WorkItem* leaf,
+                           WorkItem* next, FbItem* fb, LevelOut* lo, uint32_t max_items);
+cudaError_t launch_seg_status_lists(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                                    FbItem* fb, LevelOut* lo, uint32_t max_items);
+cudaError_t launch_copy_segs(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                             const uint32_t* range_base, uint32_t n_tiles, const uint64_t* src,
+                             uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v);
+cudaError_t launch_leaf(const LaunchCfg& c, const WorkItem* items, const uint32_t* n_items,
+                        uint32_t* cursor, const uint64_t* src, uint64_t* dst,
+                        const uint32_t* src_v, uint32_t* dst_v, Policy P, uint32_t cap,
+                        uint32_t tmax, uint32_t gmax, uint32_t warps_per_cta, uint32_t grid);
+size_t leaf_smem_per_warp(uint32_t cap, bool pairs, uint32_t tmax, uint32_t gmax);
+cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
+                            const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
+                            uint64_t* ord_lohi);
+cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
+                           const uint32_t* mtile_base, uint32_t n_mtiles, uint64_t max_n,
+                           const uint64_t* ord_lohi, uint64_t* keys, uint64_t* tmp,
+                           uint32_t* vals, uint32_t* tmp_v);
+
+}  // namespace pcf

@@ -1,0 +1,907 @@
+// pcf_level.cu -- the kernels of one global bucketing level of PCF Learned
+// Sort (Sato & Matsui, TMLR 2025, Algorithm 1 with the PCF model of
+// Sec. 3.3), for a batch of (sub)arrays ("segments"):
+//
+//   k_range     x_min, x_max of every segment (+ NaN check)          Sec. 3.3
+//   k_model     degenerate-range test and the bin function's constants
+//   k_sample    draw alpha keys, count them per bin, and (last CTA of the
+//               segment) accumulate b_k and the bucket table
+//               T[k] = floor(b_k gamma / alpha)                        Sec. 3.3, Alg. 1
+//   k_hist1     per-tile histogram of the high digit of the bucket id
+//   k_scan      decoupled-lookback exclusive prefix sum (Merrill & Garland)
+//   k_scatter1  stable scatter by the high digit ("Append" in input order)
+//   k_groups / k_hist2 / k_scatter2   the same for the low digit, per group
+//   k_buckets   the per-bucket decision of Alg. 1 (|c| >= delta -> standard
+//               sort; small -> shared-memory kernel; else next level)
+//
+// The gamma + 1 buckets are produced by two stable scatters on the high and
+// the low bits of the bucket id; two stable passes compose to the single
+// (gamma+1)-way stable partition of Alg. 1.
+#include "pcf_internal.h"
+
+namespace pcf {
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// first i in [0, n) with a[i] > v, for non-decreasing a
+template <typename T>
+__device__ __forceinline__ uint32_t upper_bound_dev(const T* a, uint32_t n, T v) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t ld_nc(const uint64_t* p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// k_range: min / max under the total order (x_min, x_max of Sec. 3.3)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_range(Seg* segs, uint32_t S, const uint32_t* range_base,
+                                               const uint64_t* __restrict__ keys, uint32_t kt,
+                                               int check_nan, uint32_t* status) {
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = upper_bound_dev(range_base, S + 1, t) - 1;
+  const uint64_t off = segs[s].off, n = segs[s].n;
+  const uint64_t base = off + (uint64_t)(t - range_base[s]) * kRangeTile;
+  const uint64_t end = min(off + n, base + kRangeTile);
+  uint64_t mn = ~0ull, mx = 0ull;
+  bool nan = false;
+  uint64_t i = base + threadIdx.x;
+  for (; i + 3 * 256 < end; i += 4 * 256) {
+    uint64_t b0 = ld_nc(keys + i), b1 = ld_nc(keys + i + 256), b2 = ld_nc(keys + i + 512),
+             b3 = ld_nc(keys + i + 768);
+    if (check_nan) nan |= is_nan_bits(b0) | is_nan_bits(b1) | is_nan_bits(b2) | is_nan_bits(b3);
+    uint64_t o0 = ord_of(b0, kt), o1 = ord_of(b1, kt), o2 = ord_of(b2, kt), o3 = ord_of(b3, kt);
+    mn = min(mn, min(min(o0, o1), min(o2, o3)));
+    mx = max(mx, max(max(o0, o1), max(o2, o3)));
+  }
+  for (; i < end; i += 256) {
+    uint64_t b = ld_nc(keys + i);
+    if (check_nan) nan |= is_nan_bits(b);
+    uint64_t o = ord_of(b, kt);
+    mn = min(mn, o);
+    mx = max(mx, o);
+  }
+  for (int d = 16; d; d >>= 1) {
+    mn = min(mn, (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d));
+    mx = max(mx, (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d));
+  }
+  nan = __any_sync(~0u, nan);
+  __shared__ uint64_t smn[8], smx[8];
+  __shared__ int snan;
+  if (threadIdx.x == 0) snan = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    smn[w] = mn;
+    smx[w] = mx;
+    if (nan) snan = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < 8; ++k) {
+      mn = min(mn, smn[k]);
+      mx = max(mx, smx[k]);
+    }
+    atomicMin((unsigned long long*)&segs[s].ord_lo, (unsigned long long)mn);
+    atomicMax((unsigned long long*)&segs[s].ord_hi, (unsigned long long)mx);
+    if (snan) atomicOr(status, STATUS_NAN);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_model: Alg. 1's early exits and the bin constants
+// ---------------------------------------------------------------------------
+__global__ void k_model(Seg* segs, uint32_t S, uint32_t kt) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  Seg& g = segs[s];
+  if (g.ord_lo == g.ord_hi) {  // one distinct value: already sorted
+    g.status = SEG_SINGLE;
+    return;
+  }
+  const uint64_t lo = bits_of_ord(g.ord_lo, kt), hi = bits_of_ord(g.ord_hi, kt);
+  g.status = make_bin_model(kt, lo, hi, g.beta, &g.bm) ? SEG_DEGEN : SEG_BUCKET;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide helpers (256 threads)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T u = __shfl_up_sync(~0u, v, d);
+    if (l >= d) v += u;
+  }
+  return v;
+}
+
+// exclusive scan across the 256 threads; returns the block total in *total
+template <typename T>
+__device__ __forceinline__ T block_excl_scan256(T v, T* sh8, T* total) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  T inc = warp_incl_scan(v);
+  if (l == 31) sh8[w] = inc;
+  __syncthreads();
+  T wsum = 0, tot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    T x = sh8[k];
+    if (k < w) wsum += x;
+    tot += x;
+  }
+  __syncthreads();
+  *total = tot;
+  return wsum + inc - v;
+}
+
+// ---------------------------------------------------------------------------
+// k_sample: training (Sec. 3.3).  alpha samples are drawn with replacement,
+// counted per bin; the last CTA of the segment turns the counts into
+// b_k = |{j : bin(a_j) <= k}| and the bucket table T[k] in place.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sample(const Seg* segs, uint32_t S,
+                                                const uint32_t* k1_base,
+                                                const uint64_t* __restrict__ keys, uint32_t kt,
+                                                uint32_t* tpool, uint32_t* done) {
+  const uint32_t c = blockIdx.x;
+  const uint32_t s = upper_bound_dev(k1_base, S + 1, c) - 1;
+  const Seg& g = segs[s];
+  if (g.status != SEG_BUCKET) return;
+  __shared__ BinModel bm;
+  __shared__ uint32_t s_last;
+  __shared__ uint32_t sh8[8];
+  if (threadIdx.x == 0) bm = g.bm;
+  __syncthreads();
+  const uint32_t cta = c - k1_base[s], nctas = k1_base[s + 1] - k1_base[s];
+  const uint64_t st = sample_state(g.seed, g.depth, g.start, g.n);
+  const uint32_t j0 = cta * kSamplesPerCta, j1 = min(g.alpha, j0 + kSamplesPerCta);
+  uint32_t* cnt = tpool + g.T_off;
+  for (uint32_t j = j0 + threadIdx.x; j < j1; j += 256) {
+    uint64_t idx = sample_index(st, j, g.n);
+    uint64_t x = ld_nc(keys + g.off + idx);
+    atomicAdd(&cnt[bin_of(bm, x)], 1u);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&done[s], 1u) == nctas - 1) ? 1u : 0u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // inclusive scan of cnt[0..beta] -> b, then T = floor(b gamma / alpha)
+  const uint32_t L = g.beta + 1, alpha = g.alpha, gamma = g.gamma;
+  uint32_t carry = 0;
+  for (uint32_t b0 = 0; b0 < L; b0 += 256 * 8) {
+    uint32_t v[8], sum = 0;
+    const uint32_t my = b0 + threadIdx.x * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = (my + k < L) ? __ldcg(cnt + my + k) : 0u;
+      sum += v[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan256(sum, sh8, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      ex += v[k];
+      if (my + k < L) cnt[my + k] = bucket_of_count(ex, alpha, gamma);
+    }
+    carry += tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// bucket id of a key under segment g: T[bin(x)]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bucket_id(const BinModel& bm, const uint32_t* __restrict__ T,
+                                              uint64_t x) {
+  return __ldg(T + bin_of(bm, x));
+}
+
+// warp-aggregated shared-memory histogram increment (match.any)
+__device__ __forceinline__ void hist_add(uint32_t* hist, uint32_t d, bool valid) {
+  const uint32_t key = valid ? d : 0xFFFFFFFFu;
+  const uint32_t peers = __match_any_sync(~0u, key);
+  const int leader = __ffs(peers) - 1;
+  if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+}
+
+// ---------------------------------------------------------------------------
+// k_hist1: per count-tile histogram of the high digit j >> b2
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
+                                               const uint32_t* tile_base, uint32_t tile_keys,
+                                               const uint64_t* __restrict__ keys, uint32_t kt,
+                                               const uint32_t* __restrict__ tpool,
+                                               uint32_t* cmat) {
+  extern __shared__ uint32_t hist[];
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
+  __shared__ BinModel bm;
+  const Seg& g = segs[s];
+  const uint32_t tt = t - tile_base[s];
+  const uint32_t D = 1u << g.b1, b2 = g.b2;
+  for (uint32_t d = threadIdx.x; d < D; d += 256) hist[d] = 0;
+  if (threadIdx.x == 0) bm = g.bm;
+  __syncthreads();
+  const uint64_t base = g.off + (uint64_t)tt * tile_keys;
+  const uint64_t end = min(g.off + g.n, base + tile_keys);
+  if (g.status != SEG_BUCKET) {
+    // not bucketed: keep the count matrix consistent (all keys in digit 0)
+    if (threadIdx.x == 0) hist[0] = (uint32_t)(end - base);
+  } else {
+    const uint32_t* T = tpool + g.T_off;
+    const uint32_t steps = (uint32_t)((end - base + 255) / 256);
+    uint32_t k = 0;
+    for (; k + 4 <= steps; k += 4) {
+      uint64_t i0 = base + (uint64_t)k * 256 + threadIdx.x;
+      uint64_t x[4];
+      bool v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint64_t i = i0 + u * 256;
+        v[u] = i < end;
+        x[u] = v[u] ? ld_nc(keys + i) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint32_t d = v[u] ? (bucket_id(bm, T, x[u]) >> b2) : 0u;
+        hist_add(hist, d, v[u]);
+      }
+    }
+    for (; k < steps; ++k) {
+      uint64_t i = base + (uint64_t)k * 256 + threadIdx.x;
+      bool v = i < end;
+      uint32_t d = v ? (bucket_id(bm, T, ld_nc(keys + i)) >> b2) : 0u;
+      hist_add(hist, d, v);
+    }
+  }
+  __syncthreads();
+  for (uint32_t d = threadIdx.x; d < D; d += 256) cmat[g.cbase1 + (uint64_t)d * g.tiles1 + tt] = hist[d];
+}
+
+// ---------------------------------------------------------------------------
+// k_scan: exclusive prefix sum of u32 data[0..n) in place, single pass with
+// decoupled look-back (Merrill & Garland 2016).  Tiles take their index from
+// an atomic counter, so every predecessor of a tile has started; each wait
+// on a predecessor's flag is bounded and gives up with STATUS_TIMEOUT.
+// Status word: [63:62] flag (0 none, 1 aggregate, 2 inclusive), [31:0] value.
+// `withhold` (test hook): that tile never publishes its aggregate.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void publish(uint64_t* w, uint64_t flag, uint32_t v) {
+  __threadfence();
+  atomicExch((unsigned long long*)w, (unsigned long long)((flag << 62) | v));
+}
+
+__global__ void __launch_bounds__(256) k_scan(uint32_t* data, uint64_t n, const uint64_t* n_dev,
+                                              uint64_t* sw, uint32_t* tile_counter,
+                                              uint32_t withhold, uint64_t spin_limit,
+                                              uint64_t* total_out, uint32_t* status) {
+  __shared__ uint32_t s_tile, s_prefix;
+  __shared__ uint32_t sh8[8];
+  __shared__ uint32_t buf[kScanTile];
+  if (n_dev) n = *n_dev;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * kScanTile;
+  if (base >= n) return;
+  const uint32_t cnt = (uint32_t)min((uint64_t)kScanTile, n - base);
+  for (uint32_t i = threadIdx.x; i < kScanTile; i += 256) buf[i] = i < cnt ? data[base + i] : 0u;
+  __syncthreads();
+  uint32_t v[16], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    v[k] = buf[threadIdx.x * 16 + k];
+    sum += v[k];
+  }
+  uint32_t tot;
+  uint32_t ex = block_excl_scan256(sum, sh8, &tot);
+  if (threadIdx.x == 0) {
+    uint32_t prefix = 0;
+    if (tile == 0) {
+      publish(&sw[0], 2, tot);
+    } else {
+      if (tile != withhold) publish(&sw[tile], 1, tot);
+      uint64_t spins = 0;
+      int64_t p = (int64_t)tile - 1;
+      while (p >= 0) {
+        uint64_t w = atomicAdd((unsigned long long*)&sw[p], 0ull);
+        uint32_t f = (uint32_t)(w >> 62);
+        if (f == 0) {
+          if (++spins > spin_limit) {
+            atomicOr(status, STATUS_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        prefix += (uint32_t)w;
+        if (f == 2) break;
+        --p;
+      }
+      if (tile != withhold) publish(&sw[tile], 2, prefix + tot);
+    }
+    s_prefix = prefix;
+    if (total_out && base + cnt == n) *total_out = (uint64_t)prefix + tot;
+  }
+  __syncthreads();
+  ex += s_prefix;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    buf[threadIdx.x * 16 + k] = ex;
+    ex += v[k];
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cnt; i += 256) data[base + i] = buf[i];
+}
+
+// ---------------------------------------------------------------------------
+// Stable scatter of one count tile (tile_n keys), by digit.  The tile is
+// staged in sub-tiles of kScatterSub keys: each warp ranks its contiguous
+// 512 keys in order (match.any + per-warp counters), the ranks are turned
+// into a digit-sorted order in shared memory, and the sub-tile is written
+// out with consecutive threads storing consecutive keys of each digit run.
+// s_gofs[d] holds the next global position of digit d for this tile.
+// ---------------------------------------------------------------------------
+constexpr int kItems = 16;  // keys per thread per sub-tile (256 threads)
+
+struct ScatterSmem {
+  uint16_t* wcnt;   // [8][D]
+  uint16_t* dbase;  // [D] sub-tile digit base
+  uint16_t* dtot;   // [D]
+  uint32_t* gofs;   // [D]
+  uint64_t* skey;   // [kScatterSub]
+  uint16_t* sdig;   // [kScatterSub]
+  uint16_t* saux;   // [kScatterSub] (pass 1)
+  uint32_t* sval;   // [kScatterSub] (pairs)
+};
+
+__host__ __device__ inline size_t scatter_smem_bytes(uint32_t D, bool pairs, bool aux) {
+  size_t b = (size_t)8 * D * 2 + (size_t)D * 2 * 2 + (size_t)D * 4;
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)kScatterSub * 8 + (size_t)kScatterSub * 2;
+  if (aux) b += (size_t)kScatterSub * 2;
+  if (pairs) b += (size_t)kScatterSub * 4;
+  return b + 64;
+}
+
+__device__ __forceinline__ ScatterSmem carve_scatter(uint8_t* p, uint32_t D, bool pairs, bool aux) {
+  ScatterSmem m;
+  m.wcnt = (uint16_t*)p;
+  p += (size_t)8 * D * 2;
+  m.dbase = (uint16_t*)p;
+  p += (size_t)D * 2;
+  m.dtot = (uint16_t*)p;
+  p += (size_t)D * 2;
+  m.gofs = (uint32_t*)p;
+  p += (size_t)D * 4;
+  p = (uint8_t*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  m.skey = (uint64_t*)p;
+  p += (size_t)kScatterSub * 8;
+  m.sdig = (uint16_t*)p;
+  p += (size_t)kScatterSub * 2;
+  m.saux = nullptr;
+  m.sval = nullptr;
+  if (aux) {
+    m.saux = (uint16_t*)p;
+    p += (size_t)kScatterSub * 2;
+  }
+  if (pairs) m.sval = (uint32_t*)p;
+  return m;
+}
+
+// PASS 1: digit = T[bin(x)] >> b2, carry = low b2 bits.  PASS 2: digit = carry.
+template <int PASS, bool PAIRS>
+__device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_off, uint32_t tile_n,
+                             const BinModel& bm, const uint32_t* __restrict__ T, uint32_t b2,
+                             const uint64_t* __restrict__ src, const uint32_t* __restrict__ src_v,
+                             const uint16_t* __restrict__ src_aux, uint64_t* __restrict__ dst,
+                             uint32_t* __restrict__ dst_v, uint16_t* __restrict__ dst_aux) {
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const uint32_t lmask = lanemask_lt();
+  const uint32_t low_mask = (1u << b2) - 1u;
+  for (uint32_t sub = 0; sub < tile_n; sub += kScatterSub) {
+    const uint32_t nsub = min(kScatterSub, tile_n - sub);
+    for (uint32_t i = tid; i < 8 * D; i += 256) sm.wcnt[i] = 0;
+    __syncthreads();
+    uint64_t key[kItems];
+    uint32_t dig[kItems], aux[kItems], rank[kItems], val[kItems];
+    const uint64_t g0 = tile_off + sub;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
+      const bool v = li < nsub;
+      key[k] = v ? ld_nc(src + g0 + li) : 0ull;
+      if (PAIRS) val[k] = v ? __ldg(src_v + g0 + li) : 0u;
+      if (PASS == 2) dig[k] = v ? (uint32_t)__ldg(src_aux + g0 + li) : 0u;
+    }
+    if (PASS == 1) {
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
+        uint32_t j = li < nsub ? bucket_id(bm, T, key[k]) : 0u;
+        dig[k] = j >> b2;
+        aux[k] = j & low_mask;
+      }
+    }
+    uint16_t* my = sm.wcnt + (size_t)w * D;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
+      const bool v = li < nsub;
+      const uint32_t peers = __match_any_sync(~0u, v ? dig[k] : 0xFFFFFFFFu);
+      uint32_t prior = v ? my[dig[k]] : 0u;
+      __syncwarp();
+      if (v && l == __ffs(peers) - 1) my[dig[k]] = (uint16_t)(prior + __popc(peers));
+      __syncwarp();
+      rank[k] = prior + __popc(peers & lmask);
+    }
+    __syncthreads();
+    // column prefix over warps, digit totals
+    for (uint32_t d = tid; d < D; d += 256) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) {
+        uint32_t c = sm.wcnt[(size_t)ww * D + d];
+        sm.wcnt[(size_t)ww * D + d] = (uint16_t)run;
+        run += c;
+      }
+      sm.dtot[d] = (uint16_t)run;
+    }
+    __syncthreads();
+    // exclusive scan of digit totals -> dbase (each thread a contiguous run)
+    {
+      __shared__ uint32_t sh8[8];
+      const uint32_t per = (D + 255) / 256;
+      const uint32_t d0 = min(D, (uint32_t)tid * per), d1 = min(D, d0 + per);
+      uint32_t sum = 0;
+      for (uint32_t d = d0; d < d1; ++d) sum += sm.dtot[d];
+      uint32_t tot;
+      uint32_t ex = block_excl_scan256(sum, sh8, &tot);
+      for (uint32_t d = d0; d < d1; ++d) {
+        sm.dbase[d] = (uint16_t)ex;
+        ex += sm.dtot[d];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
+      if (li < nsub) {
+        const uint32_t pos = sm.dbase[dig[k]] + my[dig[k]] + rank[k];
+        sm.skey[pos] = key[k];
+        sm.sdig[pos] = (uint16_t)dig[k];
+        if (PASS == 1) sm.saux[pos] = (uint16_t)aux[k];
+        if (PAIRS) sm.sval[pos] = val[k];
+      }
+    }
+    __syncthreads();
+    for (uint32_t pos = tid; pos < nsub; pos += 256) {
+      const uint32_t d = sm.sdig[pos];
+      const uint64_t o = (uint64_t)sm.gofs[d] + (pos - sm.dbase[d]);
+      dst[o] = sm.skey[pos];
+      if (PASS == 1) dst_aux[o] = sm.saux[pos];
+      if (PAIRS) dst_v[o] = sm.sval[pos];
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d < D; d += 256) sm.gofs[d] += sm.dtot[d];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_scatter1: pass 1 (src -> tmp), digit = high bits of the bucket id
+// ---------------------------------------------------------------------------
+template <bool PAIRS>
+__global__ void __launch_bounds__(256) k_scatter1(const Seg* segs, uint32_t S,
+                                                  const uint32_t* tile_base, uint32_t tile_keys,
+                                                  KeyBufs kb, const uint32_t* __restrict__ tpool,
+                                                  const uint32_t* __restrict__ cmat) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ BinModel bm;
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
+  const Seg& g = segs[s];
+  if (g.status != SEG_BUCKET) return;
+  const uint32_t tt = t - tile_base[s];
+  const uint32_t D = 1u << g.b1;
+  ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, true);
+  if (threadIdx.x == 0) bm = g.bm;
+  const uint32_t seg_base = cmat[g.cbase1];  // exclusive prefix at the segment's first entry
+  for (uint32_t d = threadIdx.x; d < D; d += 256)
+    sm.gofs[d] = (uint32_t)g.off + (cmat[g.cbase1 + (uint64_t)d * g.tiles1 + tt] - seg_base);
+  __syncthreads();
+  const uint64_t tile_off = g.off + (uint64_t)tt * tile_keys;
+  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, g.off + g.n - tile_off);
+  scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, bm, tpool + g.T_off, g.b2, kb.src, kb.src_v,
+                         nullptr, kb.tmp, kb.tmp_v, kb.tmp_aux);
+}
+
+// ---------------------------------------------------------------------------
+// k_groups: one thread per pass-1 group (segment s, high digit g): size,
+// offset and number of pass-2 count tiles.
+// ---------------------------------------------------------------------------
+__global__ void k_groups(const Seg* segs, uint32_t S, const uint64_t* group_base_dev,
+                         uint64_t n_groups, const uint32_t* cmat1, uint32_t tile_keys,
+                         Group* groups, uint32_t* g_tiles, uint32_t* g_centries) {
+  const uint64_t G = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (G >= n_groups) return;
+  const uint32_t s = upper_bound_dev(group_base_dev, S + 1, G) - 1;
+  const Seg& sg = segs[s];
+  const uint32_t g = (uint32_t)(G - sg.group_base);
+  Group gr;
+  gr.seg = s;
+  gr.pad = 0;
+  gr.n = 0;
+  gr.off = sg.off;
+  gr.key_prefix = 0;
+  gr.cbase = 0;
+  if (sg.status == SEG_BUCKET) {
+    const uint32_t D1 = 1u << sg.b1;
+    const uint32_t seg_base = cmat1[sg.cbase1];
+    const uint32_t a = cmat1[sg.cbase1 + (uint64_t)g * sg.tiles1] - seg_base;
+    const uint32_t b = (g + 1 < D1) ? cmat1[sg.cbase1 + (uint64_t)(g + 1) * sg.tiles1] - seg_base
+                                    : (uint32_t)sg.n;
+    gr.off = sg.off + a;
+    gr.n = b - a;
+  }
+  gr.tiles = (uint32_t)(((uint64_t)gr.n + tile_keys - 1) / tile_keys);
+  groups[G] = gr;
+  g_tiles[G] = gr.tiles;
+  g_centries[G] = gr.tiles << sg.b2;
+}
+
+// cbase of every group from the scanned entry counts
+__global__ void k_group_bases(Group* groups, uint64_t n_groups, const uint32_t* g_centries_scan) {
+  const uint64_t G = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (G >= n_groups) return;
+  groups[G].cbase = g_centries_scan[G];
+}
+
+// ---------------------------------------------------------------------------
+// k_hist2 / k_scatter2: pass 2 within each group, digit = carried low bits
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_hist2(const Group* groups, uint32_t n_groups,
+                                               const Seg* segs, const uint32_t* g_tile_scan,
+                                               const uint64_t* total_tiles, uint32_t tile_keys,
+                                               const uint16_t* __restrict__ aux,
+                                               uint32_t* cmat2) {
+  extern __shared__ uint32_t hist[];
+  const uint32_t t = blockIdx.x;
+  if (t >= *total_tiles) return;
+  const uint32_t G = upper_bound_dev(g_tile_scan, n_groups, t) - 1;
+  const Group gr = groups[G];
+  const uint32_t D = 1u << segs[gr.seg].b2;
+  const uint32_t tt = t - g_tile_scan[G];
+  for (uint32_t d = threadIdx.x; d < D; d += 256) hist[d] = 0;
+  __syncthreads();
+  const uint64_t base = gr.off + (uint64_t)tt * tile_keys;
+  const uint64_t end = min(gr.off + gr.n, base + tile_keys);
+  const uint32_t steps = (uint32_t)((end - base + 255) / 256);
+  for (uint32_t k = 0; k < steps; ++k) {
+    uint64_t i = base + (uint64_t)k * 256 + threadIdx.x;
+    bool v = i < end;
+    uint32_t d = v ? (uint32_t)__ldg(aux + i) : 0u;
+    hist_add(hist, d, v);
+  }
+  __syncthreads();
+  for (uint32_t d = threadIdx.x; d < D; d += 256)
+    cmat2[gr.cbase + (uint64_t)d * gr.tiles + tt] = hist[d];
+}
+
+template <bool PAIRS>
+__global__ void __launch_bounds__(256) k_scatter2(const Group* groups, uint32_t n_groups,
+                                                  const Seg* segs, const uint32_t* g_tile_scan,
+                                                  const uint64_t* total_tiles, uint32_t tile_keys,
+                                                  KeyBufs kb, const uint32_t* __restrict__ cmat2) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint32_t t = blockIdx.x;
+  if (t >= *total_tiles) return;
+  const uint32_t G = upper_bound_dev(g_tile_scan, n_groups, t) - 1;
+  const Group gr = groups[G];
+  const uint32_t D = 1u << segs[gr.seg].b2;
+  const uint32_t tt = t - g_tile_scan[G];
+  ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, false);
+  const uint32_t gbase = cmat2[gr.cbase];
+  for (uint32_t d = threadIdx.x; d < D; d += 256)
+    sm.gofs[d] = (uint32_t)gr.off + (cmat2[gr.cbase + (uint64_t)d * gr.tiles + tt] - gbase);
+  __syncthreads();
+  const uint64_t tile_off = gr.off + (uint64_t)tt * tile_keys;
+  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, gr.off + gr.n - tile_off);
+  BinModel dummy;
+  scatter_tile<2, PAIRS>(sm, D, tile_off, tile_n, dummy, nullptr, 0, kb.tmp, kb.tmp_v, kb.tmp_aux,
+                         kb.out, kb.out_v, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// k_buckets: Alg. 1's loop over buckets.  For bucket j of segment s:
+// |c_j| >= delta -> standard sort; |c_j| <= leaf_cap -> shared-memory kernel
+// (which itself applies n < tau); otherwise Learned-Sort at the next level.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
+  const uint32_t m = __ballot_sync(~0u, want);
+  if (!m) return 0;
+  const int leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
+  base = __shfl_sync(~0u, base, leader);
+  return base + __popc(m & lanemask_lt());
+}
+
+__global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, uint64_t n_buckets,
+                                                 const uint64_t* bucket_base, const Group* groups,
+                                                 const uint32_t* __restrict__ cmat2,
+                                                 uint32_t leaf_cap, WorkItem* leaf, WorkItem* next,
+                                                 FbItem* fb, LevelOut* lo, uint32_t max_items,
+                                                 uint32_t* status) {
+  const uint64_t B = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool v = B < n_buckets;
+  uint32_t s = 0, size = 0;
+  uint64_t off = 0;
+  if (v) {
+    s = upper_bound_dev(bucket_base, S + 1, B) - 1;
+    const Seg& sg = segs[s];
+    v = sg.status == SEG_BUCKET;
+    if (v) {
+      const uint32_t j = (uint32_t)(B - sg.bucket_base);
+      const uint32_t g = j >> sg.b2, d = j & ((1u << sg.b2) - 1u);
+      const Group gr = groups[sg.group_base + g];
+      if (gr.n == 0) {
+        v = false;
+      } else {
+        const uint32_t gbase = cmat2[gr.cbase];
+        const uint32_t a = cmat2[gr.cbase + (uint64_t)d * gr.tiles] - gbase;
+        const uint32_t b = (d + 1 < (1u << sg.b2))
+                               ? cmat2[gr.cbase + (uint64_t)(d + 1) * gr.tiles] - gbase
+                               : gr.n;
+        size = b - a;
+        off = gr.off + a;
+        v = size > 0;
+      }
+    }
+  }
+  const Seg* sg = v ? &segs[s] : nullptr;
+  const bool is_fb = v && size >= sg->delta && size > leaf_cap;
+  const bool is_leaf = v && !is_fb && size <= leaf_cap;
+  const bool is_next = v && !is_fb && !is_leaf;
+  // small failure-guard buckets are finished by the shared-memory kernel
+  // with the standard sort (flagged in depth's top bit)
+  const uint32_t i_leaf = warp_append(&lo->n_leaf, is_leaf);
+  const uint32_t i_next = warp_append(&lo->n_next, is_next);
+  const uint32_t i_fb = warp_append(&lo->n_fb, is_fb);
+  if (is_leaf || is_next) {
+    WorkItem it;
+    it.off = off;
+    it.start = sg->start + (off - sg->off);
+    it.seed = sg->seed;
+    it.n = size;
+    it.depth = sg->depth + 1;
+    if (is_leaf && size >= sg->delta) it.depth |= 0x80000000u;
+    if (is_leaf) {
+      if (i_leaf < max_items) leaf[i_leaf] = it;
+      else atomicOr(status, STATUS_INTERNAL);
+    } else {
+      if (i_next < max_items) next[i_next] = it;
+      else atomicOr(status, STATUS_INTERNAL);
+    }
+  }
+  if (is_fb) {
+    if (i_fb < max_items) {
+      fb[i_fb].off = off;
+      fb[i_fb].n = size;
+      atomicMax(&lo->max_fb_n, size);
+    } else {
+      atomicOr(status, STATUS_INTERNAL);
+    }
+  }
+}
+
+// Segments whose range is degenerate go to the standard sort as a whole.
+__global__ void k_seg_status_lists(const Seg* segs, uint32_t S, FbItem* fb, LevelOut* lo,
+                                   uint32_t max_items, uint32_t* status) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  if (segs[s].status != SEG_DEGEN) return;
+  uint32_t i = atomicAdd(&lo->n_fb, 1u);
+  if (i < max_items) {
+    fb[i].off = segs[s].off;
+    fb[i].n = segs[s].n;
+    atomicMax(&lo->max_fb_n, (uint32_t)segs[s].n);
+  } else {
+    atomicOr(status, STATUS_INTERNAL);
+  }
+}
+
+// Out-of-place level 0: segments that are not bucketed (one value, or a
+// degenerate range) are copied to the output as they are.
+__global__ void __launch_bounds__(256) k_copy_segs(const Seg* segs, uint32_t S,
+                                                   const uint32_t* range_base,
+                                                   const uint64_t* __restrict__ src, uint64_t* dst,
+                                                   const uint32_t* __restrict__ src_v,
+                                                   uint32_t* dst_v) {
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = upper_bound_dev(range_base, S + 1, t) - 1;
+  const Seg& g = segs[s];
+  if (g.status == SEG_BUCKET) return;
+  const uint64_t base = g.off + (uint64_t)(t - range_base[s]) * kRangeTile;
+  const uint64_t end = min(g.off + g.n, base + kRangeTile);
+  for (uint64_t i = base + threadIdx.x; i < end; i += 256) {
+    dst[i] = src[i];
+    if (dst_v) dst_v[i] = src_v[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline uint32_t cdiv(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* range_base,
+                         uint32_t n_tiles, const uint64_t* keys, bool check_nan) {
+  if (!n_tiles) return cudaSuccess;
+  k_range<<<n_tiles, 256, 0, c.stream>>>(segs, S, range_base, keys, c.kt, check_nan ? 1 : 0,
+                                         c.status);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S) {
+  if (!S) return cudaSuccess;
+  k_model<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, c.kt);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
+                          uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool, uint32_t* done,
+                          Policy) {
+  if (!n_ctas) return cudaSuccess;
+  k_sample<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt, tpool, done);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
+                         uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
+                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax) {
+  if (!n_tiles) return cudaSuccess;
+  k_hist1<<<n_tiles, 256, dmax * 4, c.stream>>>(segs, S, tile_base, tile_keys, keys, c.kt, tpool,
+                                                cmat);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const uint64_t* n_dev,
+                        uint64_t* status_words, uint32_t* tile_counter, uint32_t withhold,
+                        uint64_t spin_limit, uint64_t* total_out) {
+  if (!n) return cudaSuccess;
+  const uint32_t tiles = cdiv(n, kScanTile);
+  cudaError_t e = cudaMemsetAsync(status_words, 0, (size_t)tiles * 8, c.stream);
+  if (e) return e;
+  e = cudaMemsetAsync(tile_counter, 0, 4, c.stream);
+  if (e) return e;
+  k_scan<<<tiles, 256, 0, c.stream>>>(data, n, n_dev, status_words, tile_counter, withhold,
+                                      spin_limit, total_out, c.status);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_scatter1(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                            const uint32_t* tile_base, uint32_t n_tiles, uint32_t tile_keys,
+                            const KeyBufs& kb, const uint32_t* tpool, const uint32_t* cmat,
+                            uint32_t dmax) {
+  if (!n_tiles) return cudaSuccess;
+  const size_t sm = scatter_smem_bytes(dmax, c.pairs, true);
+  cudaError_t e;
+  if (c.pairs) {
+    if ((e = set_smem(k_scatter1<true>, sm))) return e;
+    k_scatter1<true><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb, tpool, cmat);
+    count_launch(c);
+  } else {
+    if ((e = set_smem(k_scatter1<false>, sm))) return e;
+    k_scatter1<false><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb, tpool,
+                                                       cmat);
+    count_launch(c);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_groups(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                          const uint64_t* group_base_dev, uint64_t n_groups, const uint32_t* cmat1,
+                          uint32_t tile_keys, Group* groups, uint32_t* g_tiles,
+                          uint32_t* g_centries) {
+  if (!n_groups) return cudaSuccess;
+  k_groups<<<cdiv(n_groups, 256), 256, 0, c.stream>>>(segs, S, group_base_dev, n_groups, cmat1,
+                                                      tile_keys, groups, g_tiles, g_centries);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_bases(const LaunchCfg& c, Group* groups, uint64_t n_groups,
+                               const uint32_t* g_centries_scan) {
+  if (!n_groups) return cudaSuccess;
+  k_group_bases<<<cdiv(n_groups, 256), 256, 0, c.stream>>>(groups, n_groups, g_centries_scan);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist2(const LaunchCfg& c, const Group* groups, uint32_t n_groups,
+                         const Seg* segs, const uint32_t* g_tile_scan, const uint64_t* total_tiles,
+                         uint32_t n_tiles_bound, uint32_t tile_keys, const uint16_t* aux,
+                         uint32_t* cmat2, uint32_t dmax) {
+  if (!n_tiles_bound) return cudaSuccess;
+  k_hist2<<<n_tiles_bound, 256, dmax * 4, c.stream>>>(groups, n_groups, segs, g_tile_scan,
+                                                      total_tiles, tile_keys, aux, cmat2);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter2(const LaunchCfg& c, const Group* groups, uint32_t n_groups,
+                            const Seg* segs, const uint32_t* g_tile_scan,
+                            const uint64_t* total_tiles, uint32_t n_tiles_bound,
+                            uint32_t tile_keys, const KeyBufs& kb, const uint32_t* cmat2,
+                            uint32_t dmax) {
+  if (!n_tiles_bound) return cudaSuccess;
+  const size_t sm = scatter_smem_bytes(dmax, c.pairs, false);
+  cudaError_t e;
+  if (c.pairs) {
+    if ((e = set_smem(k_scatter2<true>, sm))) return e;
+    k_scatter2<true><<<n_tiles_bound, 256, sm, c.stream>>>(groups, n_groups, segs, g_tile_scan,
+                                                           total_tiles, tile_keys, kb, cmat2);
+    count_launch(c);
+  } else {
+    if ((e = set_smem(k_scatter2<false>, sm))) return e;
+    k_scatter2<false><<<n_tiles_bound, 256, sm, c.stream>>>(groups, n_groups, segs, g_tile_scan,
+                                                            total_tiles, tile_keys, kb, cmat2);
+    count_launch(c);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint64_t n_buckets,
+                           const uint64_t* bucket_base, const Group* groups, const uint32_t* cmat2,
+                           uint32_t leaf_cap, WorkItem* leaf, WorkItem* next, FbItem* fb,
+                           LevelOut* lo, uint32_t max_items) {
+  if (!n_buckets) return cudaSuccess;
+  k_buckets<<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(segs, S, n_buckets, bucket_base, groups,
+                                                        cmat2, leaf_cap, leaf, next, fb, lo,
+                                                        max_items, c.status);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_status_lists(const LaunchCfg& c, const Seg* segs, uint32_t S, FbItem* fb,
+                                    LevelOut* lo, uint32_t max_items) {
+  if (!S) return cudaSuccess;
+  k_seg_status_lists<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, fb, lo, max_items, c.status);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_segs(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                             const uint32_t* range_base, uint32_t n_tiles, const uint64_t* src,
+                             uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v) {
+  if (!n_tiles) return cudaSuccess;
+  k_copy_segs<<<n_tiles, 256, 0, c.stream>>>(segs, S, range_base, src, dst, src_v, dst_v);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+}  // namespace pcf

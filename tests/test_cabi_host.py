@@ -1,0 +1,113 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every
+symbol the header declares, and its host-compiled copies of the device
+arithmetic (bin function, parameters, sampler) agree with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_07122_gb300 import build as pcf_build
+from paper_2405_07122_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    pcf_build.build()
+    from paper_2405_07122_gb300 import pcfsort
+    return pcfsort
+
+
+def test_exports_every_declared_symbol(P):
+    hdr = open(os.path.join(ROOT, "include", "pcfsort.h")).read()
+    declared = set(re.findall(r"\b(pcf_[a-z0-9_]+)\s*\(", hdr))
+    assert {"pcf_sort_keys", "pcf_sort_pairs", "pcf_sort_segmented"} <= declared
+    L = P.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert P.version() >= 100
+
+
+def test_status_strings(P):
+    L = P.lib()
+    for code in range(7):
+        assert L.pcf_status_string(code)
+
+
+@pytest.mark.parametrize("n", [2, 99, 100, 1000, 31622, 10**6, 10**8, 2**28, 2**32 - 1])
+def test_root_floor_matches_oracle(P, n):
+    for p, q in [(3, 4), (1, 2), (2, 3), (1, 4), (4, 4)]:
+        assert P.root_floor_host(n, p, q) == oracle.root_floor(n, p, q)
+
+
+def test_sample_index_matches_oracle(P):
+    for (seed, depth, start, n) in [(0, 0, 0, 10**6), (7, 2, 12345, 517), (2**63, 1, 9, 2**28)]:
+        ref = oracle.sample_indices(seed, depth, start, n, 64)
+        got = [P.sample_index_host(seed, depth, start, n, j) for j in range(64)]
+        assert np.array_equal(ref, np.array(got, dtype=np.uint64))
+
+
+def _models(seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for kind in ("normal", "uniform", "lognormal", "wide", "clustered", "dyadic", "u64", "u64wide",
+                 "u64small", "subnormal", "zerocross"):
+        if kind == "normal":
+            x = g.standard_normal(5000) * 10.0 ** g.uniform(-5, 5)
+        elif kind == "uniform":
+            x = g.random(5000)
+        elif kind == "lognormal":
+            x = g.lognormal(0, 2, 5000)
+        elif kind == "wide":
+            x = np.concatenate([g.standard_normal(2500) * 1e300, g.standard_normal(2500) * 1e-300])
+        elif kind == "clustered":
+            x = 1e10 + g.random(5000) * 1e-3
+        elif kind == "dyadic":
+            x = g.integers(-512, 512, 5000).astype(np.float64) / 8.0
+        elif kind == "u64":
+            x = g.integers(0, 2**40, 5000, dtype=np.uint64)
+        elif kind == "u64wide":
+            x = g.integers(0, 2**64 - 1, 5000, dtype=np.uint64, endpoint=True)
+        elif kind == "u64small":
+            x = g.integers(100, 130, 5000, dtype=np.uint64)
+        elif kind == "subnormal":
+            x = g.integers(0, 1000, 5000).astype(np.float64) * 5e-324
+        else:
+            x = np.concatenate([g.standard_normal(4990), [0.0, -0.0] * 5])
+        for beta in (1, 7, 181, 31622, 10**6, 2**21):
+            out.append((kind, x, beta))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bin_fast_path_equals_oracle(P, seed):
+    """The kernels' certified integer fast path + exact fallback gives the
+    oracle's binary64 bin for every key (same reading of Sec. 3.3)."""
+    for kind, x, beta in _models(seed):
+        kt = oracle.KEY_F64 if x.dtype == np.float64 else oracle.KEY_U64
+        bits = x.view(np.uint64) if kt == 0 else x
+        order = np.argsort(x, kind="stable")
+        lo = int(bits[order[0]])
+        hi = int(bits[order[-1]])
+        if kt == 0:  # total-order extremes (-0 < +0)
+            s = sorted(bits.tolist(), key=lambda b: (b ^ 0xFFFFFFFFFFFFFFFF) if b >> 63 else b | (1 << 63))
+            lo, hi = s[0], s[-1]
+        ref = oracle.bins(kt, lo, hi, beta, bits)
+        got = P.bins_host(kt, lo, hi, beta, bits)
+        assert (ref is None) == (got is None), kind
+        if ref is None:
+            continue
+        assert np.array_equal(ref.astype(np.uint32), got[0]), (kind, beta)
+
+
+def test_bin_fast_path_rarely_falls_back(P):
+    # on continuous data only the maximum key (which sits exactly at beta)
+    # needs the exact binary64 sequence
+    x = W.f64_keys("normal", 200000, 1)
+    bits = x.view(np.uint64)
+    lo, hi = int(bits[np.argmin(x)]), int(bits[np.argmax(x)])
+    _, fast = P.bins_host(0, lo, hi, 10**6, bits)
+    assert int((fast == 0).sum()) <= 2
