@@ -50,6 +50,21 @@ KERNEL_BYTES = {
 }
 
 
+def max_over_ranks(ms, dist, device=None):
+    """The job's time is the slowest rank's (each rank sorts its own replica)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(keys_per_rank_step, world, steps, ms):
+    """Whole-job throughput (Gkeys/s): every rank's keys over the slowest time."""
+    return keys_per_rank_step * world * steps / (ms / 1e3) / 1e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -163,9 +178,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N, help="keys per array (default 10^8)")
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "small", "zipf", "batched", "serve"],
+                    help="plain: the default 4 x 10^8 f64 line; the others are the "
+                         "secondary configurations")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     args = ap.parse_args()
-    global N
-    N = args.n
+    n = args.n
+    if args.workload != "plain" and args.impl == "ours":
+        return run_secondary(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -186,11 +207,11 @@ def main():
     __graft_entry__.build()
     from paper_2405_07122_gb300 import pcfsort
 
-    host_keys = [W.f64_keys(d, N, seed) for d, seed in DISTS]
+    host_keys = [W.f64_keys(d, n, seed) for d, seed in DISTS]
     ins = [torch.from_numpy(x).to(dev) for x in host_keys]
     outs = [torch.empty_like(t) for t in ins]
     ctx = pcfsort.Context(local)
-    ctx.reserve(N)
+    ctx.reserve(n)
     stream = torch.cuda.current_stream(dev)
 
     def step(timing=False):
@@ -232,14 +253,11 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
     ctx.enable_timing(False)
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    keys_per_step = 4 * N * world
-    value = keys_per_step * args.steps / (ms / 1e3) / 1e9
+    keys_per_step = 4 * n * world
+    value = job_value(4 * n, world, args.steps, ms)
 
     # end to end: pinned host buffer -> device -> sort -> host, per array
     pinned = [torch.from_numpy(x.copy()).pin_memory() for x in host_keys]
@@ -266,17 +284,18 @@ def main():
     dom_ms, dom_b = per_launch[dom]
     # keys processed by one launch of the dominant kernel: all N (global
     # passes; the leaf kernel sees every key of this workload too)
-    achieved = dom_b * N / (dom_ms / 1e3) / 1e9
+    achieved = dom_b * n / (dom_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_per_array": N, "arrays_per_step": 4,
+        "config": {"workload": WORKLOAD if n == N else WORKLOAD.replace("10^8", str(n)),
+                   "n_per_array": n, "arrays_per_step": 4,
                    "l2": "inputs larger than L2 (800 MB per array, L2 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "e2e": {"value": e2e, "unit": "Gkeys/s", "h2d_bytes_per_step": 8 * 4 * N,
-                "d2h_bytes_per_step": 8 * 4 * N},
+        "e2e": {"value": e2e, "unit": "Gkeys/s", "h2d_bytes_per_step": 8 * 4 * n,
+                "d2h_bytes_per_step": 8 * 4 * n},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -295,6 +314,131 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# secondary configurations (not the driver's default line)
+# ---------------------------------------------------------------------------
+def _device_sort_timer(torch):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    return timed
+
+
+def run_secondary(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_07122_gb300 import pcfsort
+    timed = _device_sort_timer(torch)
+    ctx = pcfsort.Context(0)
+    line = {"impl": "ours", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "unit": "Gkeys/s"}
+    if args.workload == "small":
+        x = torch.from_numpy(W.f64_keys("uniform", 10**6, 0)).cuda()
+        o = torch.empty_like(x)
+        ms = timed(lambda: ctx.sort_keys(x, o, key_type="f64"), max(args.steps, 10))
+        line.update(metric=METRIC, value=1e6 / ms / 1e6, ms_per_sort=ms, dtype="f64",
+                    config={"workload": "plain PCF sort, n = 10^6 float64 Uniform[0,1), keys only"})
+    elif args.workload == "zipf":
+        n = 2**28
+        k = W.zipf_u64(n, seed=5)
+        v = np.arange(n, dtype=np.uint32)
+        tk = torch.from_numpy(k.view(np.int64)).cuda()
+        tv = torch.from_numpy(v.view(np.int32)).cuda()
+        ko, vo = torch.empty_like(tk), torch.empty_like(tv)
+        ms = timed(lambda: ctx.sort_pairs(tk, tv, ko, vo, key_type="u64"), max(1, args.steps))
+        st = ctx.last_stats()
+        line.update(metric=METRIC, value=n / ms / 1e6, ms_per_sort=ms, dtype="u64",
+                    stats=st,
+                    config={"workload": "PCF sort, n = 2^28 uint64 keys, Zipf(1.2) over 10^7 "
+                                        "hashed values, uint32 payload = index (stable pairs)"})
+    elif args.workload == "batched":
+        keys, offs, _ = W.batched_f64(2048, seed=6)
+        total = int(offs[-1])
+        t = torch.from_numpy(keys).cuda()
+        o = torch.empty_like(t)
+        ms_b = timed(lambda: ctx.sort_segmented(t, offs, keys_out=o, key_type="f64"),
+                     max(1, args.steps))
+        batched_out = o.clone()
+
+        def plain():
+            for s in range(2048):
+                a, b = int(offs[s]), int(offs[s + 1])
+                ctx.sort_keys(t[a:b], o[a:b], key_type="f64", seed=s)
+        ms_p = timed(plain, 1)
+        assert bool((o == batched_out).all()), "batched and plain outputs differ"
+        line.update(metric=METRIC, value=total / ms_b / 1e6, ms_per_batch=ms_b,
+                    plain_value=total / ms_p / 1e6, plain_ms=ms_p, dtype="f64",
+                    config={"workload": "batched segmented sort: 2048 float64 arrays, lengths "
+                                        "floor(2^U(10,22)), distributions drawn from 5",
+                            "total_keys": total, "form": "one pcf_sort_segmented call vs "
+                                                          "2048 pcf_sort_keys calls"})
+    elif args.workload == "serve":
+        from paper_2405_07122_gb300 import serve
+        stream = W.request_stream(2000.0, args.duration, seed=7)
+        # device pools per (key type, distribution): requests take slices
+        pool_n = 1 << 26
+        pools = {}
+        g = torch.Generator(device="cuda")
+        g.manual_seed(7)
+        for d in W.DISTRIBUTIONS:
+            f = _torch_dist(torch, d, pool_n, g)
+            pools[("f64", d)] = f
+            pools[("u64", d)] = (torch.round(f * 4294967296.0).to(torch.int64) +
+                                 torch.tensor(-2**63, dtype=torch.int64, device="cuda"))
+        torch.cuda.synchronize()
+        srv = serve.SortServer(device=0, workers=4, mem_budget=64 << 30, batch_keys=1 << 27)
+        rng = np.random.Generator(np.random.PCG64(8))
+        handles = []
+        t0 = time.perf_counter()
+        for (ta, nreq, kt, dist, _seed) in stream:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            off = int(rng.integers(0, pool_n - nreq + 1))
+            handles.append(srv.submit(pools[(kt, dist)][off:off + nreq], kt))
+        for h in handles:
+            h.done.wait()
+        t1 = time.perf_counter()
+        srv.close()
+        keys_done = sum(h.n for h in handles)
+        lat = serve.latency_summary(handles)
+        line.update(metric="served sorted Gkeys/s (sustained)",
+                    value=keys_done / (t1 - t0) / 1e9, latency=lat, requests=len(handles),
+                    offered_gkeys_per_s=keys_done / args.duration / 1e9, dtype="f64|u64",
+                    config={"workload": "serving loop: Poisson arrivals 2000/s, sizes "
+                                        "floor(2^U(12,26)), f64 or u64, 5 distributions, "
+                                        "64 GB admission budget, 4 streams",
+                            "duration_s": args.duration})
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _torch_dist(torch, dist, n, g):
+    if dist == "uniform":
+        return torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    if dist == "normal":
+        return torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    if dist == "lognormal":
+        return torch.exp(torch.randn(n, dtype=torch.float64, device="cuda", generator=g))
+    if dist == "exponential":
+        return -torch.log1p(-torch.rand(n, dtype=torch.float64, device="cuda", generator=g))
+    means = torch.rand(5, dtype=torch.float64, device="cuda", generator=g) * 200 - 100
+    sds = torch.rand(5, dtype=torch.float64, device="cuda", generator=g) * 9.9 + 0.1
+    comp = torch.randint(0, 5, (n,), device="cuda", generator=g)
+    return means[comp] + sds[comp] * torch.randn(n, dtype=torch.float64, device="cuda",
+                                                  generator=g)
 
 
 if __name__ == "__main__":

@@ -63,7 +63,7 @@ typedef enum {
  * gamma = ...(c_num), delta = ...(d_num), recomputed for every (sub)array
  * from its own n; tau is the small-input threshold.  Supported: den in 1..4,
  * 1 <= a_num, b_num, c_num <= den, 1 <= d_num < den (0 < d < 1, as
- * Lemma nlogn requires), tau >= 2.  Default: {3,3,3,3,4,100}. */
+ * Lemma nlogn requires), 16 <= tau <= 65535.  Default: {3,3,3,3,4,100}. */
 typedef struct {
   uint32_t a_num, b_num, c_num, d_num, den;
   uint64_t tau;
@@ -71,13 +71,16 @@ typedef struct {
 
 /* Implementation knobs.  They change speed only, never the result or the
  * model: max_digit_bits = widest bucket-id digit scattered per global pass
- * (4..11); tile_log2 = log2 of keys per scatter tile (11..13); leaf_cap =
- * the largest bucket finished inside shared memory by one warp (64..1024,
- * power of two).  Zero fields keep the current value. */
+ * (4..11); tile_log2 = log2 of keys per count tile of a global pass (12..18);
+ * leaf_cap = the largest bucket finished on chip (64..1024, power of two);
+ * onchip_window = keys of the windows in which on-chip buckets are grouped
+ * per thread block (1024..8192, power of two).  Zero fields keep the
+ * current value. */
 typedef struct {
   uint32_t max_digit_bits;
   uint32_t tile_log2;
   uint32_t leaf_cap;
+  uint32_t onchip_window;
 } pcf_tuning;
 
 typedef struct pcf_ctx pcf_ctx;

@@ -116,25 +116,28 @@ PCF_HD Params params_of(const Policy& P, uint64_t n) {
 // GB300 runs binary64 at ~2 operations/clock/SM, so the kernels evaluate it
 // with a certified integer fast path and fall back to the exact binary64
 // sequence only when the fast value cannot decide the floor:
-//   X(x)  = trunc(x / 2^G)        64-bit fixed point, G chosen so |X| < 2^62
-//   D     = X(x) - X(lo)          in [0, X(hi) - X(lo)]  (trunc is monotone)
-//   V     = hi64((D << w) * Sig)  Sig = 53-bit significand of s, << 11
+//   X(y)  = trunc(y / 2^H), a fixed point of the key on a grid 2^H fine
+//           enough that X(hi) - X(lo) lies in [2^61, 2^62); X is computed
+//           modulo 2^64 with one shift of the significand, and since trunc
+//           is monotone, Dn = X(x) - X(lo) is the exact integer difference
+//           in [0, 2^62 + 2) for every key of the range
+//   V     = hi64(Dn * Sig)   Sig = 53-bit significand of s shifted left 11
 //   V / 2^F approximates v = (x - lo) s.
-// Truncation of X moves V by at most 8 units (it only happens when the range
-// spans zero, and then w <= 2), hi64 by 1 unit, and the two binary64 roundings
-// move the exact result P by at most v 2^-52 (1 + 2^-50) <= (beta+1) 2^(F-52)
-// units.  With Eu bounding all three, floor(P) = floor(V / 2^F) whenever
-// [V - Eu, V + Eu] holds no multiple of 2^F.
+// Truncation moves Dn by at most 2 (so V by at most 2), hi64 drops less
+// than 1, and the two binary64 roundings move the exact result P by at most
+// v 2^-52 (1 + 2^-50) <= (beta+1) 2^(F-52) units.  With Eu above all three,
+// floor(P) = floor(V / 2^F) whenever [V - Eu, V + Eu] holds no multiple of
+// 2^F; otherwise the exact sequence runs.
 // --------------------------------------------------------------------------
 struct BinModel {
   uint64_t lo_bits;  // raw bits of lo
   double lo_d;       // lo as binary64 (f64 keys)
   double s;          // beta / range
-  int64_t LO;        // X(lo) (f64 keys)
+  uint64_t LOw;      // X(lo) modulo 2^64 (f64) / lo (u64)
   uint64_t sig;      // significand of s << 11, in [2^63, 2^64)
   uint64_t eu;       // error bound in V units
-  int32_t C;         // f64: X(x) uses shift max(e,1) - C
-  int32_t w;         // left shift of D (-1: right shift by one, u64 only)
+  int32_t C;         // f64: X(y) shifts the significand by max(e,1) - C
+  int32_t w;         // u64: Dn = (x - lo) << w (w < 0: >> -w)
   int32_t F;         // fractional bits of V
   uint32_t beta;
   uint32_t kt;
@@ -198,13 +201,18 @@ PCF_HD bool finite_f64(double d) {
   return (f64_bits(d) & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
 }
 
-// Fixed point trunc(x / 2^G) with G = C - 1075, as a signed integer.
-PCF_HD int64_t fixed_of(uint64_t bits, int32_t C) {
-  uint32_t e = (uint32_t)(bits >> 52) & 0x7FFu;
-  uint64_t m = (bits & 0x000FFFFFFFFFFFFFull) | (e ? 0x0010000000000000ull : 0ull);
-  int32_t sh = (int32_t)(e ? e : 1u) - C;
-  uint64_t mag = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
-  return (bits >> 63) ? -(int64_t)mag : (int64_t)mag;
+// X(y) = sign(y) trunc(|y| / 2^(C - 1075)) modulo 2^64.
+PCF_HD uint64_t fixed_mod(uint64_t bits, int32_t C) {
+  const uint32_t e = (uint32_t)(bits >> 52) & 0x7FFu;
+  const uint64_t m = (bits & 0x000FFFFFFFFFFFFFull) | (e ? 0x0010000000000000ull : 0ull);
+  const int32_t sh = (int32_t)(e ? e : 1u) - C;
+  const uint64_t mag = sh >= 0 ? (sh < 64 ? (m << sh) : 0ull) : (sh > -64 ? (m >> (-sh)) : 0ull);
+  return (bits >> 63) ? (0ull - mag) : mag;
+}
+
+// v >> F as 32 bits (the quotient never exceeds beta + 1 < 2^32)
+PCF_HD uint32_t shr_F(uint64_t v, int32_t F) {
+  return F >= 32 ? ((uint32_t)(v >> 32) >> (F - 32)) : (uint32_t)(v >> F);
 }
 
 // Builds the model of the range [lo, hi] with beta bins.  Returns 0, or 1
@@ -217,49 +225,62 @@ PCF_HD int make_bin_model(uint32_t kt, uint64_t lo_bits, uint64_t hi_bits, uint3
   M->lo_bits = lo_bits;
   M->pad = 0;
   double r;
-  uint64_t range;
-  int32_t G;
+  int32_t H;  // grid exponent: X(y) ~ y / 2^H
   if (kt == KEY_F64) {
     M->lo_d = as_f64(lo_bits);
     r = dsub(as_f64(hi_bits), M->lo_d);
     if (!(r > 0.0) || !finite_f64(r)) return 1;
+    // coarse grid 2^G with |X| < 2^62, then refine so the range has 62 bits
     uint32_t elo = (uint32_t)(lo_bits >> 52) & 0x7FFu, ehi = (uint32_t)(hi_bits >> 52) & 0x7FFu;
     uint32_t em = elo > ehi ? elo : ehi;
     if (em < 1) em = 1;
-    G = (int32_t)em - 1075 - 9;
-    M->C = 1075 + G;
-    M->LO = fixed_of(lo_bits, M->C);
-    range = (uint64_t)(fixed_of(hi_bits, M->C) - M->LO);
+    const int32_t G = (int32_t)em - 1075 - 9;
+    const uint64_t coarse = fixed_mod(hi_bits, 1075 + G) - fixed_mod(lo_bits, 1075 + G);
+    if (coarse == 0) return 1;  // cannot happen for distinct finite keys
+    const int32_t w = 61 - floor_log2_u64(coarse);
+    H = G - w;
+    M->C = 1075 + H;
+    M->w = 0;
+    M->LOw = fixed_mod(lo_bits, M->C);
   } else {
     M->lo_d = 0.0;
-    range = hi_bits - lo_bits;
+    const uint64_t range = hi_bits - lo_bits;
     r = u64_to_f64(range);
-    G = 0;
+    if (range == 0) return 1;
+    M->w = 61 - floor_log2_u64(range);
+    H = -M->w;
     M->C = 0;
-    M->LO = (int64_t)lo_bits;
+    M->LOw = lo_bits;
   }
   M->s = ddiv((double)beta, r);
   if (!finite_f64(M->s) || !(M->s >= 2.2250738585072014e-308)) return 1;
-  if (range == 0) return 1;  // cannot happen for distinct finite keys
-  M->w = 62 - floor_log2_u64(range);
-  uint64_t sb = f64_bits(M->s);
-  int32_t es = (int32_t)((sb >> 52) & 0x7FFu) - 1075;
+  const uint64_t sb = f64_bits(M->s);
+  const int32_t es = (int32_t)((sb >> 52) & 0x7FFu) - 1075;
   M->sig = ((sb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;
-  M->F = M->w - G - es - 53;
+  // v = Dn 2^H s = Dn Sig 2^(H + es - 11), V = Dn Sig 2^-64  =>  F = -(H + es + 53)
+  M->F = -(H + es + 53);
   if (M->F < 1 || M->F > 63) return 1;  // unreachable for beta < 2^32
   // (beta + 1) 2^(F-52) + slack, rounded up
   double e2 = (double)(beta + 1ull);
-  int32_t ex = M->F - 52;
+  const int32_t ex = M->F - 52;
   e2 = ex >= 0 ? e2 * (double)(1ull << ex) : e2 / (double)(1ull << (-ex));
-  M->eu = (uint64_t)e2 + 17ull;
+  M->eu = (uint64_t)e2 + 8ull;
   return 0;
 }
 
+// Dn of a key (see above)
+PCF_HD uint64_t bin_dn(const BinModel& M, uint64_t xbits) {
+  if (M.kt == KEY_F64) return fixed_mod(xbits, M.C) - M.LOw;
+  const uint64_t d = xbits - M.LOw;
+  return M.w >= 0 ? (d << M.w) : (d >> (-M.w));
+}
+
 // Exact binary64 evaluation (the reading above, op by op).
-PCF_HD uint32_t bin_exact(const BinModel& M, uint64_t xbits) {
-  double d = M.kt == KEY_F64 ? dsub(as_f64(xbits), M.lo_d) : u64_to_f64(xbits - M.lo_bits);
-  double p = dmul(d, M.s);
-  if (!(p < (double)M.beta)) return M.beta;
+PCF_HD uint32_t bin_exact_v(uint32_t kt, uint64_t lo_bits, double lo_d, double s, uint32_t beta,
+                            uint64_t xbits) {
+  double d = kt == KEY_F64 ? dsub(as_f64(xbits), lo_d) : u64_to_f64(xbits - lo_bits);
+  double p = dmul(d, s);
+  if (!(p < (double)beta)) return beta;
   if (!(p > 0.0)) return 0u;
 #ifdef __CUDA_ARCH__
   return __double2uint_rd(p);
@@ -267,26 +288,56 @@ PCF_HD uint32_t bin_exact(const BinModel& M, uint64_t xbits) {
   return (uint32_t)__builtin_floor(p);
 #endif
 }
+PCF_HD uint32_t bin_exact(const BinModel& M, uint64_t xbits) {
+  return bin_exact_v(M.kt, M.lo_bits, M.lo_d, M.s, M.beta, xbits);
+}
 
-// Certified fast path; *amb is set when the exact path was needed.
+#ifdef __CUDA_ARCH__
+// Out of line, so that the binary64 instructions run only in the lanes that
+// need them (GB300 issues binary64 at 1/64 of the fp32 rate; a predicated
+// inline copy would cost every key four of them).
+__device__ __noinline__ uint32_t bin_exact_call(uint32_t kt, uint64_t lo_bits, double lo_d,
+                                                double s, uint32_t beta, uint64_t xbits) {
+  return bin_exact_v(kt, lo_bits, lo_d, s, beta, xbits);
+}
+#endif
+
+// Certified fast path, exact binary64 sequence when it cannot decide.
 PCF_HD uint32_t bin_of(const BinModel& M, uint64_t xbits) {
-  uint64_t D = M.kt == KEY_F64 ? (uint64_t)(fixed_of(xbits, M.C) - M.LO) : (xbits - M.lo_bits);
-  uint64_t Dn = M.w >= 0 ? (D << M.w) : (D >> 1);
-  uint64_t V = mulhi64(Dn, M.sig);
-  uint64_t vlo = V > M.eu ? V - M.eu : 0ull;
-  uint64_t klo = vlo >> M.F, khi = (V + M.eu) >> M.F;
+  const uint64_t V = mulhi64(bin_dn(M, xbits), M.sig);
+  const uint32_t klo = shr_F(V > M.eu ? V - M.eu : 0ull, M.F), khi = shr_F(V + M.eu, M.F);
   if (klo >= M.beta) return M.beta;
-  if (klo == khi) return (uint32_t)klo;
+  if (klo == khi) return klo;
+#ifdef __CUDA_ARCH__
+  return bin_exact_call(M.kt, M.lo_bits, M.lo_d, M.s, M.beta, xbits);
+#else
   return bin_exact(M, xbits);
+#endif
+}
+
+// Fast path only: the bin when *amb stays false; callers that evaluate many
+// keys collect the undecided ones and run bin_exact afterwards, keeping the
+// out-of-line call out of their load/compute loops.
+PCF_HD uint32_t bin_fast(const BinModel& M, uint64_t xbits, bool& amb) {
+  const uint64_t V = mulhi64(bin_dn(M, xbits), M.sig);
+  const uint32_t klo = shr_F(V > M.eu ? V - M.eu : 0ull, M.F), khi = shr_F(V + M.eu, M.F);
+  amb = klo < M.beta && klo != khi;
+  return klo >= M.beta ? M.beta : klo;
+}
+
+// Exact bin of a key (out of line on the device)
+PCF_HD uint32_t bin_exact_of(const BinModel& M, uint64_t xbits) {
+#ifdef __CUDA_ARCH__
+  return bin_exact_call(M.kt, M.lo_bits, M.lo_d, M.s, M.beta, xbits);
+#else
+  return bin_exact(M, xbits);
+#endif
 }
 
 // Whether the fast path decides this key (for tests and counters).
 PCF_HD bool bin_fast_decides(const BinModel& M, uint64_t xbits) {
-  uint64_t D = M.kt == KEY_F64 ? (uint64_t)(fixed_of(xbits, M.C) - M.LO) : (xbits - M.lo_bits);
-  uint64_t Dn = M.w >= 0 ? (D << M.w) : (D >> 1);
-  uint64_t V = mulhi64(Dn, M.sig);
-  uint64_t vlo = V > M.eu ? V - M.eu : 0ull;
-  uint64_t klo = vlo >> M.F, khi = (V + M.eu) >> M.F;
+  const uint64_t V = mulhi64(bin_dn(M, xbits), M.sig);
+  const uint32_t klo = shr_F(V > M.eu ? V - M.eu : 0ull, M.F), khi = shr_F(V + M.eu, M.F);
   return klo >= M.beta || klo == khi;
 }
 

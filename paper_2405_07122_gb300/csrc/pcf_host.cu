@@ -39,11 +39,36 @@ struct HostBuf {  // pinned staging
 
 }  // namespace
 
+namespace {
+// alpha..delta of a (sub)array, cached for n < 2^16 (levels can hold tens of
+// thousands of segments)
+struct ParamCache {
+  uint64_t key = ~0ull;
+  std::vector<Params> small;
+  const Params& get(const Policy& P, uint64_t n, Params& tmp) {
+    const uint64_t k = ((uint64_t)P.a_num << 32) ^ ((uint64_t)P.b_num << 24) ^
+                       ((uint64_t)P.c_num << 16) ^ ((uint64_t)P.d_num << 8) ^ P.den;
+    if (k != key) {
+      key = k;
+      small.assign(1u << 16, Params{0, 0, 0, 0});
+    }
+    if (n < (1u << 16)) {
+      Params& c = small[n];
+      if (c.alpha == 0) c = params_of(P, n);
+      return c;
+    }
+    tmp = params_of(P, n);
+    return tmp;
+  }
+};
+
+}  // namespace
+
 struct pcf_ctx {
   int device = 0;
   int num_sms = 0;
   Policy policy{3, 3, 3, 3, 4, 0, 100};
-  pcf_tuning tuning{10, 15, 512};
+  pcf_tuning tuning{11, 15, 512, 2048};
   std::string last_err;
   pcf_call_stats stats{};
   bool timing = false;
@@ -53,6 +78,9 @@ struct pcf_ctx {
   DevBuf segs, bases, tpool, done, cmat1, cmat2, sw, groups, gtiles, gcent, gtot;
   DevBuf leaf, next, fb, lout, status, misc, fb_items, fb_bases, fb_lohi, small_items;
   HostBuf h_stage, h_lout, h_status, h_items;
+  DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
+  uint64_t ptab_key = 0;  // policy/cap the table was built for
+  ParamCache pcache;
 };
 
 namespace {
@@ -117,7 +145,7 @@ bool policy_ok(const Policy& P) {
   if (P.a_num < 1 || P.a_num > P.den || P.b_num < 1 || P.b_num > P.den) return false;
   if (P.c_num < 1 || P.c_num > P.den) return false;
   if (P.d_num < 1 || P.d_num >= P.den) return false;
-  if (P.tau < 2 || P.tau > 65535) return false;
+  if (P.tau < 16 || P.tau > 65535) return false;
   return true;
 }
 
@@ -138,11 +166,17 @@ struct Plan {
   std::vector<uint64_t> group_base, bucket_base;
   uint64_t tpool = 0, cmat1 = 0, cmat2_bound = 0, tiles2_bound = 0, n_groups = 0, n_buckets = 0;
   uint32_t dmax1 = 1, dmax2 = 1;
+  bool two_pass = false;
 };
 
-void plan_level(const Policy& P, const pcf_tuning& tu, const std::vector<InSeg>& in, Plan& pl) {
+// Plans one global level.  When every segment's bucket id fits one digit
+// (<= max_digit_bits) the level scatters once; otherwise twice, and
+// segments with a one-digit id copy themselves in the second pass.
+void plan_level(const Policy& P, const pcf_tuning& tu, ParamCache& pc,
+                const std::vector<InSeg>& in, Plan& pl) {
   const uint32_t tile_keys = 1u << tu.tile_log2;
   const uint32_t S = (uint32_t)in.size();
+  const uint32_t dbits = std::min(tu.max_digit_bits, kMaxDigitBits);
   pl.segs.resize(S);
   pl.range_base.assign(S + 1, 0);
   pl.k1_base.assign(S + 1, 0);
@@ -151,6 +185,13 @@ void plan_level(const Policy& P, const pcf_tuning& tu, const std::vector<InSeg>&
   pl.bucket_base.assign(S + 1, 0);
   pl.tpool = pl.cmat1 = pl.cmat2_bound = pl.tiles2_bound = 0;
   pl.dmax1 = pl.dmax2 = 1;
+  pl.two_pass = false;
+  std::vector<Params> prs(S);
+  for (uint32_t s = 0; s < S; ++s) {
+    Params tmp;
+    prs[s] = pc.get(P, in[s].n, tmp);
+    if (std::max(1u, bits_of(prs[s].gamma)) > dbits) pl.two_pass = true;
+  }
   for (uint32_t s = 0; s < S; ++s) {
     Seg g;
     memset(&g, 0, sizeof g);
@@ -159,15 +200,19 @@ void plan_level(const Policy& P, const pcf_tuning& tu, const std::vector<InSeg>&
     g.start = in[s].start;
     g.seed = in[s].seed;
     g.depth = in[s].depth;
-    Params pr = params_of(P, g.n);
+    const Params& pr = prs[s];
     g.alpha = pr.alpha;
     g.beta = pr.beta;
     g.gamma = pr.gamma;
     g.delta = pr.delta;
     const uint32_t jb = std::max(1u, bits_of(pr.gamma));
-    uint32_t b1 = (jb + 1) / 2;
-    b1 = std::min(b1, std::min(tu.max_digit_bits, kMaxDigitBits));
-    if (jb - b1 > kMaxDigitBits) b1 = jb - kMaxDigitBits;
+    // two digits: make the low digit as wide as allowed, so that pass-2
+    // groups (n / 2^b1 keys each) stay large
+    uint32_t b1 = jb;
+    if (jb > dbits) {
+      const uint32_t b2 = std::min(dbits, jb - 1);
+      b1 = std::min(jb - b2, kMaxDigitBits);
+    }
     g.b1 = b1;
     g.b2 = jb - b1;
     g.T_off = pl.tpool;
@@ -184,9 +229,10 @@ void plan_level(const Policy& P, const pcf_tuning& tu, const std::vector<InSeg>&
     pl.range_base[s + 1] = pl.range_base[s] + (uint32_t)((g.n + kRangeTile - 1) / kRangeTile);
     pl.k1_base[s + 1] = pl.k1_base[s] + (pr.alpha + kSamplesPerCta - 1) / kSamplesPerCta;
     pl.tile1_base[s + 1] = pl.tile1_base[s] + g.tiles1;
-    pl.group_base[s + 1] = pl.group_base[s] + (1ull << g.b1);
+    // one group per pass-1 digit; a one-digit id copies the segment as one group
+    pl.group_base[s + 1] = pl.group_base[s] + (g.b2 ? (1ull << g.b1) : 1ull);
     pl.bucket_base[s + 1] = pl.bucket_base[s] + (uint64_t)pr.gamma + 1;
-    const uint64_t t2 = g.tiles1 + (1ull << g.b1);
+    const uint64_t t2 = g.tiles1 + (g.b2 ? (1ull << g.b1) : 1ull);
     pl.tiles2_bound += t2;
     pl.cmat2_bound += t2 << g.b2;
     pl.dmax1 = std::max(pl.dmax1, 1u << g.b1);
@@ -223,6 +269,34 @@ LeafGeom leaf_geom(pcf_ctx* ctx, bool pairs) {
   return g;
 }
 
+// alpha, beta, gamma, delta of every on-chip size n <= cap, so the leaf
+// kernel looks them up instead of evaluating floor(n^{p/q}) per bucket.
+cudaError_t ensure_ptab(pcf_ctx* ctx, cudaStream_t st) {
+  const Policy& P = ctx->policy;
+  const uint32_t cap = ctx->tuning.leaf_cap;
+  const uint64_t key = ((uint64_t)P.a_num << 56) ^ ((uint64_t)P.b_num << 48) ^
+                       ((uint64_t)P.c_num << 40) ^ ((uint64_t)P.d_num << 32) ^
+                       ((uint64_t)P.den << 24) ^ ((uint64_t)cap << 8) ^ (P.tau & 0xFF) ^
+                       (P.tau << 12);
+  if (ctx->ptab_key == key && ctx->ptab.p) return cudaSuccess;
+  std::vector<uint16_t> t((size_t)(cap + 1) * 4, 0);
+  for (uint32_t n = 2; n <= cap; ++n) {
+    Params pr = params_of(P, n);
+    t[n * 4 + 0] = (uint16_t)pr.alpha;
+    t[n * 4 + 1] = (uint16_t)pr.beta;
+    t[n * 4 + 2] = (uint16_t)pr.gamma;
+    t[n * 4 + 3] = (uint16_t)pr.delta;
+  }
+  cudaError_t e = ensure(ctx->ptab, t.size() * 2);
+  if (e) return e;
+  e = cudaMemcpyAsync(ctx->ptab.p, t.data(), t.size() * 2, cudaMemcpyHostToDevice, st);
+  if (e) return e;
+  e = cudaStreamSynchronize(st);
+  if (e) return e;
+  ctx->ptab_key = key;
+  return cudaSuccess;
+}
+
 struct Timer {
   pcf_ctx* ctx;
   cudaStream_t st;
@@ -252,6 +326,7 @@ struct Timer {
 
 constexpr uint64_t kSpinLimit = 1ull << 24;
 
+
 // The whole sort of a batch of arrays.  Level-0 segments are the caller's
 // arrays; keys flow src -> tmp (pass 1) -> out (pass 2); leaf buckets are
 // finished in place in out; fallback buckets are merge-sorted in out.
@@ -280,6 +355,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   const uint32_t tile_keys = 1u << ctx->tuning.tile_log2;
   const uint32_t cap = ctx->tuning.leaf_cap;
   const LeafGeom lg = leaf_geom(ctx, pairs);
+  CK(ensure_ptab(ctx, st));
+  const uint16_t* ptab = as<uint16_t>(ctx->ptab);
   Timer tm(ctx, st);
   tm.mark(-1);
 
@@ -296,7 +373,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     std::vector<InSeg> all = small;
     if (!all.empty()) {
       Plan pl;
-      plan_level(ctx->policy, ctx->tuning, all, pl);
+      plan_level(ctx->policy, ctx->tuning, ctx->pcache, all, pl);
       const uint32_t S = (uint32_t)all.size();
       size_t need = S * sizeof(Seg) + (S + 1) * 4;
       CK(ensure_host(ctx->h_stage, need));
@@ -312,30 +389,29 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
 
   // ---- level 0 of the small arrays: straight to the shared-memory kernel,
   // launched once the NaN check of every key has passed
+  const uint32_t window = ctx->tuning.onchip_window;
   auto launch_small = [&]() -> pcf_status {
     if (small.empty()) return PCF_OK;
     const uint32_t S = (uint32_t)small.size();
-    std::vector<WorkItem> items(S);
+    std::vector<BRec> recs(S);
     for (uint32_t i = 0; i < S; ++i) {
-      items[i].off = small[i].off;
-      items[i].start = small[i].start;
-      items[i].seed = small[i].seed;
-      items[i].n = (uint32_t)small[i].n;
-      items[i].depth = small[i].depth;
+      recs[i].off = (uint32_t)small[i].off;
+      recs[i].n = (uint32_t)small[i].n;
+      recs[i].kind = BK_LEAF | (small[i].n < ctx->policy.tau ? BK_STD : 0u);
+      recs[i].depth = small[i].depth;
+      recs[i].start = small[i].start;
+      recs[i].seed = small[i].seed;
     }
-    const size_t need = S * sizeof(WorkItem) + 64;
+    const size_t need = S * sizeof(BRec) + 64;
     CK(ensure(ctx->small_items, need));
     CK(ensure_host(ctx->h_items, need));
-    memcpy(ctx->h_items.p, items.data(), S * sizeof(WorkItem));
-    uint32_t* cnt = (uint32_t*)((char*)ctx->h_items.p + S * sizeof(WorkItem));
-    cnt[0] = S;
-    cnt[1] = 0;
-    CK(cudaMemcpyAsync(ctx->small_items.p, ctx->h_items.p, S * sizeof(WorkItem) + 8,
+    memcpy(ctx->h_items.p, recs.data(), S * sizeof(BRec));
+    CK(cudaMemcpyAsync(ctx->small_items.p, ctx->h_items.p, S * sizeof(BRec),
                        cudaMemcpyHostToDevice, st));
-    const uint32_t* dcnt = (const uint32_t*)((char*)ctx->small_items.p + S * sizeof(WorkItem));
-    CK(launch_leaf(lc, as<WorkItem>(ctx->small_items), dcnt, (uint32_t*)dcnt + 1, in_k, out_k,
-                   in_v, out_v, ctx->policy, cap, lg.tmax, lg.gmax, lg.warps,
-                   std::min<uint32_t>(lg.grid, (S + lg.warps - 1) / lg.warps)));
+    const uint64_t wb = small.front().off, span = small.back().off + small.back().n - wb;
+    CK(ensure(ctx->gtot, ((span + window - 1) / window + 2) * 4));
+    CK(launch_chunk(lc, as<BRec>(ctx->small_items), S, wb, span, window, cap, in_k, in_v, out_k,
+                    out_v, ctx->policy, ptab, as<uint32_t>(ctx->gtot)));
     ctx->stats.leaf_buckets += S;
     return PCF_OK;
   };
@@ -351,17 +427,32 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   }
 
   // ---- global levels
+  // Each level reads `src`; pass 1 writes P1 (the other buffer), pass 2 (if
+  // any) writes P2; X is where the level's buckets end.  On-chip buckets go
+  // X -> out, next-level (sub)arrays stay in X, fallback buckets are sorted
+  // from X into out.
   std::vector<InSeg> level = big;
+  CK(ensure(ctx->tmp_k, n_total * 8));
+  CK(ensure(ctx->tmp_aux, n_total * 2));
+  if (pairs) CK(ensure(ctx->tmp_v, n_total * 4));
+  uint64_t* const tmp_k = as<uint64_t>(ctx->tmp_k);
+  uint32_t* const tmp_v = pairs ? as<uint32_t>(ctx->tmp_v) : nullptr;
   const uint64_t* src = in_k;
   const uint32_t* src_v = in_v;
   bool first = true;
   while (!level.empty()) {
     Plan pl;
-    plan_level(ctx->policy, ctx->tuning, level, pl);
+    plan_level(ctx->policy, ctx->tuning, ctx->pcache, level, pl);
     const uint32_t S = (uint32_t)level.size();
     uint64_t n_level = 0;
     for (auto& s : level) n_level += s.n;
     ctx->stats.levels += 1;
+    uint64_t* P1 = (src == tmp_k) ? out_k : tmp_k;
+    uint32_t* P1v = (src == tmp_k) ? out_v : tmp_v;
+    uint64_t* P2 = (P1 == tmp_k) ? out_k : tmp_k;
+    uint32_t* P2v = (P1 == tmp_k) ? out_v : tmp_v;
+    uint64_t* X = pl.two_pass ? P2 : P1;
+    uint32_t* Xv = pl.two_pass ? P2v : P1v;
     // upload plan: segs | range_base | k1_base | tile1_base | group_base | bucket_base
     const size_t o_seg = 0, o_rb = o_seg + S * sizeof(Seg), o_k1 = o_rb + (S + 1) * 4,
                  o_t1 = o_k1 + (S + 1) * 4, o_gb = ((o_t1 + (S + 1) * 4) + 7) & ~(size_t)7,
@@ -397,43 +488,46 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     }
     CK(launch_model(lc, d_segs, S));
     tm.mark(0);
-    if (first && src != out_k)
-      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], src, out_k, src_v, out_v));
+    // (sub)arrays with one value are final; degenerate ones join the
+    // fallback list, whose keys are taken from X
+    if (src != out_k)
+      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], src, out_k, src_v, out_v,
+                          1u << SEG_SINGLE));
+    if (src != X)
+      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], src, X, src_v, Xv,
+                          1u << SEG_DEGEN));
     // lists
     const uint64_t max_items = std::max<uint64_t>(pl.n_buckets, S) + 16;
-    CK(ensure(ctx->leaf, max_items * sizeof(WorkItem)));
+    CK(ensure(ctx->leaf, max_items * sizeof(BRec)));
     CK(ensure(ctx->next, max_items * sizeof(WorkItem)));
     CK(ensure(ctx->fb, max_items * sizeof(FbItem)));
     LevelOut* d_lo = as<LevelOut>(ctx->lout);
     CK(cudaMemsetAsync(d_lo, 0, sizeof(LevelOut), st));
     CK(launch_seg_status_lists(lc, d_segs, S, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
-    // sample + PCF
+    // sample + PCF: counts per bin, then b by one inclusive scan of the pool
     CK(ensure(ctx->tpool, pl.tpool * 4));
-    CK(ensure(ctx->done, S * 4));
     CK(cudaMemsetAsync(ctx->tpool.p, 0, pl.tpool * 4, st));
-    CK(cudaMemsetAsync(ctx->done.p, 0, S * 4, st));
-    CK(launch_sample(lc, d_segs, S, d_k1, pl.k1_base[S], src, as<uint32_t>(ctx->tpool),
-                     as<uint32_t>(ctx->done), ctx->policy));
+    const uint64_t sw_need = ((std::max(std::max(pl.cmat1, pl.cmat2_bound), pl.tpool) +
+                               kScanTile - 1) / kScanTile +
+                              (pl.n_groups + kScanTile - 1) / kScanTile + 8) * 8;
+    CK(ensure(ctx->sw, sw_need));
+    uint32_t* tile_counter = as<uint32_t>(ctx->misc);
+    uint64_t* totals = (uint64_t*)((char*)ctx->misc.p + 64);
+    CK(launch_sample(lc, d_segs, S, d_k1, pl.k1_base[S], src, as<uint32_t>(ctx->tpool)));
+    CK(launch_table(lc, d_segs, S, as<uint32_t>(ctx->tpool), pl.tpool, as<uint64_t>(ctx->sw),
+                    tile_counter, spin_limit));
     tm.mark(1);
     // pass 1
-    CK(ensure(ctx->tmp_k, n_total * 8));
-    CK(ensure(ctx->tmp_aux, n_total * 2));
-    if (pairs) CK(ensure(ctx->tmp_v, n_total * 4));
     KeyBufs kb;
     kb.src = src;
     kb.src_v = src_v;
-    kb.tmp = as<uint64_t>(ctx->tmp_k);
-    kb.tmp_v = pairs ? as<uint32_t>(ctx->tmp_v) : nullptr;
+    kb.tmp = P1;
+    kb.tmp_v = P1v;
     kb.tmp_aux = as<uint16_t>(ctx->tmp_aux);
-    kb.out = out_k;
-    kb.out_v = out_v;
-    const uint64_t sw_need = ((std::max(pl.cmat1, pl.cmat2_bound) + kScanTile - 1) / kScanTile +
-                              (pl.n_groups + kScanTile - 1) / kScanTile + 8) * 8;
-    CK(ensure(ctx->sw, sw_need));
+    kb.out = P2;
+    kb.out_v = P2v;
     CK(ensure(ctx->cmat1, pl.cmat1 * 4));
     CK(cudaMemsetAsync(ctx->cmat1.p, 0, pl.cmat1 * 4, st));
-    uint32_t* tile_counter = as<uint32_t>(ctx->misc);
-    uint64_t* totals = (uint64_t*)((char*)ctx->misc.p + 64);
     CK(launch_hist1(lc, d_segs, S, d_t1, pl.tile1_base[S], tile_keys, src,
                     as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1));
     CK(launch_scan(lc, as<uint32_t>(ctx->cmat1), pl.cmat1, nullptr, as<uint64_t>(ctx->sw),
@@ -442,39 +536,52 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     CK(launch_scatter1(lc, d_segs, S, d_t1, pl.tile1_base[S], tile_keys, kb,
                        as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1));
     tm.mark(3);
+    ctx->stats.global_passes += 1;
+    ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 /*hist1*/ + 8 + 10 /*scatter1*/) +
+                              (pairs ? n_level * 8 : 0);
     // pass 2
-    CK(ensure(ctx->groups, pl.n_groups * sizeof(Group)));
-    CK(ensure(ctx->gtiles, pl.n_groups * 4));
-    CK(ensure(ctx->gcent, pl.n_groups * 4));
-    CK(launch_groups(lc, d_segs, S, d_gb, pl.n_groups, as<uint32_t>(ctx->cmat1), tile_keys,
-                     as<Group>(ctx->groups), as<uint32_t>(ctx->gtiles), as<uint32_t>(ctx->gcent)));
-    CK(launch_scan(lc, as<uint32_t>(ctx->gtiles), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
-                   tile_counter, 0xFFFFFFFFu, spin_limit, &totals[0]));
-    CK(launch_scan(lc, as<uint32_t>(ctx->gcent), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
-                   tile_counter, 0xFFFFFFFFu, spin_limit, &totals[1]));
-    CK(launch_group_bases(lc, as<Group>(ctx->groups), pl.n_groups, as<uint32_t>(ctx->gcent)));
-    CK(ensure(ctx->cmat2, pl.cmat2_bound * 4));
-    CK(cudaMemsetAsync(ctx->cmat2.p, 0, pl.cmat2_bound * 4, st));
-    CK(launch_hist2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
-                    as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound, tile_keys,
-                    kb.tmp_aux, as<uint32_t>(ctx->cmat2), pl.dmax2));
-    CK(launch_scan(lc, as<uint32_t>(ctx->cmat2), pl.cmat2_bound, &totals[1],
-                   as<uint64_t>(ctx->sw), tile_counter, 0xFFFFFFFFu, spin_limit, nullptr));
-    tm.mark(4);
-    CK(launch_scatter2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
-                       as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound,
-                       tile_keys, kb, as<uint32_t>(ctx->cmat2), pl.dmax2));
-    tm.mark(5);
-    ctx->stats.global_passes += 2;
-    ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 /*hist1*/ + 8 + 10 /*scatter1*/ +
-                                         2 /*hist2*/ + 10 + 8 /*scatter2*/) +
-                              (pairs ? n_level * 16 : 0);
-    // buckets
+    if (pl.two_pass) {
+      CK(ensure(ctx->groups, pl.n_groups * sizeof(Group)));
+      CK(ensure(ctx->gtiles, pl.n_groups * 4));
+      CK(ensure(ctx->gcent, pl.n_groups * 4));
+      CK(launch_groups(lc, d_segs, S, d_gb, pl.n_groups, as<uint32_t>(ctx->cmat1), tile_keys,
+                       as<Group>(ctx->groups), as<uint32_t>(ctx->gtiles),
+                       as<uint32_t>(ctx->gcent)));
+      CK(launch_scan(lc, as<uint32_t>(ctx->gtiles), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
+                     tile_counter, 0xFFFFFFFFu, spin_limit, &totals[0]));
+      CK(launch_scan(lc, as<uint32_t>(ctx->gcent), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
+                     tile_counter, 0xFFFFFFFFu, spin_limit, &totals[1]));
+      CK(launch_group_bases(lc, as<Group>(ctx->groups), pl.n_groups, as<uint32_t>(ctx->gcent)));
+      CK(ensure(ctx->cmat2, pl.cmat2_bound * 4));
+      CK(cudaMemsetAsync(ctx->cmat2.p, 0, pl.cmat2_bound * 4, st));
+      CK(launch_hist2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
+                      as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound, tile_keys,
+                      kb.tmp_aux, as<uint32_t>(ctx->cmat2), pl.dmax2));
+      CK(launch_scan(lc, as<uint32_t>(ctx->cmat2), pl.cmat2_bound, &totals[1],
+                     as<uint64_t>(ctx->sw), tile_counter, 0xFFFFFFFFu, spin_limit, nullptr));
+      tm.mark(4);
+      CK(launch_scatter2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
+                         as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound,
+                         tile_keys, kb, as<uint32_t>(ctx->cmat2), pl.dmax2));
+      // segments whose bucket id has one digit were already bucketed by pass 1
+      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], P1, P2, P1v, P2v,
+                          kCopyOneDigit));
+      tm.mark(5);
+      ctx->stats.global_passes += 1;
+      ctx->stats.bytes_moved += n_level * (2 /*hist2*/ + 10 + 8 /*scatter2*/) +
+                                (pairs ? n_level * 8 : 0);
+    }
+    // buckets: Alg. 1's per-bucket decision, then the on-chip finish
     CK(launch_buckets(lc, d_segs, S, pl.n_buckets, d_bb, as<Group>(ctx->groups),
-                      as<uint32_t>(ctx->cmat2), cap, as<WorkItem>(ctx->leaf),
+                      as<uint32_t>(ctx->cmat1), as<uint32_t>(ctx->cmat2), pl.two_pass, cap,
+                      (uint32_t)ctx->policy.tau, X, Xv, out_k, out_v, as<BRec>(ctx->leaf),
                       as<WorkItem>(ctx->next), as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
-    CK(launch_leaf(lc, as<WorkItem>(ctx->leaf), &d_lo->n_leaf, &d_lo->leaf_cursor, out_k, out_k,
-                   out_v, out_v, ctx->policy, cap, lg.tmax, lg.gmax, lg.warps, lg.grid));
+    {
+      const uint64_t wb = level.front().off, span = level.back().off + level.back().n - wb;
+      CK(ensure(ctx->gtot, ((span + window - 1) / window + 2) * 4));
+      CK(launch_chunk(lc, as<BRec>(ctx->leaf), (uint32_t)pl.n_buckets, wb, span, window, cap, X,
+                      Xv, out_k, out_v, ctx->policy, ptab, as<uint32_t>(ctx->gtot)));
+    }
     tm.mark(6);
     CK(cudaMemcpyAsync(ctx->h_lout.p, d_lo, sizeof(LevelOut), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
@@ -511,12 +618,14 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       CK(cudaMemcpyAsync((char*)ctx->fb_bases.p + (nf + 1) * 4, mb.data(), (nf + 1) * 4,
                          cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync(ctx->fb_lohi.p, lohi.data(), nf * 16, cudaMemcpyHostToDevice, st));
-      CK(launch_fb_range(lc, as<FbItem>(ctx->fb), nf, as<uint32_t>(ctx->fb_bases), rb[nf], out_k,
+      CK(launch_fb_range(lc, as<FbItem>(ctx->fb), nf, as<uint32_t>(ctx->fb_bases), rb[nf], X,
                          as<uint64_t>(ctx->fb_lohi)));
+      // scratch: the buffer that is not X (the items' ranges there are free)
+      uint64_t* Y = (X == tmp_k) ? out_k : tmp_k;
+      uint32_t* Yv = (X == tmp_k) ? out_v : tmp_v;
       CK(launch_fb_sort(lc, as<FbItem>(ctx->fb), nf,
                         (const uint32_t*)((char*)ctx->fb_bases.p + (nf + 1) * 4), mb[nf], max_n,
-                        as<uint64_t>(ctx->fb_lohi), out_k, as<uint64_t>(ctx->tmp_k), out_v,
-                        pairs ? as<uint32_t>(ctx->tmp_v) : nullptr));
+                        as<uint64_t>(ctx->fb_lohi), X, Y, Xv, Yv, out_k, out_v));
       CK(cudaStreamSynchronize(st));
       tm.mark(7);
     }
@@ -530,8 +639,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                 [](const InSeg& a, const InSeg& b) { return a.off < b.off; });
     }
     level.swap(nextl);
-    src = out_k;
-    src_v = out_v;
+    src = X;
+    src_v = Xv;
     first = false;
   }
   CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
@@ -605,9 +714,16 @@ pcf_status pcf_ctx_set_tuning(pcf_ctx* ctx, const pcf_tuning* t) {
   if (t->max_digit_bits) n.max_digit_bits = t->max_digit_bits;
   if (t->tile_log2) n.tile_log2 = t->tile_log2;
   if (t->leaf_cap) n.leaf_cap = t->leaf_cap;
+  if (t->onchip_window) n.onchip_window = t->onchip_window;
   if (n.max_digit_bits < 4 || n.max_digit_bits > 11) return PCF_ERR_INVALID_ARG;
   if (n.tile_log2 < 12 || n.tile_log2 > 18) return PCF_ERR_INVALID_ARG;
   if (n.leaf_cap < 64 || n.leaf_cap > 1024 || (n.leaf_cap & (n.leaf_cap - 1))) return PCF_ERR_INVALID_ARG;
+  if (n.onchip_window < 1024 || n.onchip_window > 8192 ||
+      (n.onchip_window & (n.onchip_window - 1)))
+    return PCF_ERR_INVALID_ARG;
+  // the on-chip window (keys, values and tables) must fit one block's shared memory
+  if (chunk_smem_bytes(n.onchip_window, n.leaf_cap, ctx->policy, true) > 227 * 1024)
+    return PCF_ERR_INVALID_ARG;
   ctx->tuning = n;
   return PCF_OK;
 }
@@ -777,7 +893,7 @@ pcf_status pcf_debug_level0(pcf_ctx* ctx, const void* d_keys, uint64_t n, pcf_ke
   CK(cudaSetDevice(ctx->device));
   std::vector<InSeg> in{InSeg{0, n, 0, seed, 0}};
   Plan pl;
-  plan_level(ctx->policy, ctx->tuning, in, pl);
+  plan_level(ctx->policy, ctx->tuning, ctx->pcache, in, pl);
   const uint32_t S = 1;
   CK(ensure(ctx->status, 64));
   CK(ensure(ctx->segs, sizeof(Seg) + 64));
@@ -799,9 +915,12 @@ pcf_status pcf_debug_level0(pcf_ctx* ctx, const void* d_keys, uint64_t n, pcf_ke
   CK(launch_range(lc, as<Seg>(ctx->segs), S, as<uint32_t>(ctx->bases), pl.range_base[1],
                   (const uint64_t*)d_keys, kt == PCF_KEY_F64));
   CK(launch_model(lc, as<Seg>(ctx->segs), S));
+  CK(ensure(ctx->misc, 256));
+  CK(ensure(ctx->sw, ((pl.tpool + kScanTile - 1) / kScanTile + 8) * 8));
   CK(launch_sample(lc, as<Seg>(ctx->segs), S, as<uint32_t>(ctx->bases) + 2, pl.k1_base[1],
-                   (const uint64_t*)d_keys, as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->done),
-                   ctx->policy));
+                   (const uint64_t*)d_keys, as<uint32_t>(ctx->tpool)));
+  CK(launch_table(lc, as<Seg>(ctx->segs), S, as<uint32_t>(ctx->tpool), pl.tpool,
+                  as<uint64_t>(ctx->sw), as<uint32_t>(ctx->misc), kSpinLimit));
   Seg g;
   CK(cudaMemcpy(&g, ctx->segs.p, sizeof(Seg), cudaMemcpyDeviceToHost));
   h_params8[0] = g.alpha;
@@ -815,6 +934,7 @@ pcf_status pcf_debug_level0(pcf_ctx* ctx, const void* d_keys, uint64_t n, pcf_ke
   if (h_T && g.status == SEG_BUCKET) {
     if (T_cap < (uint64_t)g.beta + 1) return PCF_ERR_INVALID_ARG;
     CK(cudaMemcpy(h_T, ctx->tpool.p, ((size_t)g.beta + 1) * 4, cudaMemcpyDeviceToHost));
+    for (uint32_t k = 0; k <= g.beta; ++k) h_T[k] = bucket_of_count(h_T[k] - g.tbase, g.alpha, g.gamma);
   }
   return PCF_OK;
 }

@@ -32,7 +32,7 @@ struct Seg {
   uint64_t cbase1;  // its pass-1 count block (2^b1 x tiles1) in the pass-1 matrix
   uint64_t key_prefix;  // sum of n over the earlier segments of the level
   uint32_t tiles1;      // count tiles of pass 1
-  uint32_t pad0;
+  uint32_t tbase;       // inclusive scan of the table pool before this segment
   uint64_t group_base;  // index of its first pass-1 group
   uint64_t bucket_base; // index of its first bucket (gamma + 1 of them)
   uint64_t ord_lo, ord_hi;  // range (total-order keys), reduced on the device
@@ -60,6 +60,21 @@ struct WorkItem {
   uint32_t depth;
 };
 
+// Every bucket of a level, in memory order (bucket index order): written by
+// k_buckets, read by the on-chip kernel.
+enum : uint32_t {
+  BK_LEAF = 1u,  // finished on chip
+  BK_STD = 2u,   // ... by Standard-Sort (|c| >= delta or |c| < tau)
+};
+struct BRec {
+  uint32_t off;    // absolute offset of its first key
+  uint32_t n;      // size
+  uint32_t kind;   // BK_* (0: empty, already finished, or handled elsewhere)
+  uint32_t depth;  // recursion depth of the Learned-Sort call on this bucket
+  uint64_t start;  // offset inside the caller's array
+  uint64_t seed;
+};
+
 // A bucket for the standard sort (failure guard |c| >= delta, or a
 // degenerate range).
 struct FbItem {
@@ -81,7 +96,7 @@ struct LevelOut {
 struct KeyBufs {
   const uint64_t* src;  // where the level reads
   uint64_t* tmp;        // pass-1 target
-  uint64_t* out;        // pass-2 target / final
+  uint64_t* out;        // pass-2 target
   const uint32_t* src_v;
   uint32_t* tmp_v;
   uint32_t* out_v;
@@ -113,14 +128,17 @@ cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32
                          uint32_t n_tiles, const uint64_t* keys, bool check_nan);
 cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S);
 cudaError_t launch_sample(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
-                          uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool,
-                          uint32_t* done, Policy P);
+                          uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool);
+// cumulative counts b (inclusive scan of the whole pool) + per-segment bases
+cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tpool,
+                         uint64_t pool_n, uint64_t* status_words, uint32_t* tile_counter,
+                         uint64_t spin_limit);
 cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
                          uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
                          const uint32_t* tpool, uint32_t* cmat, uint32_t dmax);
 cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const uint64_t* n_dev,
                         uint64_t* status_words, uint32_t* tile_counter, uint32_t withhold,
-                        uint64_t spin_limit, uint64_t* total_out);
+                        uint64_t spin_limit, uint64_t* total_out, bool inclusive = false);
 cudaError_t launch_scatter1(const LaunchCfg& c, const Seg* segs, uint32_t S,
                             const uint32_t* tile_base, uint32_t n_tiles, uint32_t tile_keys,
                             const KeyBufs& kb, const uint32_t* tpool, const uint32_t* cmat,
@@ -142,24 +160,40 @@ cudaError_t launch_scatter2(const LaunchCfg& c, const Group* groups, uint32_t n_
                             uint32_t dmax);
 cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint64_t n_buckets,
                            const uint64_t* bucket_base, const Group* groups,
-                           const uint32_t* cmat2, uint32_t leaf_cap, WorkItem* leaf,
-                           WorkItem* next, FbItem* fb, LevelOut* lo, uint32_t max_items);
+                           const uint32_t* cmat1, const uint32_t* cmat2, bool two_pass,
+                           uint32_t leaf_cap, uint32_t tau, const uint64_t* X, const uint32_t* Xv,
+                           uint64_t* out_k, uint32_t* out_v, BRec* brec, WorkItem* next,
+                           FbItem* fb, LevelOut* lo, uint32_t max_items);
 cudaError_t launch_seg_status_lists(const LaunchCfg& c, const Seg* segs, uint32_t S,
                                     FbItem* fb, LevelOut* lo, uint32_t max_items);
+// copies the segments whose status is in status_mask (bit per SEG_*), or,
+// with kCopyOneDigit, the bucketed segments whose bucket id has one digit
+constexpr uint32_t kCopyOneDigit = 0x100u;
 cudaError_t launch_copy_segs(const LaunchCfg& c, const Seg* segs, uint32_t S,
                              const uint32_t* range_base, uint32_t n_tiles, const uint64_t* src,
-                             uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v);
+                             uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v,
+                             uint32_t status_mask);
 cudaError_t launch_leaf(const LaunchCfg& c, const WorkItem* items, const uint32_t* n_items,
                         uint32_t* cursor, const uint64_t* src, uint64_t* dst,
-                        const uint32_t* src_v, uint32_t* dst_v, Policy P, uint32_t cap,
-                        uint32_t tmax, uint32_t gmax, uint32_t warps_per_cta, uint32_t grid);
+                        const uint32_t* src_v, uint32_t* dst_v, Policy P, const uint16_t* ptab,
+                        uint32_t cap, uint32_t tmax, uint32_t gmax, uint32_t warps_per_cta,
+                        uint32_t grid);
 size_t leaf_smem_per_warp(uint32_t cap, bool pairs, uint32_t tmax, uint32_t gmax);
+// on-chip finish of the leaf buckets whose records are br[0..nb): windows of
+// `window` keys starting at wbase, covering span keys
+cudaError_t launch_chunk(const LaunchCfg& c, const BRec* br, uint32_t nb, uint64_t wbase,
+                         uint64_t span, uint32_t window, uint32_t leaf_cap, const uint64_t* X,
+                         const uint32_t* Xv, uint64_t* out, uint32_t* out_v, Policy P,
+                         const uint16_t* ptab, uint32_t* first_scratch);
+size_t chunk_smem_bytes(uint32_t window, uint32_t leaf_cap, const Policy& P, bool pairs);
 cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                             const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
                             uint64_t* ord_lohi);
+// sorts the items in `keys` (scratch `tmp`), leaving the result in `final`
 cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                            const uint32_t* mtile_base, uint32_t n_mtiles, uint64_t max_n,
                            const uint64_t* ord_lohi, uint64_t* keys, uint64_t* tmp,
-                           uint32_t* vals, uint32_t* tmp_v);
+                           uint32_t* vals, uint32_t* tmp_v, uint64_t* final_k,
+                           uint32_t* final_v);
 
 }  // namespace pcf

@@ -195,7 +195,8 @@ __device__ __forceinline__ uint32_t wscan_incl(uint32_t v) {
 template <bool PAIRS>
 __device__ uint32_t learned_step(const WarpSmem& s, uint32_t sp, uint32_t o, uint32_t c,
                                  uint32_t depth, uint64_t start, uint64_t seed, uint32_t kt,
-                                 const Policy& P, uint32_t stack_cap, uint32_t tmax, uint32_t gmax,
+                                 const Policy& P, const uint16_t* __restrict__ ptab,
+                                 uint32_t stack_cap, uint32_t tmax, uint32_t gmax,
                                  uint32_t* status) {
   const uint32_t lane = threadIdx.x & 31;
   // range of the sub-array (Sec. 3.3: x_min, x_max)
@@ -211,7 +212,14 @@ __device__ uint32_t learned_step(const WarpSmem& s, uint32_t sp, uint32_t o, uin
     mx = max(mx, (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d));
   }
   if (mn == mx) return sp;  // one distinct value: already sorted
-  const Params pr = params_of(P, c);
+  Params pr;
+  {
+    const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + c);
+    pr.alpha = q.x;
+    pr.beta = q.y;
+    pr.gamma = q.z;
+    pr.delta = q.w;
+  }
   if (pr.beta + 1 > tmax || pr.gamma + 1 > gmax) {
     if (lane == 0) atomicOr(status, STATUS_INTERNAL);
     warp_merge_sort<PAIRS>(s, o, c, kt);
@@ -324,7 +332,8 @@ __device__ uint32_t learned_step(const WarpSmem& s, uint32_t sp, uint32_t o, uin
 // Learned-Sort of A[0, n) (or the standard sort when std_only)
 template <bool PAIRS>
 __device__ void warp_learned_sort(const WarpSmem& s, uint32_t n, uint32_t depth0, uint64_t start0,
-                                  uint64_t seed, uint32_t kt, const Policy& P, bool std_only,
+                                  uint64_t seed, uint32_t kt, const Policy& P,
+                                  const uint16_t* __restrict__ ptab, bool std_only,
                                   uint32_t stack_cap, uint32_t tmax, uint32_t gmax,
                                   uint32_t* status) {
   const uint32_t lane = threadIdx.x & 31;
@@ -345,7 +354,7 @@ __device__ void warp_learned_sort(const WarpSmem& s, uint32_t n, uint32_t depth0
     if (jb.kind == JOB_SORT || jb.c < P.tau) {
       if (jb.c > 1) warp_merge_sort<PAIRS>(s, jb.o, jb.c, kt);
     } else {
-      sp = learned_step<PAIRS>(s, sp, jb.o, jb.c, jb.depth, start0 + jb.o, seed, kt, P,
+      sp = learned_step<PAIRS>(s, sp, jb.o, jb.c, jb.depth, start0 + jb.o, seed, kt, P, ptab,
                                stack_cap, tmax, gmax, status);
     }
     __syncwarp();
@@ -357,8 +366,9 @@ __global__ void __launch_bounds__(256) k_leaf(const WorkItem* __restrict__ items
                                               const uint32_t* n_items, uint32_t* cursor,
                                               const uint64_t* __restrict__ src, uint64_t* dst,
                                               const uint32_t* __restrict__ src_v, uint32_t* dst_v,
-                                              uint32_t kt, Policy P, uint32_t cap, uint32_t tmax,
-                                              uint32_t gmax, uint32_t* status) {
+                                              uint32_t kt, Policy P,
+                                              const uint16_t* __restrict__ ptab, uint32_t cap,
+                                              uint32_t tmax, uint32_t gmax, uint32_t* status) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t per = warp_smem_bytes(cap, PAIRS, tmax, gmax);
@@ -381,7 +391,7 @@ __global__ void __launch_bounds__(256) k_leaf(const WorkItem* __restrict__ items
     }
     __syncwarp();
     const bool std_only = (w.depth & kStdFlag) != 0;
-    warp_learned_sort<PAIRS>(s, w.n, w.depth & ~kStdFlag, w.start, w.seed, kt, P, std_only,
+    warp_learned_sort<PAIRS>(s, w.n, w.depth & ~kStdFlag, w.start, w.seed, kt, P, ptab, std_only,
                              stack_cap, tmax, gmax, status);
     __syncwarp();
     for (uint32_t i = lane; i < w.n; i += 32) {
@@ -559,10 +569,15 @@ __global__ void __launch_bounds__(256) k_fb_copy(const FbItem* items, uint32_t n
                                                  const uint32_t* tile_base,
                                                  const uint64_t* ord_lohi, const uint64_t* src,
                                                  uint64_t* dst, const uint32_t* src_v,
-                                                 uint32_t* dst_v) {
+                                                 uint32_t* dst_v, const uint64_t* orig,
+                                                 const uint32_t* orig_v) {
   const uint32_t t = blockIdx.x;
   const uint32_t i = ub_dev(tile_base, n_items + 1, t) - 1;
-  if (ord_lohi[2 * i] == ord_lohi[2 * i + 1]) return;
+  if (ord_lohi[2 * i] == ord_lohi[2 * i + 1]) {  // never moved: copy from where it is
+    src = orig;
+    src_v = orig_v;
+  }
+  if (src == dst) return;
   const FbItem it = items[i];
   const uint64_t base = it.off + (uint64_t)(t - tile_base[i]) * kMergeTile;
   const uint64_t end = min(it.off + it.n, base + kMergeTile);
@@ -579,8 +594,9 @@ static inline uint32_t cdiv32(uint64_t a, uint64_t b) { return (uint32_t)((a + b
 
 cudaError_t launch_leaf(const LaunchCfg& c, const WorkItem* items, const uint32_t* n_items,
                         uint32_t* cursor, const uint64_t* src, uint64_t* dst,
-                        const uint32_t* src_v, uint32_t* dst_v, Policy P, uint32_t cap,
-                        uint32_t tmax, uint32_t gmax, uint32_t warps_per_cta, uint32_t grid) {
+                        const uint32_t* src_v, uint32_t* dst_v, Policy P, const uint16_t* ptab,
+                        uint32_t cap, uint32_t tmax, uint32_t gmax, uint32_t warps_per_cta,
+                        uint32_t grid) {
   const size_t sm = warp_smem_bytes(cap, c.pairs, tmax, gmax) * warps_per_cta;
   cudaError_t e;
   if (c.pairs) {
@@ -588,16 +604,16 @@ cudaError_t launch_leaf(const LaunchCfg& c, const WorkItem* items, const uint32_
                                   (int)sm)))
       return e;
     k_leaf<true><<<grid, 32 * warps_per_cta, sm, c.stream>>>(items, n_items, cursor, src, dst,
-                                                             src_v, dst_v, c.kt, P, cap, tmax,
-                                                             gmax, c.status);
+                                                             src_v, dst_v, c.kt, P, ptab, cap,
+                                                             tmax, gmax, c.status);
     count_launch(c);
   } else {
     if ((e = cudaFuncSetAttribute(k_leaf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm)))
       return e;
     k_leaf<false><<<grid, 32 * warps_per_cta, sm, c.stream>>>(items, n_items, cursor, src, dst,
-                                                              src_v, dst_v, c.kt, P, cap, tmax,
-                                                              gmax, c.status);
+                                                              src_v, dst_v, c.kt, P, ptab, cap,
+                                                              tmax, gmax, c.status);
     count_launch(c);
   }
   return cudaGetLastError();
@@ -619,7 +635,8 @@ cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_
 cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                            const uint32_t* mtile_base, uint32_t n_mtiles, uint64_t max_n,
                            const uint64_t* ord_lohi, uint64_t* keys, uint64_t* tmp,
-                           uint32_t* vals, uint32_t* tmp_v) {
+                           uint32_t* vals, uint32_t* tmp_v, uint64_t* final_k,
+                           uint32_t* final_v) {
   if (!n_mtiles) return cudaSuccess;
   if (c.pairs) {
     k_fb_block_sort<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi,
@@ -635,7 +652,6 @@ cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_i
   uint64_t* B = tmp;
   uint32_t* Av = vals;
   uint32_t* Bv = tmp_v;
-  int passes = 0;
   for (uint64_t w = kMergeTile; w < max_n; w *= 2) {
     if (c.pairs) {
       k_fb_merge<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi, w, A,
@@ -652,15 +668,15 @@ cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_i
     uint32_t* tv = Av;
     Av = Bv;
     Bv = tv;
-    ++passes;
   }
-  if (passes & 1) {
+  // items with one distinct value were never moved: they are in `keys`
+  if (A != final_k || keys != final_k) {
     if (c.pairs) {
       k_fb_copy<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi, A,
-                                                      keys, Av, vals);
+                                                      final_k, Av, final_v, keys, vals);
     } else {
       k_fb_copy<false><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi, A,
-                                                       keys, nullptr, nullptr);
+                                                       final_k, nullptr, nullptr, keys, nullptr);
     }
     count_launch(c);
     if ((e = cudaGetLastError())) return e;

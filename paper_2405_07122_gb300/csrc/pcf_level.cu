@@ -146,24 +146,23 @@ __device__ __forceinline__ T block_excl_scan256(T v, T* sh8, T* total) {
 }
 
 // ---------------------------------------------------------------------------
-// k_sample: training (Sec. 3.3).  alpha samples are drawn with replacement,
-// counted per bin; the last CTA of the segment turns the counts into
-// b_k = |{j : bin(a_j) <= k}| and the bucket table T[k] in place.
+// k_sample: training (Sec. 3.3): alpha samples drawn with replacement and
+// counted per bin.  The cumulative counts b_k = |{j : bin(a_j) <= k}| come
+// from one inclusive scan of the whole table pool (k_scan) and a per-segment
+// base (k_seg_base), so that b_k = pool[T_off + k] - tbase.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_sample(const Seg* segs, uint32_t S,
                                                 const uint32_t* k1_base,
                                                 const uint64_t* __restrict__ keys, uint32_t kt,
-                                                uint32_t* tpool, uint32_t* done) {
+                                                uint32_t* tpool) {
   const uint32_t c = blockIdx.x;
   const uint32_t s = upper_bound_dev(k1_base, S + 1, c) - 1;
   const Seg& g = segs[s];
   if (g.status != SEG_BUCKET) return;
   __shared__ BinModel bm;
-  __shared__ uint32_t s_last;
-  __shared__ uint32_t sh8[8];
   if (threadIdx.x == 0) bm = g.bm;
   __syncthreads();
-  const uint32_t cta = c - k1_base[s], nctas = k1_base[s + 1] - k1_base[s];
+  const uint32_t cta = c - k1_base[s];
   const uint64_t st = sample_state(g.seed, g.depth, g.start, g.n);
   const uint32_t j0 = cta * kSamplesPerCta, j1 = min(g.alpha, j0 + kSamplesPerCta);
   uint32_t* cnt = tpool + g.T_off;
@@ -172,40 +171,24 @@ __global__ void __launch_bounds__(256) k_sample(const Seg* segs, uint32_t S,
     uint64_t x = ld_nc(keys + g.off + idx);
     atomicAdd(&cnt[bin_of(bm, x)], 1u);
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&done[s], 1u) == nctas - 1) ? 1u : 0u;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // inclusive scan of cnt[0..beta] -> b, then T = floor(b gamma / alpha)
-  const uint32_t L = g.beta + 1, alpha = g.alpha, gamma = g.gamma;
-  uint32_t carry = 0;
-  for (uint32_t b0 = 0; b0 < L; b0 += 256 * 8) {
-    uint32_t v[8], sum = 0;
-    const uint32_t my = b0 + threadIdx.x * 8;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      v[k] = (my + k < L) ? __ldcg(cnt + my + k) : 0u;
-      sum += v[k];
-    }
-    uint32_t tot;
-    uint32_t ex = block_excl_scan256(sum, sh8, &tot) + carry;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      ex += v[k];
-      if (my + k < L) cnt[my + k] = bucket_of_count(ex, alpha, gamma);
-    }
-    carry += tot;
-  }
+}
+
+// tbase of each segment: the inclusive pool scan just before its table
+__global__ void k_seg_base(Seg* segs, uint32_t S, const uint32_t* tpool) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const uint64_t o = segs[s].T_off;
+  segs[s].tbase = o ? tpool[o - 1] : 0u;
 }
 
 // ---------------------------------------------------------------------------
 // bucket id of a key under segment g: T[bin(x)]
 // ---------------------------------------------------------------------------
+// bucket of a key under segment g (Alg. 1: floor(F(x) gamma), F = b_bin / alpha)
 __device__ __forceinline__ uint32_t bucket_id(const BinModel& bm, const uint32_t* __restrict__ T,
+                                              uint32_t tbase, uint32_t alpha, uint32_t gamma,
                                               uint64_t x) {
-  return __ldg(T + bin_of(bm, x));
+  return bucket_of_count(__ldg(T + bin_of(bm, x)) - tbase, alpha, gamma);
 }
 
 // warp-aggregated shared-memory histogram increment (match.any)
@@ -219,6 +202,11 @@ __device__ __forceinline__ void hist_add(uint32_t* hist, uint32_t d, bool valid)
 // ---------------------------------------------------------------------------
 // k_hist1: per count-tile histogram of the high digit j >> b2
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void hist_inc(uint32_t* hist, uint32_t d, bool valid, bool aggregate) {
+  if (aggregate) hist_add(hist, d, valid);
+  else if (valid) atomicAdd(&hist[d], 1u);
+}
+
 __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
                                                const uint32_t* tile_base, uint32_t tile_keys,
                                                const uint64_t* __restrict__ keys, uint32_t kt,
@@ -231,6 +219,8 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
   const Seg& g = segs[s];
   const uint32_t tt = t - tile_base[s];
   const uint32_t D = 1u << g.b1, b2 = g.b2;
+  // few digits: collisions are common, aggregate them per warp (match.any)
+  const bool agg = D <= 64;
   for (uint32_t d = threadIdx.x; d < D; d += 256) hist[d] = 0;
   if (threadIdx.x == 0) bm = g.bm;
   __syncthreads();
@@ -241,29 +231,37 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
     if (threadIdx.x == 0) hist[0] = (uint32_t)(end - base);
   } else {
     const uint32_t* T = tpool + g.T_off;
-    const uint32_t steps = (uint32_t)((end - base + 255) / 256);
-    uint32_t k = 0;
-    for (; k + 4 <= steps; k += 4) {
-      uint64_t i0 = base + (uint64_t)k * 256 + threadIdx.x;
-      uint64_t x[4];
-      bool v[4];
+    const uint32_t tb = g.tbase, al = g.alpha, ga = g.gamma;
+    constexpr int U = 8;
+    for (uint64_t i0 = base; i0 < end; i0 += 256 * U) {
+      uint64_t x[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        uint64_t i = i0 + u * 256;
-        v[u] = i < end;
-        x[u] = v[u] ? ld_nc(keys + i) : 0ull;
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
+        x[u] = i < end ? ld_nc(keys + i) : 0ull;
       }
+      uint32_t bn[U], amb = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        uint32_t d = v[u] ? (bucket_id(bm, T, x[u]) >> b2) : 0u;
-        hist_add(hist, d, v[u]);
+      for (int u = 0; u < U; ++u) {
+        bool a;
+        bn[u] = bin_fast(bm, x[u], a);
+        amb |= (uint32_t)a << u;
       }
-    }
-    for (; k < steps; ++k) {
-      uint64_t i = base + (uint64_t)k * 256 + threadIdx.x;
-      bool v = i < end;
-      uint32_t d = v ? (bucket_id(bm, T, ld_nc(keys + i)) >> b2) : 0u;
-      hist_add(hist, d, v);
+      if (amb) {
+#pragma unroll 1
+        for (int u = 0; u < U; ++u)
+          if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
+      }
+      uint32_t tv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) tv[u] = __ldg(T + bn[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
+        const bool v = i < end;
+        const uint32_t d = v ? (bucket_of_count(tv[u] - tb, al, ga) >> b2) : 0u;
+        hist_inc(hist, d, v, agg);
+      }
     }
   }
   __syncthreads();
@@ -286,7 +284,8 @@ __device__ __forceinline__ void publish(uint64_t* w, uint64_t flag, uint32_t v) 
 __global__ void __launch_bounds__(256) k_scan(uint32_t* data, uint64_t n, const uint64_t* n_dev,
                                               uint64_t* sw, uint32_t* tile_counter,
                                               uint32_t withhold, uint64_t spin_limit,
-                                              uint64_t* total_out, uint32_t* status) {
+                                              uint64_t* total_out, uint32_t* status,
+                                              int inclusive) {
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t sh8[8];
   __shared__ uint32_t buf[kScanTile];
@@ -339,7 +338,7 @@ __global__ void __launch_bounds__(256) k_scan(uint32_t* data, uint64_t n, const 
   ex += s_prefix;
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    buf[threadIdx.x * 16 + k] = ex;
+    buf[threadIdx.x * 16 + k] = inclusive ? ex + v[k] : ex;
     ex += v[k];
   }
   __syncthreads();
@@ -404,7 +403,8 @@ __device__ __forceinline__ ScatterSmem carve_scatter(uint8_t* p, uint32_t D, boo
 // PASS 1: digit = T[bin(x)] >> b2, carry = low b2 bits.  PASS 2: digit = carry.
 template <int PASS, bool PAIRS>
 __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_off, uint32_t tile_n,
-                             const BinModel& bm, const uint32_t* __restrict__ T, uint32_t b2,
+                             const BinModel& bm, const uint32_t* __restrict__ T, uint32_t tbase,
+                             uint32_t alpha, uint32_t gamma, uint32_t b2,
                              const uint64_t* __restrict__ src, const uint32_t* __restrict__ src_v,
                              const uint16_t* __restrict__ src_aux, uint64_t* __restrict__ dst,
                              uint32_t* __restrict__ dst_v, uint16_t* __restrict__ dst_aux) {
@@ -413,7 +413,11 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
   const uint32_t low_mask = (1u << b2) - 1u;
   for (uint32_t sub = 0; sub < tile_n; sub += kScatterSub) {
     const uint32_t nsub = min(kScatterSub, tile_n - sub);
-    for (uint32_t i = tid; i < 8 * D; i += 256) sm.wcnt[i] = 0;
+    {
+      uint4* z = reinterpret_cast<uint4*>(sm.wcnt);  // 8*D u16, D a power of two >= 1
+      const uint32_t nz = (8 * D * 2 + 15) / 16;
+      for (uint32_t i = tid; i < nz; i += 256) z[i] = make_uint4(0, 0, 0, 0);
+    }
     __syncthreads();
     uint64_t key[kItems];
     uint32_t dig[kItems], aux[kItems], rank[kItems], val[kItems];
@@ -427,24 +431,47 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
       if (PASS == 2) dig[k] = v ? (uint32_t)__ldg(src_aux + g0 + li) : 0u;
     }
     if (PASS == 1) {
+      uint32_t amb = 0;
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        bool a;
+        dig[k] = bin_fast(bm, key[k], a);
+        amb |= (uint32_t)a << k;
+      }
+      if (amb) {
+#pragma unroll 1
+        for (int k = 0; k < kItems; ++k)
+          if ((amb >> k) & 1u) dig[k] = bin_exact_of(bm, key[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) aux[k] = __ldg(T + dig[k]);
 #pragma unroll
       for (int k = 0; k < kItems; ++k) {
         const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
-        uint32_t j = li < nsub ? bucket_id(bm, T, key[k]) : 0u;
+        const uint32_t j = li < nsub ? bucket_of_count(aux[k] - tbase, alpha, gamma) : 0u;
         dig[k] = j >> b2;
         aux[k] = j & low_mask;
       }
     }
+    // per-warp counters as u32 pairs of u16 lanes would race; the counters
+    // are u16 in shared memory and updated with 32-bit atomics on the
+    // aligned word holding them (one leader per digit per step, and shared
+    // atomics of one warp apply in program order, so ranks follow input
+    // order: the scatter is stable)
     uint16_t* my = sm.wcnt + (size_t)w * D;
+    uint32_t* myw = reinterpret_cast<uint32_t*>(my);
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
       const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
       const bool v = li < nsub;
       const uint32_t peers = __match_any_sync(~0u, v ? dig[k] : 0xFFFFFFFFu);
-      uint32_t prior = v ? my[dig[k]] : 0u;
-      __syncwarp();
-      if (v && l == __ffs(peers) - 1) my[dig[k]] = (uint16_t)(prior + __popc(peers));
-      __syncwarp();
+      const int leader = __ffs(peers) - 1;
+      uint32_t prior = 0;
+      if (v && l == leader) {
+        const uint32_t sh = (dig[k] & 1u) * 16u;
+        prior = (atomicAdd(&myw[dig[k] >> 1], (uint32_t)__popc(peers) << sh) >> sh) & 0xFFFFu;
+      }
+      prior = __shfl_sync(~0u, prior, leader);
       rank[k] = prior + __popc(peers & lmask);
     }
     __syncthreads();
@@ -524,8 +551,8 @@ __global__ void __launch_bounds__(256) k_scatter1(const Seg* segs, uint32_t S,
   __syncthreads();
   const uint64_t tile_off = g.off + (uint64_t)tt * tile_keys;
   const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, g.off + g.n - tile_off);
-  scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, bm, tpool + g.T_off, g.b2, kb.src, kb.src_v,
-                         nullptr, kb.tmp, kb.tmp_v, kb.tmp_aux);
+  scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, bm, tpool + g.T_off, g.tbase, g.alpha, g.gamma,
+                         g.b2, kb.src, kb.src_v, nullptr, kb.tmp, kb.tmp_v, kb.tmp_aux);
 }
 
 // ---------------------------------------------------------------------------
@@ -547,7 +574,10 @@ __global__ void k_groups(const Seg* segs, uint32_t S, const uint64_t* group_base
   gr.off = sg.off;
   gr.key_prefix = 0;
   gr.cbase = 0;
-  if (sg.status == SEG_BUCKET) {
+  if (sg.status == SEG_BUCKET && sg.b2 == 0) {
+    // no second digit: pass 2 is one copy of the whole segment
+    if (g == 0) gr.n = (uint32_t)sg.n;
+  } else if (sg.status == SEG_BUCKET) {
     const uint32_t D1 = 1u << sg.b1;
     const uint32_t seg_base = cmat1[sg.cbase1];
     const uint32_t a = cmat1[sg.cbase1 + (uint64_t)g * sg.tiles1] - seg_base;
@@ -582,18 +612,27 @@ __global__ void __launch_bounds__(256) k_hist2(const Group* groups, uint32_t n_g
   if (t >= *total_tiles) return;
   const uint32_t G = upper_bound_dev(g_tile_scan, n_groups, t) - 1;
   const Group gr = groups[G];
+  if (segs[gr.seg].b2 == 0) return;  // one-digit id: copied, not scattered
   const uint32_t D = 1u << segs[gr.seg].b2;
+  const bool agg = D <= 64;
   const uint32_t tt = t - g_tile_scan[G];
   for (uint32_t d = threadIdx.x; d < D; d += 256) hist[d] = 0;
   __syncthreads();
   const uint64_t base = gr.off + (uint64_t)tt * tile_keys;
   const uint64_t end = min(gr.off + gr.n, base + tile_keys);
-  const uint32_t steps = (uint32_t)((end - base + 255) / 256);
-  for (uint32_t k = 0; k < steps; ++k) {
-    uint64_t i = base + (uint64_t)k * 256 + threadIdx.x;
-    bool v = i < end;
-    uint32_t d = v ? (uint32_t)__ldg(aux + i) : 0u;
-    hist_add(hist, d, v);
+  constexpr int U = 16;
+  for (uint64_t i0 = base; i0 < end; i0 += 256 * U) {
+    uint32_t d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
+      d[u] = i < end ? (uint32_t)__ldg(aux + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
+      hist_inc(hist, d[u], i < end, agg);
+    }
   }
   __syncthreads();
   for (uint32_t d = threadIdx.x; d < D; d += 256)
@@ -610,6 +649,7 @@ __global__ void __launch_bounds__(256) k_scatter2(const Group* groups, uint32_t 
   if (t >= *total_tiles) return;
   const uint32_t G = upper_bound_dev(g_tile_scan, n_groups, t) - 1;
   const Group gr = groups[G];
+  if (segs[gr.seg].b2 == 0) return;  // one-digit id: copied, not scattered
   const uint32_t D = 1u << segs[gr.seg].b2;
   const uint32_t tt = t - g_tile_scan[G];
   ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, false);
@@ -620,8 +660,8 @@ __global__ void __launch_bounds__(256) k_scatter2(const Group* groups, uint32_t 
   const uint64_t tile_off = gr.off + (uint64_t)tt * tile_keys;
   const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, gr.off + gr.n - tile_off);
   BinModel dummy;
-  scatter_tile<2, PAIRS>(sm, D, tile_off, tile_n, dummy, nullptr, 0, kb.tmp, kb.tmp_v, kb.tmp_aux,
-                         kb.out, kb.out_v, nullptr);
+  scatter_tile<2, PAIRS>(sm, D, tile_off, tile_n, dummy, nullptr, 0, 1, 1, 0, kb.tmp, kb.tmp_v,
+                         kb.tmp_aux, kb.out, kb.out_v, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -639,27 +679,47 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
   return base + __popc(m & lanemask_lt());
 }
 
+constexpr uint32_t kTiny = 16;  // buckets this small are sorted by one thread
+
+template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, uint64_t n_buckets,
                                                  const uint64_t* bucket_base, const Group* groups,
-                                                 const uint32_t* __restrict__ cmat2,
-                                                 uint32_t leaf_cap, WorkItem* leaf, WorkItem* next,
+                                                 const uint32_t* __restrict__ cmat1,
+                                                 const uint32_t* __restrict__ cmat2, int two_pass,
+                                                 uint32_t leaf_cap, uint32_t tau, uint32_t kt,
+                                                 const uint64_t* __restrict__ X,
+                                                 const uint32_t* __restrict__ Xv, uint64_t* out_k,
+                                                 uint32_t* out_v, BRec* brec, WorkItem* next,
                                                  FbItem* fb, LevelOut* lo, uint32_t max_items,
                                                  uint32_t* status) {
+  // [kTiny][256] (transposed: thread t owns column t, so accesses are
+  // conflict-free)
+  __shared__ uint64_t tk[kTiny][256];
+  __shared__ uint32_t tv[PAIRS ? kTiny : 1][PAIRS ? 256 : 1];
   const uint64_t B = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool v = B < n_buckets;
+  const bool in = B < n_buckets;
   uint32_t s = 0, size = 0;
-  uint64_t off = 0;
-  if (v) {
+  uint64_t off = 0;  // start of the bucket, also when empty (records stay ordered)
+  bool v = false;
+  if (in) {
     s = upper_bound_dev(bucket_base, S + 1, B) - 1;
     const Seg& sg = segs[s];
-    v = sg.status == SEG_BUCKET;
-    if (v) {
+    off = sg.off;
+    if (sg.status == SEG_BUCKET && sg.b2 == 0) {
+      // bucket j is pass-1 digit j (positions kept by the pass-2 copy)
+      const uint32_t j = (uint32_t)(B - sg.bucket_base);
+      const uint32_t base = cmat1[sg.cbase1];
+      const uint32_t a = cmat1[sg.cbase1 + (uint64_t)j * sg.tiles1] - base;
+      const uint32_t b = (j + 1 < (1u << sg.b1)) ? cmat1[sg.cbase1 + (uint64_t)(j + 1) * sg.tiles1] - base
+                                                 : (uint32_t)sg.n;
+      size = b - a;
+      off = sg.off + a;
+    } else if (sg.status == SEG_BUCKET) {
       const uint32_t j = (uint32_t)(B - sg.bucket_base);
       const uint32_t g = j >> sg.b2, d = j & ((1u << sg.b2) - 1u);
       const Group gr = groups[sg.group_base + g];
-      if (gr.n == 0) {
-        v = false;
-      } else {
+      off = gr.off;
+      if (gr.n > 0) {
         const uint32_t gbase = cmat2[gr.cbase];
         const uint32_t a = cmat2[gr.cbase + (uint64_t)d * gr.tiles] - gbase;
         const uint32_t b = (d + 1 < (1u << sg.b2))
@@ -667,34 +727,61 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
                                : gr.n;
         size = b - a;
         off = gr.off + a;
-        v = size > 0;
       }
     }
+    v = sg.status == SEG_BUCKET && size > 0;
   }
   const Seg* sg = v ? &segs[s] : nullptr;
+  // Standard-Sort (|c| >= delta, or |c| < tau inside the recursive call) of a
+  // tiny bucket: insertion sort by this thread, X -> out
+  const bool std_sort = v && (size >= sg->delta || size < tau);
+  if (std_sort && size <= kTiny) {
+    const uint32_t t = threadIdx.x;
+    for (uint32_t i = 0; i < size; ++i) {
+      const uint64_t key = X[off + i];
+      const uint64_t ok = ord_of(key, kt);
+      const uint32_t val = PAIRS ? Xv[off + i] : 0u;
+      uint32_t q = i;
+      while (q > 0 && ord_of(tk[q - 1][t], kt) > ok) {
+        tk[q][t] = tk[q - 1][t];
+        if (PAIRS) tv[q][t] = tv[q - 1][t];
+        --q;
+      }
+      tk[q][t] = key;
+      if (PAIRS) tv[q][t] = val;
+    }
+    for (uint32_t i = 0; i < size; ++i) {
+      out_k[off + i] = tk[i][t];
+      if (PAIRS) out_v[off + i] = tv[i][t];
+    }
+    v = false;
+  }
   const bool is_fb = v && size >= sg->delta && size > leaf_cap;
   const bool is_leaf = v && !is_fb && size <= leaf_cap;
   const bool is_next = v && !is_fb && !is_leaf;
-  // small failure-guard buckets are finished by the shared-memory kernel
-  // with the standard sort (flagged in depth's top bit)
+  if (in) {
+    BRec r;
+    r.off = (uint32_t)off;
+    r.n = size;
+    r.kind = is_leaf ? (BK_LEAF | (std_sort ? BK_STD : 0u)) : 0u;
+    r.depth = sg ? sg->depth + 1 : 0u;
+    r.start = sg ? sg->start + (off - sg->off) : 0ull;
+    r.seed = sg ? sg->seed : 0ull;
+    brec[B] = r;
+  }
   const uint32_t i_leaf = warp_append(&lo->n_leaf, is_leaf);
+  (void)i_leaf;
   const uint32_t i_next = warp_append(&lo->n_next, is_next);
   const uint32_t i_fb = warp_append(&lo->n_fb, is_fb);
-  if (is_leaf || is_next) {
+  if (is_next) {
     WorkItem it;
     it.off = off;
     it.start = sg->start + (off - sg->off);
     it.seed = sg->seed;
     it.n = size;
     it.depth = sg->depth + 1;
-    if (is_leaf && size >= sg->delta) it.depth |= 0x80000000u;
-    if (is_leaf) {
-      if (i_leaf < max_items) leaf[i_leaf] = it;
-      else atomicOr(status, STATUS_INTERNAL);
-    } else {
-      if (i_next < max_items) next[i_next] = it;
-      else atomicOr(status, STATUS_INTERNAL);
-    }
+    if (i_next < max_items) next[i_next] = it;
+    else atomicOr(status, STATUS_INTERNAL);
   }
   if (is_fb) {
     if (i_fb < max_items) {
@@ -729,17 +816,27 @@ __global__ void __launch_bounds__(256) k_copy_segs(const Seg* segs, uint32_t S,
                                                    const uint32_t* range_base,
                                                    const uint64_t* __restrict__ src, uint64_t* dst,
                                                    const uint32_t* __restrict__ src_v,
-                                                   uint32_t* dst_v) {
+                                                   uint32_t* dst_v, uint32_t status_mask) {
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(range_base, S + 1, t) - 1;
   const Seg& g = segs[s];
-  if (g.status == SEG_BUCKET) return;
+  const bool sel = (status_mask & kCopyOneDigit) ? (g.status == SEG_BUCKET && g.b2 == 0)
+                                                 : ((status_mask >> g.status) & 1u) != 0;
+  if (!sel) return;
   const uint64_t base = g.off + (uint64_t)(t - range_base[s]) * kRangeTile;
   const uint64_t end = min(g.off + g.n, base + kRangeTile);
-  for (uint64_t i = base + threadIdx.x; i < end; i += 256) {
-    dst[i] = src[i];
-    if (dst_v) dst_v[i] = src_v[i];
+  uint64_t i = base + threadIdx.x;
+  for (; i + 3 * 256 < end; i += 4 * 256) {
+    const uint64_t a = ld_nc(src + i), b = ld_nc(src + i + 256), c = ld_nc(src + i + 512),
+                   d = ld_nc(src + i + 768);
+    dst[i] = a;
+    dst[i + 256] = b;
+    dst[i + 512] = c;
+    dst[i + 768] = d;
   }
+  for (; i < end; i += 256) dst[i] = src[i];
+  if (dst_v)
+    for (uint64_t q = base + threadIdx.x; q < end; q += 256) dst_v[q] = src_v[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -764,10 +861,20 @@ cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S) {
 }
 
 cudaError_t launch_sample(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
-                          uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool, uint32_t* done,
-                          Policy) {
+                          uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool) {
   if (!n_ctas) return cudaSuccess;
-  k_sample<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt, tpool, done);
+  k_sample<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt, tpool);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tpool,
+                         uint64_t pool_n, uint64_t* status_words, uint32_t* tile_counter,
+                         uint64_t spin_limit) {
+  cudaError_t e = launch_scan(c, tpool, pool_n, nullptr, status_words, tile_counter, 0xFFFFFFFFu,
+                              spin_limit, nullptr, true);
+  if (e) return e;
+  k_seg_base<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, tpool);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -784,7 +891,7 @@ cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const 
 
 cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const uint64_t* n_dev,
                         uint64_t* status_words, uint32_t* tile_counter, uint32_t withhold,
-                        uint64_t spin_limit, uint64_t* total_out) {
+                        uint64_t spin_limit, uint64_t* total_out, bool inclusive) {
   if (!n) return cudaSuccess;
   const uint32_t tiles = cdiv(n, kScanTile);
   cudaError_t e = cudaMemsetAsync(status_words, 0, (size_t)tiles * 8, c.stream);
@@ -792,7 +899,7 @@ cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const ui
   e = cudaMemsetAsync(tile_counter, 0, 4, c.stream);
   if (e) return e;
   k_scan<<<tiles, 256, 0, c.stream>>>(data, n, n_dev, status_words, tile_counter, withhold,
-                                      spin_limit, total_out, c.status);
+                                      spin_limit, total_out, c.status, inclusive ? 1 : 0);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -876,13 +983,20 @@ cudaError_t launch_scatter2(const LaunchCfg& c, const Group* groups, uint32_t n_
 }
 
 cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint64_t n_buckets,
-                           const uint64_t* bucket_base, const Group* groups, const uint32_t* cmat2,
-                           uint32_t leaf_cap, WorkItem* leaf, WorkItem* next, FbItem* fb,
-                           LevelOut* lo, uint32_t max_items) {
+                           const uint64_t* bucket_base, const Group* groups, const uint32_t* cmat1,
+                           const uint32_t* cmat2, bool two_pass, uint32_t leaf_cap, uint32_t tau,
+                           const uint64_t* X, const uint32_t* Xv, uint64_t* out_k, uint32_t* out_v,
+                           BRec* brec, WorkItem* next, FbItem* fb, LevelOut* lo,
+                           uint32_t max_items) {
   if (!n_buckets) return cudaSuccess;
-  k_buckets<<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(segs, S, n_buckets, bucket_base, groups,
-                                                        cmat2, leaf_cap, leaf, next, fb, lo,
-                                                        max_items, c.status);
+  if (c.pairs)
+    k_buckets<true><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
+        segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
+        c.kt, X, Xv, out_k, out_v, brec, next, fb, lo, max_items, c.status);
+  else
+    k_buckets<false><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
+        segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
+        c.kt, X, Xv, out_k, out_v, brec, next, fb, lo, max_items, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -897,9 +1011,11 @@ cudaError_t launch_seg_status_lists(const LaunchCfg& c, const Seg* segs, uint32_
 
 cudaError_t launch_copy_segs(const LaunchCfg& c, const Seg* segs, uint32_t S,
                              const uint32_t* range_base, uint32_t n_tiles, const uint64_t* src,
-                             uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v) {
+                             uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v,
+                             uint32_t status_mask) {
   if (!n_tiles) return cudaSuccess;
-  k_copy_segs<<<n_tiles, 256, 0, c.stream>>>(segs, S, range_base, src, dst, src_v, dst_v);
+  k_copy_segs<<<n_tiles, 256, 0, c.stream>>>(segs, S, range_base, src, dst, src_v, dst_v,
+                                             status_mask);
   count_launch(c);
   return cudaGetLastError();
 }
