@@ -68,7 +68,7 @@ struct pcf_ctx {
   int device = 0;
   int num_sms = 0;
   Policy policy{3, 3, 3, 3, 4, 0, 100};
-  pcf_tuning tuning{11, 15, 512, 2048};
+  pcf_tuning tuning{11, 14, 1024, 1024};
   std::string last_err;
   pcf_call_stats stats{};
   bool timing = false;
@@ -77,6 +77,7 @@ struct pcf_ctx {
   DevBuf tmp_k, tmp_v, tmp_aux, host_keys;
   DevBuf segs, bases, tpool, done, cmat1, cmat2, sw, groups, gtiles, gcent, gtot;
   DevBuf leaf, next, fb, lout, status, misc, fb_items, fb_bases, fb_lohi, small_items;
+  DevBuf segs_b, pcols, pbsums;  // the other level's plan, its count columns
   HostBuf h_stage, h_lout, h_status, h_items;
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
   uint64_t ptab_key = 0;  // policy/cap the table was built for
@@ -241,6 +242,46 @@ void plan_level(const Policy& P, const pcf_tuning& tu, ParamCache& pc,
   pl.n_groups = pl.group_base[S];
   pl.n_buckets = pl.bucket_base[S];
 }
+
+// A level's plan on the device (Seg rows and base arrays in one buffer) and
+// the totals the host needs to launch the level.
+struct PlanLayout {
+  size_t o_rb, o_k1, o_t1, o_gb, o_bb, bytes;
+};
+
+PlanLayout plan_layout(uint64_t rows) {
+  PlanLayout L;
+  L.o_rb = rows * sizeof(Seg);
+  L.o_k1 = L.o_rb + (rows + 1) * 4;
+  L.o_t1 = L.o_k1 + (rows + 1) * 4;
+  L.o_gb = (L.o_t1 + (rows + 1) * 4 + 7) & ~(size_t)7;
+  L.o_bb = L.o_gb + (rows + 1) * 8;
+  L.bytes = L.o_bb + (rows + 1) * 8;
+  return L;
+}
+
+DevPlan dev_plan(void* base, const PlanLayout& L) {
+  char* b = (char*)base;
+  DevPlan d;
+  d.segs = (Seg*)b;
+  d.rb = (uint32_t*)(b + L.o_rb);
+  d.k1 = (uint32_t*)(b + L.o_k1);
+  d.t1 = (uint32_t*)(b + L.o_t1);
+  d.gb = (uint64_t*)(b + L.o_gb);
+  d.bb = (uint64_t*)(b + L.o_bb);
+  return d;
+}
+
+struct LevelPlan {
+  uint32_t S = 0;
+  uint64_t n_level = 0, wb = 0, we = 0;  // keys, first offset, end
+  uint32_t n_range = 0, n_k1 = 0, n_t1 = 0;
+  uint64_t n_groups = 0, n_buckets = 0, tpool = 0, cmat1 = 0, cmat2_bound = 0,
+           tiles2_bound = 0;
+  uint32_t dmax1 = 1, dmax2 = 1;
+  bool two_pass = false;
+  DevPlan dp{};
+};
 
 struct LeafGeom {
   uint32_t tmax, gmax, warps, grid;
@@ -431,7 +472,6 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   // any) writes P2; X is where the level's buckets end.  On-chip buckets go
   // X -> out, next-level (sub)arrays stay in X, fallback buckets are sorted
   // from X into out.
-  std::vector<InSeg> level = big;
   CK(ensure(ctx->tmp_k, n_total * 8));
   CK(ensure(ctx->tmp_aux, n_total * 2));
   if (pairs) CK(ensure(ctx->tmp_v, n_total * 4));
@@ -439,44 +479,60 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   uint32_t* const tmp_v = pairs ? as<uint32_t>(ctx->tmp_v) : nullptr;
   const uint64_t* src = in_k;
   const uint32_t* src_v = in_v;
-  bool first = true;
-  while (!level.empty()) {
+  const uint32_t dbits = std::min(ctx->tuning.max_digit_bits, kMaxDigitBits);
+  // Level 0 is planned on the host (the caller's arrays); every later level
+  // is planned on the device by the level before it, in the other buffer.
+  DevBuf* pbuf[2] = {&ctx->segs, &ctx->segs_b};
+  int cur = 0;
+  LevelPlan L;
+  if (!big.empty()) {
     Plan pl;
-    plan_level(ctx->policy, ctx->tuning, ctx->pcache, level, pl);
-    const uint32_t S = (uint32_t)level.size();
-    uint64_t n_level = 0;
-    for (auto& s : level) n_level += s.n;
+    plan_level(ctx->policy, ctx->tuning, ctx->pcache, big, pl);
+    const uint32_t S = (uint32_t)big.size();
+    const PlanLayout PL = plan_layout(S);
+    CK(ensure_host(ctx->h_stage, PL.bytes));
+    CK(ensure(*pbuf[cur], PL.bytes));
+    char* hs = (char*)ctx->h_stage.p;
+    memcpy(hs, pl.segs.data(), S * sizeof(Seg));
+    memcpy(hs + PL.o_rb, pl.range_base.data(), (S + 1) * 4);
+    memcpy(hs + PL.o_k1, pl.k1_base.data(), (S + 1) * 4);
+    memcpy(hs + PL.o_t1, pl.tile1_base.data(), (S + 1) * 4);
+    memcpy(hs + PL.o_gb, pl.group_base.data(), (S + 1) * 8);
+    memcpy(hs + PL.o_bb, pl.bucket_base.data(), (S + 1) * 8);
+    CK(cudaMemcpyAsync(pbuf[cur]->p, hs, PL.bytes, cudaMemcpyHostToDevice, st));
+    L.S = S;
+    for (auto& sg : big) L.n_level += sg.n;
+    L.wb = big.front().off;
+    L.we = big.back().off + big.back().n;
+    L.n_range = pl.range_base[S];
+    L.n_k1 = pl.k1_base[S];
+    L.n_t1 = pl.tile1_base[S];
+    L.n_groups = pl.n_groups;
+    L.n_buckets = pl.n_buckets;
+    L.tpool = pl.tpool;
+    L.cmat1 = pl.cmat1;
+    L.cmat2_bound = pl.cmat2_bound;
+    L.tiles2_bound = pl.tiles2_bound;
+    L.dmax1 = pl.dmax1;
+    L.dmax2 = pl.dmax2;
+    L.two_pass = pl.two_pass;
+    L.dp = dev_plan(pbuf[cur]->p, PL);
+  }
+  bool first = true;
+  while (L.S) {
+    const uint32_t S = L.S;
+    const uint64_t n_level = L.n_level;
     ctx->stats.levels += 1;
     uint64_t* P1 = (src == tmp_k) ? out_k : tmp_k;
     uint32_t* P1v = (src == tmp_k) ? out_v : tmp_v;
     uint64_t* P2 = (P1 == tmp_k) ? out_k : tmp_k;
     uint32_t* P2v = (P1 == tmp_k) ? out_v : tmp_v;
-    uint64_t* X = pl.two_pass ? P2 : P1;
-    uint32_t* Xv = pl.two_pass ? P2v : P1v;
-    // upload plan: segs | range_base | k1_base | tile1_base | group_base | bucket_base
-    const size_t o_seg = 0, o_rb = o_seg + S * sizeof(Seg), o_k1 = o_rb + (S + 1) * 4,
-                 o_t1 = o_k1 + (S + 1) * 4, o_gb = ((o_t1 + (S + 1) * 4) + 7) & ~(size_t)7,
-                 o_bb = o_gb + (S + 1) * 8, need = o_bb + (S + 1) * 8;
-    CK(ensure_host(ctx->h_stage, need));
-    CK(ensure(ctx->segs, need));
-    char* hs = (char*)ctx->h_stage.p;
-    memcpy(hs + o_seg, pl.segs.data(), S * sizeof(Seg));
-    memcpy(hs + o_rb, pl.range_base.data(), (S + 1) * 4);
-    memcpy(hs + o_k1, pl.k1_base.data(), (S + 1) * 4);
-    memcpy(hs + o_t1, pl.tile1_base.data(), (S + 1) * 4);
-    memcpy(hs + o_gb, pl.group_base.data(), (S + 1) * 8);
-    memcpy(hs + o_bb, pl.bucket_base.data(), (S + 1) * 8);
-    CK(cudaMemcpyAsync(ctx->segs.p, hs, need, cudaMemcpyHostToDevice, st));
-    char* ds = (char*)ctx->segs.p;
-    Seg* d_segs = (Seg*)(ds + o_seg);
-    const uint32_t* d_rb = (const uint32_t*)(ds + o_rb);
-    const uint32_t* d_k1 = (const uint32_t*)(ds + o_k1);
-    const uint32_t* d_t1 = (const uint32_t*)(ds + o_t1);
-    const uint64_t* d_gb = (const uint64_t*)(ds + o_gb);
-    const uint64_t* d_bb = (const uint64_t*)(ds + o_bb);
+    uint64_t* X = L.two_pass ? P2 : P1;
+    uint32_t* Xv = L.two_pass ? P2v : P1v;
+    Seg* d_segs = L.dp.segs;
 
     // range, model
-    CK(launch_range(lc, d_segs, S, d_rb, pl.range_base[S], src, first && kt == KEY_F64));
+    CK(launch_range(lc, d_segs, S, L.dp.rb, L.n_range, src, first && kt == KEY_F64));
     if (first && kt == KEY_F64) {
       CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -491,30 +547,31 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     // (sub)arrays with one value are final; degenerate ones join the
     // fallback list, whose keys are taken from X
     if (src != out_k)
-      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], src, out_k, src_v, out_v,
+      CK(launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, src, out_k, src_v, out_v,
                           1u << SEG_SINGLE));
     if (src != X)
-      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], src, X, src_v, Xv,
+      CK(launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, src, X, src_v, Xv,
                           1u << SEG_DEGEN));
     // lists
-    const uint64_t max_items = std::max<uint64_t>(pl.n_buckets, S) + 16;
+    const uint64_t max_items = std::max<uint64_t>(L.n_buckets, S) + 16;
     CK(ensure(ctx->leaf, max_items * sizeof(BRec)));
-    CK(ensure(ctx->next, max_items * sizeof(WorkItem)));
+    CK(ensure(ctx->next, max_items * 4));
     CK(ensure(ctx->fb, max_items * sizeof(FbItem)));
     LevelOut* d_lo = as<LevelOut>(ctx->lout);
     CK(cudaMemsetAsync(d_lo, 0, sizeof(LevelOut), st));
     CK(launch_seg_status_lists(lc, d_segs, S, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
     // sample + PCF: counts per bin, then b by one inclusive scan of the pool
-    CK(ensure(ctx->tpool, pl.tpool * 4));
-    CK(cudaMemsetAsync(ctx->tpool.p, 0, pl.tpool * 4, st));
-    const uint64_t sw_need = ((std::max(std::max(pl.cmat1, pl.cmat2_bound), pl.tpool) +
-                               kScanTile - 1) / kScanTile +
-                              (pl.n_groups + kScanTile - 1) / kScanTile + 8) * 8;
+    CK(ensure(ctx->tpool, L.tpool * 4));
+    CK(cudaMemsetAsync(ctx->tpool.p, 0, L.tpool * 4, st));
+    const uint64_t scan_max =
+        std::max(std::max(L.cmat1, L.cmat2_bound), std::max(L.tpool, L.n_buckets));
+    const uint64_t sw_need = ((scan_max + kScanTile - 1) / kScanTile +
+                              (L.n_groups + kScanTile - 1) / kScanTile + 8) * 8;
     CK(ensure(ctx->sw, sw_need));
     uint32_t* tile_counter = as<uint32_t>(ctx->misc);
     uint64_t* totals = (uint64_t*)((char*)ctx->misc.p + 64);
-    CK(launch_sample(lc, d_segs, S, d_k1, pl.k1_base[S], src, as<uint32_t>(ctx->tpool)));
-    CK(launch_table(lc, d_segs, S, as<uint32_t>(ctx->tpool), pl.tpool, as<uint64_t>(ctx->sw),
+    CK(launch_sample(lc, d_segs, S, L.dp.k1, L.n_k1, src, as<uint32_t>(ctx->tpool)));
+    CK(launch_table(lc, d_segs, S, as<uint32_t>(ctx->tpool), L.tpool, as<uint64_t>(ctx->sw),
                     tile_counter, spin_limit));
     tm.mark(1);
     // pass 1
@@ -526,63 +583,76 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     kb.tmp_aux = as<uint16_t>(ctx->tmp_aux);
     kb.out = P2;
     kb.out_v = P2v;
-    CK(ensure(ctx->cmat1, pl.cmat1 * 4));
-    CK(cudaMemsetAsync(ctx->cmat1.p, 0, pl.cmat1 * 4, st));
-    CK(launch_hist1(lc, d_segs, S, d_t1, pl.tile1_base[S], tile_keys, src,
-                    as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1));
-    CK(launch_scan(lc, as<uint32_t>(ctx->cmat1), pl.cmat1, nullptr, as<uint64_t>(ctx->sw),
+    CK(ensure(ctx->cmat1, L.cmat1 * 4));
+    CK(cudaMemsetAsync(ctx->cmat1.p, 0, L.cmat1 * 4, st));
+    CK(launch_hist1(lc, d_segs, S, L.dp.t1, L.n_t1, tile_keys, src, as<uint32_t>(ctx->tpool),
+                    as<uint32_t>(ctx->cmat1), L.dmax1));
+    CK(launch_scan(lc, as<uint32_t>(ctx->cmat1), L.cmat1, nullptr, as<uint64_t>(ctx->sw),
                    tile_counter, scan_withhold, spin_limit, nullptr));
     tm.mark(2);
-    CK(launch_scatter1(lc, d_segs, S, d_t1, pl.tile1_base[S], tile_keys, kb,
-                       as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1));
+    CK(launch_scatter1(lc, d_segs, S, L.dp.t1, L.n_t1, tile_keys, kb, as<uint32_t>(ctx->tpool),
+                       as<uint32_t>(ctx->cmat1), L.dmax1));
     tm.mark(3);
     ctx->stats.global_passes += 1;
     ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 /*hist1*/ + 8 + 10 /*scatter1*/) +
                               (pairs ? n_level * 8 : 0);
     // pass 2
-    if (pl.two_pass) {
-      CK(ensure(ctx->groups, pl.n_groups * sizeof(Group)));
-      CK(ensure(ctx->gtiles, pl.n_groups * 4));
-      CK(ensure(ctx->gcent, pl.n_groups * 4));
-      CK(launch_groups(lc, d_segs, S, d_gb, pl.n_groups, as<uint32_t>(ctx->cmat1), tile_keys,
+    if (L.two_pass) {
+      CK(ensure(ctx->groups, L.n_groups * sizeof(Group)));
+      CK(ensure(ctx->gtiles, L.n_groups * 4));
+      CK(ensure(ctx->gcent, L.n_groups * 4));
+      CK(launch_groups(lc, d_segs, S, L.dp.gb, L.n_groups, as<uint32_t>(ctx->cmat1), tile_keys,
                        as<Group>(ctx->groups), as<uint32_t>(ctx->gtiles),
                        as<uint32_t>(ctx->gcent)));
-      CK(launch_scan(lc, as<uint32_t>(ctx->gtiles), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
+      CK(launch_scan(lc, as<uint32_t>(ctx->gtiles), L.n_groups, nullptr, as<uint64_t>(ctx->sw),
                      tile_counter, 0xFFFFFFFFu, spin_limit, &totals[0]));
-      CK(launch_scan(lc, as<uint32_t>(ctx->gcent), pl.n_groups, nullptr, as<uint64_t>(ctx->sw),
+      CK(launch_scan(lc, as<uint32_t>(ctx->gcent), L.n_groups, nullptr, as<uint64_t>(ctx->sw),
                      tile_counter, 0xFFFFFFFFu, spin_limit, &totals[1]));
-      CK(launch_group_bases(lc, as<Group>(ctx->groups), pl.n_groups, as<uint32_t>(ctx->gcent)));
-      CK(ensure(ctx->cmat2, pl.cmat2_bound * 4));
-      CK(cudaMemsetAsync(ctx->cmat2.p, 0, pl.cmat2_bound * 4, st));
-      CK(launch_hist2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
-                      as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound, tile_keys,
-                      kb.tmp_aux, as<uint32_t>(ctx->cmat2), pl.dmax2));
-      CK(launch_scan(lc, as<uint32_t>(ctx->cmat2), pl.cmat2_bound, &totals[1],
+      CK(launch_group_bases(lc, as<Group>(ctx->groups), L.n_groups, as<uint32_t>(ctx->gcent)));
+      CK(ensure(ctx->cmat2, L.cmat2_bound * 4));
+      CK(cudaMemsetAsync(ctx->cmat2.p, 0, L.cmat2_bound * 4, st));
+      CK(launch_hist2(lc, as<Group>(ctx->groups), (uint32_t)L.n_groups, d_segs,
+                      as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)L.tiles2_bound, tile_keys,
+                      kb.tmp_aux, as<uint32_t>(ctx->cmat2), L.dmax2));
+      CK(launch_scan(lc, as<uint32_t>(ctx->cmat2), L.cmat2_bound, &totals[1],
                      as<uint64_t>(ctx->sw), tile_counter, 0xFFFFFFFFu, spin_limit, nullptr));
       tm.mark(4);
-      CK(launch_scatter2(lc, as<Group>(ctx->groups), (uint32_t)pl.n_groups, d_segs,
-                         as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)pl.tiles2_bound,
-                         tile_keys, kb, as<uint32_t>(ctx->cmat2), pl.dmax2));
+      CK(launch_scatter2(lc, as<Group>(ctx->groups), (uint32_t)L.n_groups, d_segs,
+                         as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)L.tiles2_bound,
+                         tile_keys, kb, as<uint32_t>(ctx->cmat2), L.dmax2));
       // segments whose bucket id has one digit were already bucketed by pass 1
-      CK(launch_copy_segs(lc, d_segs, S, d_rb, pl.range_base[S], P1, P2, P1v, P2v,
-                          kCopyOneDigit));
+      CK(launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, P1, P2, P1v, P2v, kCopyOneDigit));
       tm.mark(5);
       ctx->stats.global_passes += 1;
       ctx->stats.bytes_moved += n_level * (2 /*hist2*/ + 10 + 8 /*scatter2*/) +
                                 (pairs ? n_level * 8 : 0);
     }
     // buckets: Alg. 1's per-bucket decision, then the on-chip finish
-    CK(launch_buckets(lc, d_segs, S, pl.n_buckets, d_bb, as<Group>(ctx->groups),
-                      as<uint32_t>(ctx->cmat1), as<uint32_t>(ctx->cmat2), pl.two_pass, cap,
+    uint32_t* next_flag = as<uint32_t>(ctx->next);
+    CK(launch_buckets(lc, d_segs, S, L.n_buckets, L.dp.bb, as<Group>(ctx->groups),
+                      as<uint32_t>(ctx->cmat1), as<uint32_t>(ctx->cmat2), L.two_pass, cap,
                       (uint32_t)ctx->policy.tau, X, Xv, out_k, out_v, as<BRec>(ctx->leaf),
-                      as<WorkItem>(ctx->next), as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
+                      next_flag, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
     {
-      const uint64_t wb = level.front().off, span = level.back().off + level.back().n - wb;
+      const uint64_t span = L.we - L.wb;
       CK(ensure(ctx->gtot, ((span + window - 1) / window + 2) * 4));
-      CK(launch_chunk(lc, as<BRec>(ctx->leaf), (uint32_t)pl.n_buckets, wb, span, window, cap, X,
+      CK(launch_chunk(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, L.wb, span, window, cap, X,
                       Xv, out_k, out_v, ctx->policy, ptab, as<uint32_t>(ctx->gtot)));
     }
     tm.mark(6);
+    // the next level's plan, built on the device into the other buffer; a
+    // next-level (sub)array holds more than cap keys, which bounds its rows
+    const uint64_t s_max = std::min<uint64_t>(L.n_buckets, n_level / (cap + 1)) + 1;
+    const PlanLayout NL = plan_layout(s_max);
+    CK(ensure(*pbuf[cur ^ 1], NL.bytes));
+    const DevPlan ndp = dev_plan(pbuf[cur ^ 1]->p, NL);
+    const uint32_t ncb = (uint32_t)((s_max + 2047) / 2048);
+    CK(ensure(ctx->pcols, (size_t)PC_NCOL * s_max * 4));
+    CK(ensure(ctx->pbsums, (size_t)PC_NCOL * ncb * 4));
+    CK(launch_plan_next(lc, as<BRec>(ctx->leaf), next_flag, L.n_buckets, (uint32_t)s_max,
+                        ctx->policy, dbits, tile_keys, ndp, as<uint32_t>(ctx->pcols),
+                        as<uint32_t>(ctx->pbsums), d_lo, as<uint64_t>(ctx->sw), tile_counter,
+                        spin_limit, &totals[2]));
     CK(cudaMemcpyAsync(ctx->h_lout.p, d_lo, sizeof(LevelOut), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -592,7 +662,6 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     if (stw & STATUS_INTERNAL) return PCF_ERR_INTERNAL;
     ctx->stats.leaf_buckets += lo.n_leaf;
     // standard sort of the large failure-guard / degenerate buckets
-    std::vector<InSeg> nextl;
     if (lo.n_fb) {
       const uint32_t nf = lo.n_fb;
       std::vector<FbItem> items(nf);
@@ -629,16 +698,30 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       CK(cudaStreamSynchronize(st));
       tm.mark(7);
     }
-    if (lo.n_next) {
-      std::vector<WorkItem> items(lo.n_next);
-      CK(cudaMemcpy(items.data(), ctx->next.p, lo.n_next * sizeof(WorkItem),
-                    cudaMemcpyDeviceToHost));
-      nextl.reserve(lo.n_next);
-      for (auto& it : items) nextl.push_back(InSeg{it.off, it.n, it.start, it.seed, it.depth});
-      std::sort(nextl.begin(), nextl.end(),
-                [](const InSeg& a, const InSeg& b) { return a.off < b.off; });
+    // the next level
+    const PlanTotals& pt = lo.plan;
+    LevelPlan N;
+    N.S = pt.S;
+    if (N.S) {
+      N.n_level = pt.n_keys;
+      N.wb = pt.lo;
+      N.we = pt.hi;
+      N.n_range = (uint32_t)pt.col[PC_RANGE];
+      N.n_k1 = (uint32_t)pt.col[PC_K1];
+      N.n_t1 = (uint32_t)pt.col[PC_TILES1];
+      N.n_groups = pt.col[PC_GROUPS];
+      N.n_buckets = pt.col[PC_BUCKETS];
+      N.tpool = pt.col[PC_TPOOL];
+      N.cmat1 = pt.col[PC_CMAT1];
+      N.cmat2_bound = pt.col[PC_CMAT2];
+      N.tiles2_bound = pt.col[PC_TILES2];
+      N.dmax1 = std::max(1u, pt.dmax1);
+      N.dmax2 = std::max(1u, pt.dmax2);
+      N.two_pass = pt.two_pass != 0;
+      N.dp = ndp;
     }
-    level.swap(nextl);
+    L = N;
+    cur ^= 1;
     src = X;
     src_v = Xv;
     first = false;

@@ -82,6 +82,39 @@ struct FbItem {
   uint64_t n;
 };
 
+// Device-side plan of the next level: one row per (sub)array, these count
+// columns, scanned into bases.
+enum : uint32_t {
+  PC_RANGE = 0,  // range tiles
+  PC_K1,         // sample CTAs
+  PC_TILES1,     // pass-1 count tiles
+  PC_GROUPS,     // pass-1 groups
+  PC_BUCKETS,    // gamma + 1
+  PC_TPOOL,      // beta + 1
+  PC_CMAT1,      // pass-1 count entries
+  PC_CMAT2,      // pass-2 count entries (bound)
+  PC_TILES2,     // pass-2 tiles (bound)
+  PC_NCOL
+};
+
+struct PlanTotals {
+  uint64_t col[PC_NCOL];  // column totals
+  uint64_t n_keys;        // sum of n
+  uint64_t lo, hi;        // smallest offset, largest end
+  uint32_t S;             // (sub)arrays
+  uint32_t dmax1, dmax2, two_pass;
+};
+
+// Where a level's plan lives on the device.
+struct DevPlan {
+  Seg* segs;
+  uint32_t* rb;  // range tile bases [S+1]
+  uint32_t* k1;  // sample CTA bases [S+1]
+  uint32_t* t1;  // pass-1 tile bases [S+1]
+  uint64_t* gb;  // group bases [S+1]
+  uint64_t* bb;  // bucket bases [S+1]
+};
+
 // Counters written by k_buckets.
 struct LevelOut {
   uint32_t n_leaf;
@@ -91,6 +124,7 @@ struct LevelOut {
   uint64_t leaf_keys, next_keys, fb_keys;
   uint32_t max_fb_n;  // largest standard-sort bucket (sizes the merge passes)
   uint32_t leaf_cursor; // work counter of the leaf kernel
+  PlanTotals plan;    // the next level's plan (device-built)
 };
 
 struct KeyBufs {
@@ -162,8 +196,16 @@ cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint
                            const uint64_t* bucket_base, const Group* groups,
                            const uint32_t* cmat1, const uint32_t* cmat2, bool two_pass,
                            uint32_t leaf_cap, uint32_t tau, const uint64_t* X, const uint32_t* Xv,
-                           uint64_t* out_k, uint32_t* out_v, BRec* brec, WorkItem* next,
+                           uint64_t* out_k, uint32_t* out_v, BRec* brec, uint32_t* next_flag,
                            FbItem* fb, LevelOut* lo, uint32_t max_items);
+// builds the next level's plan from the flagged buckets (next_flag[B] = 1
+// for a bucket of the next level; scanned in place), s_max rows at most;
+// n_flagged receives the number of (sub)arrays
+cudaError_t launch_plan_next(const LaunchCfg& c, const BRec* brec, uint32_t* next_flag,
+                             uint64_t n_buckets, uint32_t s_max, Policy P, uint32_t dbits,
+                             uint32_t tile_keys, const DevPlan& out, uint32_t* cols,
+                             uint32_t* block_sums, LevelOut* lo, uint64_t* sw,
+                             uint32_t* tile_counter, uint64_t spin_limit, uint64_t* n_flagged);
 cudaError_t launch_seg_status_lists(const LaunchCfg& c, const Seg* segs, uint32_t S,
                                     FbItem* fb, LevelOut* lo, uint32_t max_items);
 // copies the segments whose status is in status_mask (bit per SEG_*), or,

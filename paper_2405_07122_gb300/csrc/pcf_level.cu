@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
                                                  uint32_t leaf_cap, uint32_t tau, uint32_t kt,
                                                  const uint64_t* __restrict__ X,
                                                  const uint32_t* __restrict__ Xv, uint64_t* out_k,
-                                                 uint32_t* out_v, BRec* brec, WorkItem* next,
+                                                 uint32_t* out_v, BRec* brec, uint32_t* next_flag,
                                                  FbItem* fb, LevelOut* lo, uint32_t max_items,
                                                  uint32_t* status) {
   // [kTiny][256] (transposed: thread t owns column t, so accesses are
@@ -769,20 +769,12 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     r.seed = sg ? sg->seed : 0ull;
     brec[B] = r;
   }
+  if (in) next_flag[B] = is_next ? 1u : 0u;
   const uint32_t i_leaf = warp_append(&lo->n_leaf, is_leaf);
   (void)i_leaf;
   const uint32_t i_next = warp_append(&lo->n_next, is_next);
+  (void)i_next;
   const uint32_t i_fb = warp_append(&lo->n_fb, is_fb);
-  if (is_next) {
-    WorkItem it;
-    it.off = off;
-    it.start = sg->start + (off - sg->off);
-    it.seed = sg->seed;
-    it.n = size;
-    it.depth = sg->depth + 1;
-    if (i_next < max_items) next[i_next] = it;
-    else atomicOr(status, STATUS_INTERNAL);
-  }
   if (is_fb) {
     if (i_fb < max_items) {
       fb[i_fb].off = off;
@@ -793,6 +785,168 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     }
   }
 }
+
+// ---------------------------------------------------------------------------
+// Device-side plan of the next level.  Every bucket flagged "next" (larger
+// than the on-chip kernel takes, below delta) is one Learned-Sort call of the
+// next level (Alg. 1).  An exclusive scan of the flags numbers them in bucket
+// order, which is memory order, so the next level's (sub)arrays need no sort;
+// a thread per flagged bucket writes its Seg and its per-segment counts, and
+// a column scan of the counts gives every base the level's kernels read.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bits_of_dev(uint32_t v) { return v ? 32u - __clz(v) : 0u; }
+
+__global__ void k_next_segs(const BRec* __restrict__ brec, const uint32_t* __restrict__ pos,
+                            const uint64_t* __restrict__ n_flagged, uint64_t n_buckets, Policy P,
+                            uint32_t dbits, uint32_t tile_keys, Seg* nsegs, uint32_t* cols,
+                            uint32_t s_max, LevelOut* lo, uint32_t* status) {
+  const uint64_t B = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (B >= n_buckets) return;
+  const uint32_t s = pos[B];
+  const uint32_t s_end = B + 1 < n_buckets ? pos[B + 1] : (uint32_t)*n_flagged;
+  if (s_end == s) return;
+  if (s >= s_max) {
+    atomicOr(status, STATUS_INTERNAL);
+    return;
+  }
+  const BRec r = brec[B];
+  Seg g;
+  memset(&g, 0, sizeof g);
+  g.off = r.off;
+  g.n = r.n;
+  g.start = r.start;
+  g.seed = r.seed;
+  g.depth = r.depth;
+  const Params pr = params_of(P, r.n);
+  g.alpha = pr.alpha;
+  g.beta = pr.beta;
+  g.gamma = pr.gamma;
+  g.delta = pr.delta;
+  // bucket-id digits as on the host: one digit when it fits, else the low
+  // digit as wide as allowed
+  const uint32_t jb = max(1u, bits_of_dev(pr.gamma));
+  uint32_t b1 = jb;
+  if (jb > dbits) {
+    const uint32_t b2 = min(dbits, jb - 1);
+    b1 = min(jb - b2, kMaxDigitBits);
+    atomicOr(&lo->plan.two_pass, 1u);
+  }
+  g.b1 = b1;
+  g.b2 = jb - b1;
+  g.tiles1 = (uint32_t)((r.n + tile_keys - 1) / tile_keys);
+  g.ord_lo = ~0ull;
+  g.ord_hi = 0;
+  g.status = SEG_BUCKET;
+  nsegs[s] = g;
+  const uint32_t ng = g.b2 ? (1u << g.b1) : 1u;
+  cols[PC_RANGE * s_max + s] = (r.n + kRangeTile - 1) / kRangeTile;
+  cols[PC_K1 * s_max + s] = (pr.alpha + kSamplesPerCta - 1) / kSamplesPerCta;
+  cols[PC_TILES1 * s_max + s] = g.tiles1;
+  cols[PC_GROUPS * s_max + s] = ng;
+  cols[PC_BUCKETS * s_max + s] = pr.gamma + 1;
+  cols[PC_TPOOL * s_max + s] = pr.beta + 1;
+  cols[PC_CMAT1 * s_max + s] = g.tiles1 << g.b1;
+  cols[PC_CMAT2 * s_max + s] = (g.tiles1 + ng) << g.b2;
+  cols[PC_TILES2 * s_max + s] = g.tiles1 + ng;
+  atomicMax(&lo->plan.dmax1, 1u << g.b1);
+  atomicMax(&lo->plan.dmax2, 1u << g.b2);
+  atomicAdd((unsigned long long*)&lo->plan.n_keys, (unsigned long long)r.n);
+}
+
+// Exclusive scan of the PC_NCOL count columns over the S rows: per-block
+// sums, a scan of the block sums, then the rows.
+constexpr uint32_t kColRows = 2048;
+
+__global__ void __launch_bounds__(256) k_cols_reduce(const uint32_t* __restrict__ cols,
+                                                     uint32_t s_max, const uint64_t* n_rows,
+                                                     uint32_t* block_sums, uint32_t n_blocks) {
+  const uint32_t S = (uint32_t)(*n_rows < s_max ? *n_rows : (uint64_t)s_max);
+  const uint32_t r0 = blockIdx.x * kColRows, r1 = min(S, r0 + kColRows);
+  __shared__ uint32_t sh8[8];
+  for (uint32_t c = 0; c < PC_NCOL; ++c) {
+    uint32_t sum = 0;
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += 256) sum += cols[c * s_max + r];
+    uint32_t tot;
+    block_excl_scan256(sum, sh8, &tot);
+    if (threadIdx.x == 0) block_sums[c * n_blocks + blockIdx.x] = tot;
+  }
+}
+
+// One warp per column scans the block sums (exclusive, in place); the
+// totals and the end entries [S] of the base arrays are written here.
+__global__ void __launch_bounds__(32 * PC_NCOL) k_cols_scan(uint32_t* block_sums,
+                                                            uint32_t n_blocks,
+                                                            const uint64_t* n_rows,
+                                                            uint32_t s_max, const Seg* nsegs,
+                                                            DevPlan dp, LevelOut* lo) {
+  const uint32_t c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t S = (uint32_t)(*n_rows < s_max ? *n_rows : (uint64_t)s_max);
+  uint64_t carry = 0;
+  for (uint32_t b0 = 0; b0 < n_blocks; b0 += 32) {
+    const uint32_t b = b0 + lane;
+    const uint32_t v = b < n_blocks ? block_sums[c * n_blocks + b] : 0u;
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(~0u, inc, d);
+      if (lane >= (uint32_t)d) inc += u;
+    }
+    if (b < n_blocks) block_sums[c * n_blocks + b] = (uint32_t)carry + inc - v;
+    carry += __shfl_sync(~0u, inc, 31);
+  }
+  if (lane != 0) return;
+  lo->plan.col[c] = carry;
+  if (c == PC_RANGE) dp.rb[S] = (uint32_t)carry;
+  if (c == PC_K1) dp.k1[S] = (uint32_t)carry;
+  if (c == PC_TILES1) dp.t1[S] = (uint32_t)carry;
+  if (c == PC_GROUPS) dp.gb[S] = carry;
+  if (c == PC_BUCKETS) dp.bb[S] = carry;
+  if (c == 0) {
+    lo->plan.S = S;
+    lo->plan.lo = S ? nsegs[0].off : 0;
+    lo->plan.hi = S ? nsegs[S - 1].off + nsegs[S - 1].n : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_cols_apply(const uint32_t* __restrict__ cols,
+                                                    uint32_t s_max, const uint64_t* n_rows,
+                                                    const uint32_t* __restrict__ block_sums,
+                                                    uint32_t n_blocks, DevPlan dp) {
+  const uint32_t S = (uint32_t)(*n_rows < s_max ? *n_rows : (uint64_t)s_max);
+  const uint32_t r0 = blockIdx.x * kColRows, r1 = min(S, r0 + kColRows);
+  __shared__ uint32_t sh8[8];
+  constexpr uint32_t kPer = kColRows / 256;  // rows per thread, consecutive
+  for (uint32_t c = 0; c < PC_TILES2; ++c) {
+    if (c == PC_CMAT2) continue;
+    uint32_t v[kPer], sum = 0;
+    const uint32_t rt = r0 + threadIdx.x * kPer;
+#pragma unroll
+    for (uint32_t i = 0; i < kPer; ++i) {
+      v[i] = rt + i < r1 ? cols[c * s_max + rt + i] : 0u;
+      sum += v[i];
+    }
+    uint32_t tot;
+    uint32_t run = block_sums[c * n_blocks + blockIdx.x] + block_excl_scan256(sum, sh8, &tot);
+#pragma unroll
+    for (uint32_t i = 0; i < kPer; ++i) {
+      const uint32_t r = rt + i;
+      if (r < r1) {
+        switch (c) {
+          case PC_RANGE: dp.rb[r] = run; break;
+          case PC_K1: dp.k1[r] = run; break;
+          case PC_TILES1: dp.t1[r] = run; break;
+          case PC_GROUPS: dp.gb[r] = run; dp.segs[r].group_base = run; break;
+          case PC_BUCKETS: dp.bb[r] = run; dp.segs[r].bucket_base = run; break;
+          case PC_TPOOL: dp.segs[r].T_off = run; break;
+          case PC_CMAT1: dp.segs[r].cbase1 = run; break;
+          default: break;
+        }
+      }
+      run += v[i];
+    }
+  }
+}
+
 
 // Segments whose range is degenerate go to the standard sort as a whole.
 __global__ void k_seg_status_lists(const Seg* segs, uint32_t S, FbItem* fb, LevelOut* lo,
@@ -986,17 +1140,17 @@ cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint
                            const uint64_t* bucket_base, const Group* groups, const uint32_t* cmat1,
                            const uint32_t* cmat2, bool two_pass, uint32_t leaf_cap, uint32_t tau,
                            const uint64_t* X, const uint32_t* Xv, uint64_t* out_k, uint32_t* out_v,
-                           BRec* brec, WorkItem* next, FbItem* fb, LevelOut* lo,
+                           BRec* brec, uint32_t* next_flag, FbItem* fb, LevelOut* lo,
                            uint32_t max_items) {
   if (!n_buckets) return cudaSuccess;
   if (c.pairs)
     k_buckets<true><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
         segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
-        c.kt, X, Xv, out_k, out_v, brec, next, fb, lo, max_items, c.status);
+        c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, c.status);
   else
     k_buckets<false><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
         segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
-        c.kt, X, Xv, out_k, out_v, brec, next, fb, lo, max_items, c.status);
+        c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1016,6 +1170,29 @@ cudaError_t launch_copy_segs(const LaunchCfg& c, const Seg* segs, uint32_t S,
   if (!n_tiles) return cudaSuccess;
   k_copy_segs<<<n_tiles, 256, 0, c.stream>>>(segs, S, range_base, src, dst, src_v, dst_v,
                                              status_mask);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan_next(const LaunchCfg& c, const BRec* brec, uint32_t* next_flag,
+                             uint64_t n_buckets, uint32_t s_max, Policy P, uint32_t dbits,
+                             uint32_t tile_keys, const DevPlan& out, uint32_t* cols,
+                             uint32_t* block_sums, LevelOut* lo, uint64_t* sw,
+                             uint32_t* tile_counter, uint64_t spin_limit, uint64_t* n_flagged) {
+  if (!n_buckets) return cudaSuccess;
+  cudaError_t e = launch_scan(c, next_flag, n_buckets, nullptr, sw, tile_counter, 0xFFFFFFFFu,
+                              spin_limit, n_flagged);
+  if (e) return e;
+  k_next_segs<<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(brec, next_flag, n_flagged, n_buckets,
+                                                          P, dbits, tile_keys, out.segs, cols,
+                                                          s_max, lo, c.status);
+  count_launch(c);
+  const uint32_t nb = cdiv(s_max, kColRows);
+  k_cols_reduce<<<nb, 256, 0, c.stream>>>(cols, s_max, n_flagged, block_sums, nb);
+  count_launch(c);
+  k_cols_scan<<<1, 32 * PC_NCOL, 0, c.stream>>>(block_sums, nb, n_flagged, s_max, out.segs, out, lo);
+  count_launch(c);
+  k_cols_apply<<<nb, 256, 0, c.stream>>>(cols, s_max, n_flagged, block_sums, nb, out);
   count_launch(c);
   return cudaGetLastError();
 }
