@@ -75,7 +75,7 @@ typedef struct {
  * leaf_cap = the largest bucket finished on chip (64..1024, power of two);
  * onchip_window = keys of the windows in which on-chip buckets are grouped
  * per thread block (1024..8192, power of two).  Zero fields keep the
- * current value. */
+ * current value.  Default: {11, 14, 1024, 1024}. */
 typedef struct {
   uint32_t max_digit_bits;
   uint32_t tile_log2;
@@ -131,6 +131,35 @@ pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_
                               void* d_keys_out, uint32_t* d_vals_out,
                               const uint64_t* h_offsets, uint32_t S, pcf_key_type kt,
                               uint64_t seed, void* stream);
+
+/* Allocation-free batched sort of small arrays (keys only; the paper has no
+ * counterpart: it is an interface for callers that must not allocate device
+ * memory during a call -- cudaMalloc/cudaFree synchronise the whole device,
+ * and memory held by a caching allocator or an engine may be exhausted).
+ *
+ * Sorts S arrays of at most PCF_STATIC_MAX_ARRAY_KEYS keys each, exactly as
+ * pcf_sort_segmented would with the default policy and seed + s for array s.
+ * d_offsets: S+1 non-decreasing u64 DEVICE values, d_offsets[0] = 0,
+ * d_offsets[S] = n_total (checked on the device).  In-place when
+ * d_keys_in == d_keys_out.  Runs on the calling thread's current device.
+ *
+ * Scratch: one fixed device array of the library (about 2.1 MB per device),
+ * its address resolved by cudaGetSymbolAddress on the first call on each
+ * device; make that first call before any stream capture on the device.
+ * Calls no allocating CUDA or library function.  All calls on a device share
+ * the scratch: calls in flight at the same time on one device race and give
+ * undefined results -- serialise them.
+ *
+ * Errors: PCF_ERR_INVALID_ARG when S > PCF_STATIC_MAX_ARRAYS, n_total >
+ * PCF_STATIC_MAX_KEYS, an array longer than PCF_STATIC_MAX_ARRAY_KEYS or
+ * offsets that break the rules above (nothing written); PCF_ERR_INVALID_KEY
+ * on a NaN key (nothing written).  Returns when the sort is complete. */
+#define PCF_STATIC_MAX_ARRAY_KEYS 1024u
+#define PCF_STATIC_MAX_ARRAYS 65536u
+#define PCF_STATIC_MAX_KEYS (1u << 22)
+pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_keys_out,
+                                     const uint64_t* d_offsets, uint32_t S, uint64_t n_total,
+                                     pcf_key_type kt, uint64_t seed, void* stream);
 
 /* End-to-end form on HOST buffers: copies h_keys (n keys, ideally pinned)
  * to the device, sorts, and copies the result back into h_keys. */

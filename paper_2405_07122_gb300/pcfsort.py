@@ -77,6 +77,7 @@ def lib():
             "pcf_sort_segmented": [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_u64), _u32,
                                    ctypes.c_int, _u64, _vp],
             "pcf_sort_keys_host": [_vp, _vp, _u64, ctypes.c_int, _u64, _vp],
+            "pcf_sort_segmented_static": [_vp, _vp, _vp, _u32, _u64, ctypes.c_int, _u64, _vp],
             "pcf_debug_scan": [_vp, _vp, _u64, _u32, _u64, _vp],
             "pcf_debug_level0": [_vp, _vp, _u64, ctypes.c_int, _u64, ctypes.POINTER(_u64),
                                  ctypes.POINTER(_u32), _u64],
@@ -246,6 +247,26 @@ def bins_host(kt, lo_bits, hi_bits, beta, xs_bits):
     rc = lib().pcf_debug_bins_host(kt, lo_bits, hi_bits, beta, xs.ctypes.data, xs.size,
                                    out.ctypes.data, fast.ctypes.data)
     return None if rc else (out, fast)
+
+
+STATIC_MAX_ARRAY_KEYS = 1024
+STATIC_MAX_ARRAYS = 65536
+STATIC_MAX_KEYS = 1 << 22
+
+
+def sort_segmented_static(keys_in, offsets_dev, n_total, keys_out=None, key_type=None, seed=0,
+                          stream=None):
+    """pcf_sort_segmented_static: allocation-free sort of S small arrays.
+    offsets_dev: CUDA int64/uint64 tensor of S+1 boundaries; n_total = its
+    last value.  Calls on one device must not overlap."""
+    kt = _kt(key_type or ("f64" if str(keys_in.dtype) == "torch.float64" else "u64"))
+    ko = keys_in if keys_out is None else keys_out
+    rc = lib().pcf_sort_segmented_static(keys_in.data_ptr(), ko.data_ptr(),
+                                         offsets_dev.data_ptr(), offsets_dev.numel() - 1,
+                                         n_total, kt, seed, _stream_ptr(stream))
+    if rc:
+        raise PcfError(rc)
+    return ko
 
 
 def root_floor_host(n, p, q):
