@@ -143,7 +143,7 @@ pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_
  * d_offsets[S] = n_total (checked on the device).  In-place when
  * d_keys_in == d_keys_out.  Runs on the calling thread's current device.
  *
- * Scratch: one fixed device array of the library (about 2.1 MB per device),
+ * Scratch: one fixed device array of the library (about 2.9 MB per device),
  * its address resolved by cudaGetSymbolAddress on the first call on each
  * device; make that first call before any stream capture on the device.
  * Calls no allocating CUDA or library function.  All calls on a device share

@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(256) k_chunk(const BRec* __restrict__ br,
         amb |= (uint32_t)am << u;
       }
       if (amb) {
-#pragma unroll 1
+#pragma unroll
         for (int u = 0; u < 4; ++u)
           if ((amb >> u) & 1u) bn[u] = bin_exact_of(sm.act[a[u]].bm, x[u]);
       }

@@ -78,6 +78,7 @@ struct pcf_ctx {
   DevBuf segs, bases, tpool, done, cmat1, cmat2, sw, groups, gtiles, gcent, gtot;
   DevBuf leaf, next, fb, lout, status, misc, fb_items, fb_bases, fb_lohi, small_items;
   DevBuf segs_b, pcols, pbsums;  // the other level's plan, its count columns
+  DevBuf olist;                  // on-chip buckets listed by size class
   HostBuf h_stage, h_lout, h_status, h_items;
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
   uint64_t ptab_key = 0;  // policy/cap the table was built for
@@ -430,7 +431,6 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
 
   // ---- level 0 of the small arrays: straight to the shared-memory kernel,
   // launched once the NaN check of every key has passed
-  const uint32_t window = ctx->tuning.onchip_window;
   auto launch_small = [&]() -> pcf_status {
     if (small.empty()) return PCF_OK;
     const uint32_t S = (uint32_t)small.size();
@@ -449,10 +449,10 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     memcpy(ctx->h_items.p, recs.data(), S * sizeof(BRec));
     CK(cudaMemcpyAsync(ctx->small_items.p, ctx->h_items.p, S * sizeof(BRec),
                        cudaMemcpyHostToDevice, st));
-    const uint64_t wb = small.front().off, span = small.back().off + small.back().n - wb;
-    CK(ensure(ctx->gtot, ((span + window - 1) / window + 2) * 4));
-    CK(launch_chunk(lc, as<BRec>(ctx->small_items), S, wb, span, window, cap, in_k, in_v, out_k,
-                    out_v, ctx->policy, ptab, as<uint32_t>(ctx->gtot)));
+    CK(ensure(ctx->olist, (size_t)S * 12));
+    CK(launch_onchip(lc, as<BRec>(ctx->small_items), S, cap, in_k, in_v, out_k, out_v,
+                     ctx->policy, ptab, as<uint32_t>(ctx->olist),
+                     (uint32_t*)((char*)ctx->misc.p + 128)));
     ctx->stats.leaf_buckets += S;
     return PCF_OK;
   };
@@ -633,12 +633,10 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                       as<uint32_t>(ctx->cmat1), as<uint32_t>(ctx->cmat2), L.two_pass, cap,
                       (uint32_t)ctx->policy.tau, X, Xv, out_k, out_v, as<BRec>(ctx->leaf),
                       next_flag, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
-    {
-      const uint64_t span = L.we - L.wb;
-      CK(ensure(ctx->gtot, ((span + window - 1) / window + 2) * 4));
-      CK(launch_chunk(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, L.wb, span, window, cap, X,
-                      Xv, out_k, out_v, ctx->policy, ptab, as<uint32_t>(ctx->gtot)));
-    }
+    CK(ensure(ctx->olist, (size_t)L.n_buckets * 12));
+    CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k, out_v,
+                     ctx->policy, ptab, as<uint32_t>(ctx->olist),
+                     (uint32_t*)((char*)ctx->misc.p + 128)));
     tm.mark(6);
     // the next level's plan, built on the device into the other buffer; a
     // next-level (sub)array holds more than cap keys, which bounds its rows
@@ -805,7 +803,7 @@ pcf_status pcf_ctx_set_tuning(pcf_ctx* ctx, const pcf_tuning* t) {
       (n.onchip_window & (n.onchip_window - 1)))
     return PCF_ERR_INVALID_ARG;
   // the on-chip window (keys, values and tables) must fit one block's shared memory
-  if (chunk_smem_bytes(n.onchip_window, n.leaf_cap, ctx->policy, true) > 227 * 1024)
+  if (onchip_smem_bytes(n.leaf_cap, ctx->policy, true) > 227 * 1024)
     return PCF_ERR_INVALID_ARG;
   ctx->tuning = n;
   return PCF_OK;

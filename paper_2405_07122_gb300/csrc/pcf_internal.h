@@ -228,6 +228,21 @@ cudaError_t launch_chunk(const LaunchCfg& c, const BRec* br, uint32_t nb, uint64
                          const uint32_t* Xv, uint64_t* out, uint32_t* out_v, Policy P,
                          const uint16_t* ptab, uint32_t* first_scratch);
 size_t chunk_smem_bytes(uint32_t window, uint32_t leaf_cap, const Policy& P, bool pairs);
+// on-chip finish, one warp per bucket: every BK_LEAF record of br[0..nb)
+// (any order), keys X -> out at the record's offset
+struct OnchipGeo {
+  uint32_t capw;   // keys of a warp's slice (the largest bucket it takes)
+  uint32_t tmax;   // beta + 1 bound
+  uint32_t kmax;   // gamma + 1 bound
+  uint32_t smax;   // pending calls per warp
+  uint32_t bytes;  // shared memory of one warp's slice
+};
+OnchipGeo onchip_geometry(uint32_t capw, const Policy& P, bool pairs);
+size_t onchip_smem_bytes(uint32_t capw, const Policy& P, bool pairs);
+// lists: 3 nb u32 of scratch; counts: 3 u32 of scratch
+cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
+                          const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
+                          Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts);
 cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                             const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
                             uint64_t* ord_lohi);

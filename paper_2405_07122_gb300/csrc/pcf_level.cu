@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
         amb |= (uint32_t)a << u;
       }
       if (amb) {
-#pragma unroll 1
+#pragma unroll
         for (int u = 0; u < U; ++u)
           if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
       }
@@ -439,7 +439,7 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
         amb |= (uint32_t)a << k;
       }
       if (amb) {
-#pragma unroll 1
+#pragma unroll
         for (int k = 0; k < kItems; ++k)
           if ((amb >> k) & 1u) dig[k] = bin_exact_of(bm, key[k]);
       }

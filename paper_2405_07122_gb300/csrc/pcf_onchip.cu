@@ -1,0 +1,627 @@
+// pcf_onchip.cu -- buckets finished on chip, one warp per bucket.
+//
+// Every bucket of a global level that fits on chip is one call of
+// Learned-Sort (Algorithm 1 of Sato & Matsui, TMLR 2025, with the PCF model
+// of Sec. 3.3).  A warp takes a bucket, stages its keys in the warp's slice
+// of shared memory (as order-preserving integers), and runs the recursion
+// there with warp-synchronous code -- no block barriers, so the 30-40 warps
+// of an SM overlap each other's latencies:
+//   - Learned-Sort step: range (warp reduction), the model (lane 0; the
+//     binary64 division runs in one lane), alpha samples with replacement
+//     counted per bin (Sec. 3.3), b_k by a warp scan and the bucket table
+//     floor(b_k gamma / alpha), the bucket of every key, the bucket sizes and
+//     starts, and the Append into buckets (stable for key-value sorts);
+//   - Alg. 1's decision for every new bucket: Standard-Sort when |c| >= delta
+//     or |c| < tau, else a further Learned-Sort step (pushed on a per-warp
+//     stack of pending calls);
+//   - Standard-Sort: a new bucket of at most 32 keys by ranking each of its
+//     keys among the bucket's; a whole call by ranking (at most 16 keys, or
+//     32 for key-value sorts), a bitonic network across the warp's registers
+//     (keys only, at most 256) or a merge sort (key-value, stable).
+// The leaf records are first listed by size class; the warps of a launch
+// take the buckets of one class in turn (the class's slice size bounds the
+// keys of a bucket; three classes up to 1024 keys).
+#include "pcf_internal.h"
+
+namespace pcf {
+
+namespace onchip {
+
+constexpr uint32_t kWarps = 4;   // independent warps per CTA
+constexpr uint32_t kRank = 32;     // key-value Standard-Sorts up to this size rank each key
+constexpr uint32_t kRankKeys = 16; // ... keys-only ones (a bitonic network above)
+
+struct Item {  // a pending call on [o, o + n) of the warp's buffers
+  uint16_t o, n;
+  uint16_t depth, std;  // std: 1 = Standard-Sort, 0 = Learned-Sort
+  uint64_t start;       // offset inside the caller's array (keys the samples)
+};
+
+// Layout of one warp's slice.
+struct Slice {
+  uint64_t* A;   // [capw] keys (total-order integers); calls finish here
+  uint64_t* B;   // [capw] scatter target / merge scratch
+  uint32_t* Av;  // [capw] values (key-value sorts)
+  uint32_t* Bv;
+  BinModel* bm;  // the current call's model (written by lane 0)
+  Item* stk;     // [smax] pending calls
+  uint32_t* tab; // [tmax] bin counts -> bucket table
+  uint32_t* cnt; // [kmax] bucket sizes
+  uint32_t* cur; // [kmax] bucket starts, then ends
+  uint16_t* J;   // [capw] bucket of each source position
+  uint16_t* Bj;  // [capw] bucket of each target position
+};
+
+__host__ __device__ inline size_t slice_bytes(const OnchipGeo& g, bool pairs) {
+  size_t b = (size_t)g.capw * 16 + (pairs ? (size_t)g.capw * 8 : 0);
+  b += (sizeof(BinModel) + 15) & ~(size_t)15;
+  b += (size_t)g.smax * sizeof(Item);
+  b += (size_t)g.tmax * 4 + (size_t)g.kmax * 8 + (size_t)g.capw * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+__device__ inline Slice carve(uint8_t* p, const OnchipGeo& g, bool pairs) {
+  Slice s;
+  s.A = (uint64_t*)p;
+  p += (size_t)g.capw * 8;
+  s.B = (uint64_t*)p;
+  p += (size_t)g.capw * 8;
+  s.Av = s.Bv = nullptr;
+  if (pairs) {
+    s.Av = (uint32_t*)p;
+    p += (size_t)g.capw * 4;
+    s.Bv = (uint32_t*)p;
+    p += (size_t)g.capw * 4;
+  }
+  s.bm = (BinModel*)p;
+  p += (sizeof(BinModel) + 15) & ~(size_t)15;
+  s.stk = (Item*)p;
+  p += (size_t)g.smax * sizeof(Item);
+  s.tab = (uint32_t*)p;
+  p += (size_t)g.tmax * 4;
+  s.cnt = (uint32_t*)p;
+  p += (size_t)g.kmax * 4;
+  s.cur = (uint32_t*)p;
+  p += (size_t)g.kmax * 4;
+  s.J = (uint16_t*)p;
+  p += (size_t)g.capw * 2;
+  s.Bj = (uint16_t*)p;
+  return s;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt_() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t wscan(uint32_t v, uint32_t lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t u = __shfl_up_sync(~0u, v, d);
+    if (lane >= (uint32_t)d) v += u;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+  return (uint64_t)__shfl_sync(~0u, (unsigned long long)v, src);
+}
+
+// ---------------------------------------------------------------------------
+// Standard-Sorts (R7: any sort; the output is the unique sorted order)
+// ---------------------------------------------------------------------------
+
+// Rank of key v at position p among positions [s, e) of K: keys before p
+// that are <= v, and keys after p that are < v (equal keys keep their order).
+__device__ __forceinline__ uint32_t rank_in(const uint64_t* K, uint32_t s, uint32_t e, uint32_t p,
+                                            uint64_t v) {
+  uint32_t r = 0;
+  uint32_t t = s;
+#pragma unroll 4
+  for (; t < p; ++t) r += K[t] <= v ? 1u : 0u;
+#pragma unroll 4
+  for (t = p + 1; t < e; ++t) r += K[t] < v ? 1u : 0u;
+  return r;
+}
+
+// [o, o + c) of A ranked into B, then copied back; c <= kRank * 32.  Ties are
+// broken by position, so equal keys keep their order (stable).
+template <bool PAIRS>
+__device__ void rank_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) {
+  for (uint32_t p0 = 0; p0 < c; p0 += 32) {
+    const uint32_t p = p0 + lane;
+    if (p < c) {
+      const uint64_t v = w.A[o + p];
+      const uint32_t r = rank_in(w.A + o, 0, c, p, v);
+      w.B[o + r] = v;
+      if (PAIRS) w.Bv[o + r] = w.Av[o + p];
+    }
+  }
+  __syncwarp();
+  for (uint32_t p = lane; p < c; p += 32) {
+    w.A[o + p] = w.B[o + p];
+    if (PAIRS) w.Av[o + p] = w.Bv[o + p];
+  }
+  __syncwarp();
+}
+
+// Bitonic network over 32 E slots (keys only): element i = lane * E + e;
+// the padding (all ones) sorts last and is not written back.  The stage
+// loops run at run time (a fully unrolled network overflows the
+// instruction cache once several kernels' warps interleave).
+template <int E>
+__device__ __forceinline__ void bitonic_intra(uint64_t (&v)[E], uint32_t lane, uint32_t k,
+                                              uint32_t j) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int f = e ^ (int)j;
+    if (f > e) {
+      const bool up = ((lane * E + e) & k) == 0;
+      const uint64_t a = v[e], b = v[f];
+      const bool sw = up ? (a > b) : (a < b);
+      v[e] = sw ? b : a;
+      v[f] = sw ? a : b;
+    }
+  }
+}
+
+template <int E>
+__device__ void bitonic_sort(uint64_t* A, uint32_t o, uint32_t c, uint32_t lane) {
+  uint64_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = lane * E + e;
+    v[e] = i < c ? A[o + i] : ~0ull;
+  }
+  constexpr uint32_t P = 32u * E;
+#pragma unroll 1
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+#pragma unroll 1
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      if (j >= (uint32_t)E) {
+        const uint32_t lj = j / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t i = lane * E + e;
+          const uint64_t other = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)v[e], lj);
+          const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+          v[e] = keep_min ? (other < v[e] ? other : v[e]) : (other > v[e] ? other : v[e]);
+        }
+      } else if (j == 1) {
+        bitonic_intra<E>(v, lane, k, 1);
+      } else if (j == 2) {
+        if (E > 2) bitonic_intra<E>(v, lane, k, 2);
+      } else {
+        if (E > 4) bitonic_intra<E>(v, lane, k, 4);
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = lane * E + e;
+    if (i < c) A[o + i] = v[e];
+  }
+  __syncwarp();
+}
+
+// merge-path split of the first k outputs of merge(L, R) (ties: left first)
+__device__ __forceinline__ uint32_t mpath(const uint64_t* L, uint32_t nL, const uint64_t* R,
+                                          uint32_t nR, uint32_t k) {
+  uint32_t lo = k > nR ? k - nR : 0u, hi = min(k, nL);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (L[mid] <= R[k - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// stable merge sort of A[o, o + c) by the warp (B as scratch): runs of
+// ceil(c/32) keys by insertion in one lane each, then merge rounds
+template <bool PAIRS>
+__device__ void merge_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) {
+  uint64_t* A = w.A;
+  uint64_t* B = w.B;
+  uint32_t* Av = w.Av;
+  uint32_t* Bv = w.Bv;
+  const uint32_t r = (c + 31) / 32;
+  {
+    const uint32_t a = min(c, lane * r), b = min(c, a + r);
+    for (uint32_t i = a + 1; i < b; ++i) {
+      const uint64_t key = A[o + i];
+      const uint32_t val = PAIRS ? Av[o + i] : 0u;
+      uint32_t j = i;
+      while (j > a && A[o + j - 1] > key) {
+        A[o + j] = A[o + j - 1];
+        if (PAIRS) Av[o + j] = Av[o + j - 1];
+        --j;
+      }
+      A[o + j] = key;
+      if (PAIRS) Av[o + j] = val;
+    }
+  }
+  __syncwarp();
+  for (uint32_t wd = r; wd < c; wd *= 2) {
+    const uint32_t a0 = min(c, lane * r), b0 = min(c, a0 + r);
+    uint32_t a = a0;
+    while (a < b0) {
+      const uint32_t p0 = (a / (2 * wd)) * (2 * wd);
+      const uint32_t pe = min(c, p0 + 2 * wd);
+      const uint32_t nL = min(wd, c - p0), nR = pe - p0 - nL;
+      const uint64_t* L = A + o + p0;
+      const uint64_t* R = L + nL;
+      const uint32_t e = min(b0, pe);
+      const uint32_t k = a - p0;
+      uint32_t i = mpath(L, nL, R, nR, k), j = k - i;
+      for (uint32_t q = a; q < e; ++q) {
+        const bool takeL = j >= nR || (i < nL && L[i] <= R[j]);
+        if (takeL) {
+          B[o + q] = L[i];
+          if (PAIRS) Bv[o + q] = Av[o + p0 + i];
+          ++i;
+        } else {
+          B[o + q] = R[j];
+          if (PAIRS) Bv[o + q] = Av[o + p0 + nL + j];
+          ++j;
+        }
+      }
+      a = e;
+    }
+    __syncwarp();
+    for (uint32_t q = lane; q < c; q += 32) {
+      A[o + q] = B[o + q];
+      if (PAIRS) Av[o + q] = Bv[o + q];
+    }
+    __syncwarp();
+  }
+}
+
+template <bool PAIRS>
+__device__ void std_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) {
+  if (c <= 1) return;
+  if (c <= (PAIRS ? kRank : kRankKeys)) {
+    rank_sort<PAIRS>(w, o, c, lane);
+  } else if (PAIRS || c > 256) {
+    merge_sort<PAIRS>(w, o, c, lane);
+  } else if (c <= 32) {
+    bitonic_sort<1>(w.A, o, c, lane);
+  } else if (c <= 64) {
+    bitonic_sort<2>(w.A, o, c, lane);
+  } else if (c <= 128) {
+    bitonic_sort<4>(w.A, o, c, lane);
+  } else {
+    bitonic_sort<8>(w.A, o, c, lane);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One Learned-Sort step on [o, o + n) (Algorithm 1, Sec. 3.3).  New buckets
+// are finished here (ranked) when small, else pushed.  Returns false when
+// the per-warp stack would overflow.
+// ---------------------------------------------------------------------------
+template <bool PAIRS>
+__device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
+                           uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
+                           uint32_t& top, uint32_t lane) {
+  const uint32_t o = it.o, n = it.n;
+  // range
+  uint64_t mn = ~0ull, mx = 0ull;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint64_t v = w.A[o + i];
+    mn = v < mn ? v : mn;
+    mx = v > mx ? v : mx;
+  }
+#pragma unroll
+  for (int d = 16; d; d >>= 1) {
+    const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+    const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+    mn = a < mn ? a : mn;
+    mx = b > mx ? b : mx;
+  }
+  if (mn == mx) return true;  // one value: sorted
+  const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
+  const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
+  int degen = 0;
+  if (lane == 0) degen = make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
+  degen = __shfl_sync(~0u, degen, 0);
+  if (degen) {  // R5: a degenerate range goes to Standard-Sort
+    std_sort<PAIRS>(w, o, n, lane);
+    return true;
+  }
+  for (uint32_t k = lane; k <= beta; k += 32) w.tab[k] = 0;
+  for (uint32_t k = lane; k <= gamma; k += 32) w.cnt[k] = 0;
+  __syncwarp();
+  const BinModel bm = *w.bm;
+  // training: alpha samples with replacement, counted per bin
+  const uint64_t state = sample_state(seed, it.depth, it.start, n);
+  for (uint32_t s = lane; s < alpha; s += 32) {
+    const uint32_t idx = (uint32_t)sample_index(state, s, n);
+    const uint64_t x = bits_of_ord(w.A[o + idx], kt);
+    bool amb;
+    uint32_t bn = bin_fast(bm, x, amb);
+    if (amb) bn = bin_exact_of(bm, x);
+    atomicAdd(&w.tab[bn], 1u);
+  }
+  __syncwarp();
+  // b_k and the bucket table
+  {
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 <= beta; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const uint32_t v = k <= beta ? w.tab[k] : 0u;
+      const uint32_t inc = wscan(v, lane) + carry;
+      if (k <= beta) w.tab[k] = bucket_of_count(inc, alpha, gamma);
+      carry = __shfl_sync(~0u, inc, 31);
+    }
+  }
+  __syncwarp();
+  // the bucket of every key, and the bucket sizes
+  for (uint32_t i0 = 0; i0 < n; i0 += 128) {
+    uint64_t x[4];
+    uint32_t bn[4], amb = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + u * 32 + lane;
+      x[u] = i < n ? bits_of_ord(w.A[o + i], kt) : bm.lo_bits;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      bool a;
+      bn[u] = bin_fast(bm, x[u], a);
+      amb |= (uint32_t)a << u;
+    }
+    if (amb) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + u * 32 + lane;
+      if (i < n) {
+        const uint32_t j = w.tab[bn[u]];
+        w.J[i] = (uint16_t)j;
+        atomicAdd(&w.cnt[j], 1u);
+      }
+    }
+  }
+  __syncwarp();
+  // bucket starts
+  {
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 <= gamma; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const uint32_t v = k <= gamma ? w.cnt[k] : 0u;
+      const uint32_t inc = wscan(v, lane) + carry;
+      if (k <= gamma) w.cur[k] = inc - v;
+      carry = __shfl_sync(~0u, inc, 31);
+    }
+  }
+  __syncwarp();
+  // Append: A -> B by bucket (in input order for key-value sorts)
+  if (!PAIRS) {
+    for (uint32_t i = lane; i < n; i += 32) {
+      const uint32_t j = w.J[i];
+      const uint32_t pos = atomicAdd(&w.cur[j], 1u);
+      w.B[o + pos] = w.A[o + i];
+      w.Bj[pos] = (uint16_t)j;
+    }
+  } else {
+    const uint32_t lm = lanemask_lt_();
+    for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool v = i < n;
+      const uint32_t j = v ? w.J[i] : 0xFFFFFFFFu;
+      const uint32_t peers = __match_any_sync(~0u, j);
+      const int leader = __ffs(peers) - 1;
+      uint32_t prior = 0;
+      if (v && (int)lane == leader) prior = atomicAdd(&w.cur[j], (uint32_t)__popc(peers));
+      prior = __shfl_sync(~0u, prior, leader);
+      if (v) {
+        const uint32_t pos = prior + __popc(peers & lm);
+        w.B[o + pos] = w.A[o + i];
+        w.Bv[o + pos] = w.Av[o + i];
+        w.Bj[pos] = (uint16_t)j;
+      }
+    }
+  }
+  __syncwarp();
+  // Alg. 1 for every new bucket c (cur[j] now holds its end): ranked here
+  // when a Standard-Sort of at most kRank keys, else copied back and pushed
+  const uint32_t lm = lanemask_lt_();
+  bool ok = true;
+  for (uint32_t p0 = 0; p0 < n; p0 += 32) {
+    const uint32_t p = p0 + lane;
+    bool push = false;
+    Item ch;
+    if (p < n) {
+      const uint32_t j = w.Bj[p];
+      const uint32_t c = w.cnt[j], e = w.cur[j], s = e - c;
+      const uint64_t v = w.B[o + p];
+      const bool stdc = c >= delta || c < P.tau;
+      if (c == 1) {
+        w.A[o + p] = v;
+        if (PAIRS) w.Av[o + p] = w.Bv[o + p];
+      } else if (stdc && c <= kRank) {
+        const uint32_t r = rank_in(w.B + o, s, e, p, v);
+        w.A[o + s + r] = v;
+        if (PAIRS) w.Av[o + s + r] = w.Bv[o + p];
+      } else {
+        w.A[o + p] = v;
+        if (PAIRS) w.Av[o + p] = w.Bv[o + p];
+        if (p == s) {
+          push = true;
+          ch.o = (uint16_t)(o + s);
+          ch.n = (uint16_t)c;
+          ch.depth = (uint16_t)(it.depth + 1);
+          ch.std = stdc ? 1 : 0;
+          ch.start = it.start + s;
+        }
+      }
+    }
+    const uint32_t bal = __ballot_sync(~0u, push);
+    if (push) {
+      const uint32_t slot = top + __popc(bal & lm);
+      if (slot < geo.smax) w.stk[slot] = ch;
+    }
+    top += __popc(bal);
+    if (top > geo.smax) ok = false;
+  }
+  __syncwarp();
+  return ok;
+}
+
+// The leaf records of each size class, compacted (a thread per record).
+constexpr uint32_t kClasses = 3;
+__global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t b1, uint32_t b2,
+                             uint32_t* lists, uint32_t* counts) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t cls = kClasses;
+  if (i < nb) {
+    const BRec r = br[i];
+    if ((r.kind & BK_LEAF) && r.n > 0) cls = r.n <= b1 ? 0u : (r.n <= b2 ? 1u : 2u);
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < kClasses; ++k) {
+    const uint32_t bal = __ballot_sync(~0u, cls == k);
+    if (!bal) continue;
+    const int leader = __ffs(bal) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(&counts[k], (uint32_t)__popc(bal));
+    base = __shfl_sync(~0u, base, leader);
+    if (cls == k) lists[(size_t)k * nb + base + __popc(bal & lanemask_lt_())] = i;
+  }
+}
+
+template <bool PAIRS>
+__global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restrict__ br,
+                                                           const uint32_t* __restrict__ list,
+                                                           const uint32_t* __restrict__ count,
+                                                           OnchipGeo geo,
+                                                           const uint64_t* __restrict__ X,
+                                                           const uint32_t* __restrict__ Xv,
+                                                           uint64_t* out, uint32_t* out_v,
+                                                           uint32_t kt, Policy P,
+                                                           const uint16_t* __restrict__ ptab,
+                                                           uint32_t* status) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const Slice w = carve(smem_raw + (size_t)wib * slice_bytes(geo, PAIRS), geo, PAIRS);
+  const uint32_t gw = blockIdx.x * kWarps + wib, nw = gridDim.x * kWarps;
+  const uint32_t nitems = *count;
+  for (uint32_t li = gw; li < nitems; li += nw) {
+    const BRec r = br[list[li]];
+    const uint32_t off = r.off, n = r.n;
+    for (uint32_t i = lane; i < n; i += 32) {
+      w.A[i] = ord_of(__ldg(X + off + i), kt);
+      if (PAIRS) w.Av[i] = __ldg(Xv + off + i);
+    }
+    __syncwarp();
+    bool ok = true;
+    if (r.kind & BK_STD) {
+      std_sort<PAIRS>(w, 0, n, lane);
+    } else {
+      uint32_t top = 1;
+      if (lane == 0) {
+        Item it;
+        it.o = 0;
+        it.n = (uint16_t)n;
+        it.depth = (uint16_t)r.depth;
+        it.std = 0;
+        it.start = r.start;
+        w.stk[0] = it;
+      }
+      __syncwarp();
+      while (top > 0 && ok) {
+        --top;
+        const Item it = w.stk[top];
+        __syncwarp();
+        if (it.std) std_sort<PAIRS>(w, it.o, it.n, lane);
+        else ok = learn_step<PAIRS>(w, geo, it, r.seed, kt, P, ptab, top, lane);
+      }
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(status, STATUS_INTERNAL);
+      return;
+    }
+    for (uint32_t i = lane; i < n; i += 32) {
+      out[off + i] = bits_of_ord(w.A[i], kt);
+      if (PAIRS) out_v[off + i] = w.Av[i];
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace onchip
+
+using namespace onchip;
+
+OnchipGeo onchip_geometry(uint32_t capw, const Policy& P, bool pairs) {
+  OnchipGeo g;
+  g.capw = capw;
+  // floor(n^(p/q)) does not decrease with n: the largest call bounds all
+  const Params pr = params_of(P, capw);
+  g.tmax = (max(2u, pr.beta + 1) + 3) & ~3u;
+  g.kmax = (max(2u, pr.gamma + 1) + 3) & ~3u;
+  g.smax = capw / 16 + 4;
+  g.bytes = (uint32_t)slice_bytes(g, pairs);
+  return g;
+}
+
+size_t onchip_smem_bytes(uint32_t capw, const Policy& P, bool pairs) {
+  return (size_t)kWarps * onchip_geometry(capw, P, pairs).bytes;
+}
+
+static int num_sms_of_current_device() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 148;
+  }
+  return cached[dev];
+}
+
+cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
+                          const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
+                          Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts) {
+  if (!nb) return cudaSuccess;
+  // size classes (0, 256], (256, 512], (512, 1024], clipped to leaf_cap
+  cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kClasses, c.stream);
+  if (e) return e;
+  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, 256, 512, lists, counts);
+  count_launch(c);
+  if ((e = cudaGetLastError())) return e;
+  uint32_t cls = 0;
+  for (uint32_t capw = 256, lo = 0; lo < leaf_cap; capw *= 2, ++cls) {
+    const uint32_t hi = min(capw, leaf_cap);
+    const OnchipGeo g = onchip_geometry(hi, P, c.pairs);
+    const size_t sm = (size_t)kWarps * g.bytes;
+    const uint32_t per_sm = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm + 1024u))));
+    const uint32_t grid = (uint32_t)num_sms_of_current_device() * per_sm;
+    const uint32_t* list = lists + (size_t)cls * nb;
+    if (c.pairs) {
+      if ((e = cudaFuncSetAttribute(k_onchip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      k_onchip<true><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv, out,
+                                                         out_v, c.kt, P, ptab, c.status);
+    } else {
+      if ((e = cudaFuncSetAttribute(k_onchip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm)))
+        return e;
+      k_onchip<false><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv,
+                                                          out, out_v, c.kt, P, ptab, c.status);
+    }
+    count_launch(c);
+    if ((e = cudaGetLastError())) return e;
+    lo = hi;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace pcf

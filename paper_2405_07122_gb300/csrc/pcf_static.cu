@@ -8,9 +8,8 @@
 // memory is held by a caching allocator or reserved up front by an engine may
 // have no memory left to give.  For those callers this entry point runs the
 // on-chip path of the library (every array short enough to be finished in
-// shared memory, Algorithm 1 with the Sec. 3.3 model inside one thread-block
-// window) with all of its scratch in one file-scope device array of fixed
-// size.  It calls no allocating CUDA or library function.
+// shared memory, Algorithm 1 with the Sec. 3.3 model run by one warp) with
+// all of its scratch in one file-scope device array of fixed size.  It calls no allocating CUDA or library function.
 //
 // All calls on a device share that array: two calls in flight at the same
 // time on one device (two streams, two host threads) race on it and their
@@ -31,14 +30,12 @@ namespace {
 constexpr uint32_t kStCap = 1024;           // keys per array
 constexpr uint32_t kStMaxSegs = 65536;      // arrays per call
 constexpr uint64_t kStMaxKeys = 1ull << 22; // keys per call
-constexpr uint32_t kStWindow = 2048;        // keys per on-chip window
-constexpr uint32_t kStFirst = (uint32_t)(kStMaxKeys / kStWindow) + 2;
 
 // Layout of the scratch array.
 constexpr size_t kOffBrec = 0;                                      // BRec[kStMaxSegs]
-constexpr size_t kOffFirst = kOffBrec + sizeof(BRec) * kStMaxSegs;  // u32[kStFirst]
-constexpr size_t kOffPtab = (kOffFirst + 4 * kStFirst + 255) & ~(size_t)255;  // u16[4 (cap+1)]
-constexpr size_t kOffStatus = (kOffPtab + 8 * (kStCap + 1) + 255) & ~(size_t)255;  // u32[64]
+constexpr size_t kOffLists = (kOffBrec + sizeof(BRec) * kStMaxSegs + 255) & ~(size_t)255;  // u32[3 S]
+constexpr size_t kOffPtab = (kOffLists + 12 * (size_t)kStMaxSegs + 255) & ~(size_t)255;  // u16[4 (cap+1)]
+constexpr size_t kOffStatus = (kOffPtab + 8 * (kStCap + 1) + 255) & ~(size_t)255;  // u32[64]: status, class counts
 constexpr size_t kStBytes = kOffStatus + 256;
 
 // Extra status bit of this entry point: an offset check failed on the device.
@@ -123,14 +120,15 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
   if (g_addr_err[dev] != cudaSuccess) return PCF_ERR_CUDA;
   unsigned char* base = (unsigned char*)g_addr[dev];
   BRec* brec = (BRec*)(base + kOffBrec);
-  uint32_t* first = (uint32_t*)(base + kOffFirst);
   uint16_t* ptab = (uint16_t*)(base + kOffPtab);
   uint32_t* status = (uint32_t*)(base + kOffStatus);
+  uint32_t* lists = (uint32_t*)(base + kOffLists);
   cudaStream_t st = (cudaStream_t)stream;
   const Policy P{3, 3, 3, 3, 4, 0, 100};  // the default policy (Sec. 4)
 
-  // the status word is the only scratch that must start at zero; records,
-  // table and window starts are fully written before they are read
+  // the status word is the only scratch that must start at zero here (the
+  // class counts are cleared by the on-chip launch itself); the records,
+  // lists and table are fully written before they are read
   if (cudaMemsetAsync(status, 0, 4, st) != cudaSuccess) return PCF_ERR_CUDA;
   const uint64_t work = std::max<uint64_t>(std::max<uint64_t>(S, kStCap + 1), n_total / 8);
   const uint32_t grid = (uint32_t)std::min<uint64_t>((work + 255) / 256, 1024);
@@ -152,8 +150,8 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
   lc.pairs = false;
   lc.status = status;
   lc.launches = nullptr;
-  if (launch_chunk(lc, brec, S, 0, n_total, kStWindow, kStCap, (const uint64_t*)d_keys_in,
-                   nullptr, (uint64_t*)d_keys_out, nullptr, P, ptab, first) != cudaSuccess)
+  if (launch_onchip(lc, brec, S, kStCap, (const uint64_t*)d_keys_in, nullptr,
+                    (uint64_t*)d_keys_out, nullptr, P, ptab, lists, status + 16) != cudaSuccess)
     return PCF_ERR_CUDA;
   if (cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
