@@ -79,6 +79,7 @@ struct pcf_ctx {
   DevBuf leaf, next, fb, lout, status, misc, fb_items, fb_bases, fb_lohi, small_items;
   DevBuf segs_b, pcols, pbsums;  // the other level's plan, its count columns
   DevBuf olist;                  // on-chip buckets listed by size class
+  DevBuf jbuf;                   // bucket id of every key of a level
   HostBuf h_stage, h_lout, h_status, h_items;
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
   uint64_t ptab_key = 0;  // policy/cap the table was built for
@@ -474,6 +475,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   // from X into out.
   CK(ensure(ctx->tmp_k, n_total * 8));
   CK(ensure(ctx->tmp_aux, n_total * 2));
+  CK(ensure(ctx->jbuf, n_total * 4));
   if (pairs) CK(ensure(ctx->tmp_v, n_total * 4));
   uint64_t* const tmp_k = as<uint64_t>(ctx->tmp_k);
   uint32_t* const tmp_v = pairs ? as<uint32_t>(ctx->tmp_v) : nullptr;
@@ -581,12 +583,13 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     kb.tmp = P1;
     kb.tmp_v = P1v;
     kb.tmp_aux = as<uint16_t>(ctx->tmp_aux);
+    kb.jbuf = as<uint32_t>(ctx->jbuf);
     kb.out = P2;
     kb.out_v = P2v;
     CK(ensure(ctx->cmat1, L.cmat1 * 4));
     CK(cudaMemsetAsync(ctx->cmat1.p, 0, L.cmat1 * 4, st));
     CK(launch_hist1(lc, d_segs, S, L.dp.t1, L.n_t1, tile_keys, src, as<uint32_t>(ctx->tpool),
-                    as<uint32_t>(ctx->cmat1), L.dmax1));
+                    as<uint32_t>(ctx->cmat1), L.dmax1, as<uint32_t>(ctx->jbuf)));
     CK(launch_scan(lc, as<uint32_t>(ctx->cmat1), L.cmat1, nullptr, as<uint64_t>(ctx->sw),
                    tile_counter, scan_withhold, spin_limit, nullptr));
     tm.mark(2);
@@ -820,6 +823,7 @@ pcf_status pcf_ctx_reserve(pcf_ctx* ctx, uint64_t n_total, int pairs) {
   CK(cudaSetDevice(ctx->device));
   CK(ensure(ctx->tmp_k, n_total * 8));
   CK(ensure(ctx->tmp_aux, n_total * 2));
+  CK(ensure(ctx->jbuf, n_total * 4));
   if (pairs) CK(ensure(ctx->tmp_v, n_total * 4));
   return PCF_OK;
 }

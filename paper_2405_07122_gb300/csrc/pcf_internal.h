@@ -135,6 +135,7 @@ struct KeyBufs {
   uint32_t* tmp_v;
   uint32_t* out_v;
   uint16_t* tmp_aux;    // low bucket-id digit carried from pass 1 to pass 2
+  const uint32_t* jbuf; // bucket id of every key of the level (written by k_hist1)
 };
 
 // ---- kernel launchers (pcf_kernels.cu) ----
@@ -169,7 +170,7 @@ cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tp
                          uint64_t spin_limit);
 cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
                          uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
-                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax);
+                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout);
 cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const uint64_t* n_dev,
                         uint64_t* status_words, uint32_t* tile_counter, uint32_t withhold,
                         uint64_t spin_limit, uint64_t* total_out, bool inclusive = false);

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
                                                const uint32_t* tile_base, uint32_t tile_keys,
                                                const uint64_t* __restrict__ keys, uint32_t kt,
                                                const uint32_t* __restrict__ tpool,
-                                               uint32_t* cmat) {
+                                               uint32_t* cmat, uint32_t* __restrict__ jout) {
   extern __shared__ uint32_t hist[];
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
@@ -259,8 +259,9 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
       for (int u = 0; u < U; ++u) {
         const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
         const bool v = i < end;
-        const uint32_t d = v ? (bucket_of_count(tv[u] - tb, al, ga) >> b2) : 0u;
-        hist_inc(hist, d, v, agg);
+        const uint32_t j = v ? bucket_of_count(tv[u] - tb, al, ga) : 0u;
+        if (v) jout[i] = j;
+        hist_inc(hist, j >> b2, v, agg);
       }
     }
   }
@@ -403,8 +404,7 @@ __device__ __forceinline__ ScatterSmem carve_scatter(uint8_t* p, uint32_t D, boo
 // PASS 1: digit = T[bin(x)] >> b2, carry = low b2 bits.  PASS 2: digit = carry.
 template <int PASS, bool PAIRS>
 __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_off, uint32_t tile_n,
-                             const BinModel& bm, const uint32_t* __restrict__ T, uint32_t tbase,
-                             uint32_t alpha, uint32_t gamma, uint32_t b2,
+                             const uint32_t* __restrict__ src_j, uint32_t b2,
                              const uint64_t* __restrict__ src, const uint32_t* __restrict__ src_v,
                              const uint16_t* __restrict__ src_aux, uint64_t* __restrict__ dst,
                              uint32_t* __restrict__ dst_v, uint16_t* __restrict__ dst_aux) {
@@ -431,24 +431,11 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
       if (PASS == 2) dig[k] = v ? (uint32_t)__ldg(src_aux + g0 + li) : 0u;
     }
     if (PASS == 1) {
-      uint32_t amb = 0;
-#pragma unroll
-      for (int k = 0; k < kItems; ++k) {
-        bool a;
-        dig[k] = bin_fast(bm, key[k], a);
-        amb |= (uint32_t)a << k;
-      }
-      if (amb) {
-#pragma unroll
-        for (int k = 0; k < kItems; ++k)
-          if ((amb >> k) & 1u) dig[k] = bin_exact_of(bm, key[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < kItems; ++k) aux[k] = __ldg(T + dig[k]);
+      // the bucket id j of every key was stored by the histogram pass
 #pragma unroll
       for (int k = 0; k < kItems; ++k) {
         const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
-        const uint32_t j = li < nsub ? bucket_of_count(aux[k] - tbase, alpha, gamma) : 0u;
+        const uint32_t j = li < nsub ? __ldg(src_j + g0 + li) : 0u;
         dig[k] = j >> b2;
         aux[k] = j & low_mask;
       }
@@ -536,7 +523,6 @@ __global__ void __launch_bounds__(256) k_scatter1(const Seg* segs, uint32_t S,
                                                   KeyBufs kb, const uint32_t* __restrict__ tpool,
                                                   const uint32_t* __restrict__ cmat) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ BinModel bm;
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
   const Seg& g = segs[s];
@@ -544,15 +530,14 @@ __global__ void __launch_bounds__(256) k_scatter1(const Seg* segs, uint32_t S,
   const uint32_t tt = t - tile_base[s];
   const uint32_t D = 1u << g.b1;
   ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, true);
-  if (threadIdx.x == 0) bm = g.bm;
   const uint32_t seg_base = cmat[g.cbase1];  // exclusive prefix at the segment's first entry
   for (uint32_t d = threadIdx.x; d < D; d += 256)
     sm.gofs[d] = (uint32_t)g.off + (cmat[g.cbase1 + (uint64_t)d * g.tiles1 + tt] - seg_base);
   __syncthreads();
   const uint64_t tile_off = g.off + (uint64_t)tt * tile_keys;
   const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, g.off + g.n - tile_off);
-  scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, bm, tpool + g.T_off, g.tbase, g.alpha, g.gamma,
-                         g.b2, kb.src, kb.src_v, nullptr, kb.tmp, kb.tmp_v, kb.tmp_aux);
+  scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, kb.jbuf, g.b2, kb.src, kb.src_v, nullptr, kb.tmp,
+                         kb.tmp_v, kb.tmp_aux);
 }
 
 // ---------------------------------------------------------------------------
@@ -659,9 +644,8 @@ __global__ void __launch_bounds__(256) k_scatter2(const Group* groups, uint32_t 
   __syncthreads();
   const uint64_t tile_off = gr.off + (uint64_t)tt * tile_keys;
   const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, gr.off + gr.n - tile_off);
-  BinModel dummy;
-  scatter_tile<2, PAIRS>(sm, D, tile_off, tile_n, dummy, nullptr, 0, 1, 1, 0, kb.tmp, kb.tmp_v,
-                         kb.tmp_aux, kb.out, kb.out_v, nullptr);
+  scatter_tile<2, PAIRS>(sm, D, tile_off, tile_n, nullptr, 0, kb.tmp, kb.tmp_v, kb.tmp_aux, kb.out,
+                         kb.out_v, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1035,10 +1019,10 @@ cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tp
 
 cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
                          uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
-                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax) {
+                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout) {
   if (!n_tiles) return cudaSuccess;
   k_hist1<<<n_tiles, 256, dmax * 4, c.stream>>>(segs, S, tile_base, tile_keys, keys, c.kt, tpool,
-                                                cmat);
+                                                cmat, jout);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -554,6 +554,206 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// Buckets of more than 256 keys (keys only): the four warps of a CTA share
+// one bucket, so that its critical path is a quarter as long.  The same
+// steps as learn_step; scans and Standard-Sorts of whole calls run in warp 0.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kCta = kWarps * 32;
+
+struct CtaShared {
+  uint64_t mn[kWarps], mx[kWarps];
+  uint32_t top, flag, ovf;
+};
+
+__device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
+                               uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
+                               CtaShared& sh) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t o = it.o, n = it.n;
+  uint64_t mn = ~0ull, mx = 0ull;
+  for (uint32_t i = tid; i < n; i += kCta) {
+    const uint64_t v = w.A[o + i];
+    mn = v < mn ? v : mn;
+    mx = v > mx ? v : mx;
+  }
+#pragma unroll
+  for (int d = 16; d; d >>= 1) {
+    const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+    const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+    mn = a < mn ? a : mn;
+    mx = b > mx ? b : mx;
+  }
+  if (lane == 0) {
+    sh.mn[wid] = mn;
+    sh.mx[wid] = mx;
+  }
+  __syncthreads();
+#pragma unroll
+  for (uint32_t k = 0; k < kWarps; ++k) {
+    mn = sh.mn[k] < mn ? sh.mn[k] : mn;
+    mx = sh.mx[k] > mx ? sh.mx[k] : mx;
+  }
+  if (mn == mx) return;  // one value: sorted
+  const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
+  const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
+  if (tid == 0)
+    sh.flag = (uint32_t)make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
+  for (uint32_t k = tid; k <= beta; k += kCta) w.tab[k] = 0;
+  for (uint32_t k = tid; k <= gamma; k += kCta) w.cnt[k] = 0;
+  __syncthreads();
+  if (sh.flag) {  // R5: a degenerate range goes to Standard-Sort
+    if (wid == 0) std_sort<false>(w, o, n, lane);
+    return;
+  }
+  const BinModel bm = *w.bm;
+  const uint64_t state = sample_state(seed, it.depth, it.start, n);
+  for (uint32_t s = tid; s < alpha; s += kCta) {
+    const uint32_t idx = (uint32_t)sample_index(state, s, n);
+    const uint64_t x = bits_of_ord(w.A[o + idx], kt);
+    bool amb;
+    uint32_t bn = bin_fast(bm, x, amb);
+    if (amb) bn = bin_exact_of(bm, x);
+    atomicAdd(&w.tab[bn], 1u);
+  }
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 <= beta; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const uint32_t v = k <= beta ? w.tab[k] : 0u;
+      const uint32_t inc = wscan(v, lane) + carry;
+      if (k <= beta) w.tab[k] = bucket_of_count(inc, alpha, gamma);
+      carry = __shfl_sync(~0u, inc, 31);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i0 = 0; i0 < n; i0 += 2 * kCta) {
+    uint64_t x[2];
+    uint32_t bn[2], amb = 0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint32_t i = i0 + u * kCta + tid;
+      x[u] = i < n ? bits_of_ord(w.A[o + i], kt) : bm.lo_bits;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      bool a;
+      bn[u] = bin_fast(bm, x[u], a);
+      amb |= (uint32_t)a << u;
+    }
+    if (amb) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint32_t i = i0 + u * kCta + tid;
+      if (i < n) {
+        const uint32_t j = w.tab[bn[u]];
+        w.J[i] = (uint16_t)j;
+        atomicAdd(&w.cnt[j], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 <= gamma; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const uint32_t v = k <= gamma ? w.cnt[k] : 0u;
+      const uint32_t inc = wscan(v, lane) + carry;
+      if (k <= gamma) w.cur[k] = inc - v;
+      carry = __shfl_sync(~0u, inc, 31);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += kCta) {
+    const uint32_t j = w.J[i];
+    const uint32_t pos = atomicAdd(&w.cur[j], 1u);
+    w.B[o + pos] = w.A[o + i];
+    w.Bj[pos] = (uint16_t)j;
+  }
+  __syncthreads();
+  for (uint32_t p = tid; p < n; p += kCta) {
+    const uint32_t j = w.Bj[p];
+    const uint32_t c = w.cnt[j], e = w.cur[j], s = e - c;
+    const uint64_t v = w.B[o + p];
+    const bool stdc = c >= delta || c < P.tau;
+    if (c == 1) {
+      w.A[o + p] = v;
+    } else if (stdc && c <= kRank) {
+      w.A[o + s + rank_in(w.B + o, s, e, p, v)] = v;
+    } else {
+      w.A[o + p] = v;
+      if (p == s) {
+        Item ch;
+        ch.o = (uint16_t)(o + s);
+        ch.n = (uint16_t)c;
+        ch.depth = (uint16_t)(it.depth + 1);
+        ch.std = stdc ? 1 : 0;
+        ch.start = it.start + s;
+        const uint32_t slot = atomicAdd(&sh.top, 1u);
+        if (slot < geo.smax) w.stk[slot] = ch;
+        else sh.ovf = 1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCta, 8) k_onchip_cta(const BRec* __restrict__ br,
+                                                        const uint32_t* __restrict__ list,
+                                                        const uint32_t* __restrict__ count,
+                                                        OnchipGeo geo,
+                                                        const uint64_t* __restrict__ X,
+                                                        uint64_t* out, uint32_t kt, Policy P,
+                                                        const uint16_t* __restrict__ ptab,
+                                                        uint32_t* status) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ CtaShared sh;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const Slice w = carve(smem_raw, geo, false);
+  const uint32_t nitems = *count;
+  for (uint32_t li = blockIdx.x; li < nitems; li += gridDim.x) {
+    const BRec r = br[list[li]];
+    const uint32_t off = r.off, n = r.n;
+    for (uint32_t i = tid; i < n; i += kCta) w.A[i] = ord_of(__ldg(X + off + i), kt);
+    if (tid == 0) {
+      Item it;
+      it.o = 0;
+      it.n = (uint16_t)n;
+      it.depth = (uint16_t)r.depth;
+      it.std = (r.kind & BK_STD) ? 1 : 0;
+      it.start = r.start;
+      w.stk[0] = it;
+      sh.top = 1;
+      sh.ovf = 0;
+    }
+    __syncthreads();
+    while (true) {
+      const uint32_t top = sh.top;
+      if (top == 0 || sh.ovf) break;
+      const Item it = w.stk[top - 1];
+      __syncthreads();
+      if (tid == 0) sh.top = top - 1;  // seen by the pushes after the next barrier
+      if (it.std) {
+        __syncthreads();
+        if (wid == 0) std_sort<false>(w, it.o, it.n, lane);
+      } else {
+        learn_step_cta(w, geo, it, r.seed, kt, P, ptab, sh);
+      }
+      __syncthreads();
+    }
+    if (sh.ovf) {
+      if (tid == 0) atomicOr(status, STATUS_INTERNAL);
+      return;
+    }
+    for (uint32_t i = tid; i < n; i += kCta) out[off + i] = bits_of_ord(w.A[i], kt);
+    __syncthreads();
+  }
+}
+
 }  // namespace onchip
 
 using namespace onchip;
@@ -604,7 +804,16 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
     const uint32_t per_sm = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm + 1024u))));
     const uint32_t grid = (uint32_t)num_sms_of_current_device() * per_sm;
     const uint32_t* list = lists + (size_t)cls * nb;
-    if (c.pairs) {
+    if (cls > 0 && !c.pairs) {
+      // a CTA per bucket (one slice per CTA)
+      const size_t sm1 = g.bytes;
+      const uint32_t per1 = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm1 + 1024u))));
+      if ((e = cudaFuncSetAttribute(k_onchip_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm1)))
+        return e;
+      k_onchip_cta<<<(uint32_t)num_sms_of_current_device() * per1, kCta, sm1, c.stream>>>(
+          br, list, counts + cls, g, X, out, c.kt, P, ptab, c.status);
+    } else if (c.pairs) {
       if ((e = cudaFuncSetAttribute(k_onchip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm)))
         return e;
