@@ -440,17 +440,28 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
         aux[k] = j & low_mask;
       }
     }
-    // per-warp counters as u32 pairs of u16 lanes would race; the counters
-    // are u16 in shared memory and updated with 32-bit atomics on the
-    // aligned word holding them (one leader per digit per step, and shared
-    // atomics of one warp apply in program order, so ranks follow input
-    // order: the scatter is stable)
+    // per-warp counters, u16 in shared memory, updated with 32-bit atomics
+    // on the aligned word holding them.  Key-value sorts rank stably: one
+    // leader per digit per step (match.any), and shared atomics of one warp
+    // apply in program order, so ranks follow input order.  Keys-only sorts
+    // let every key take its rank from its own atomic: keys of one digit in
+    // one step may then land in either order, which no result can show
+    // (equal keys are indistinguishable, and every bucket is sorted later).
     uint16_t* my = sm.wcnt + (size_t)w * D;
     uint32_t* myw = reinterpret_cast<uint32_t*>(my);
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
       const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
       const bool v = li < nsub;
+      if (!PAIRS) {
+        uint32_t prior = 0;
+        if (v) {
+          const uint32_t sh = (dig[k] & 1u) * 16u;
+          prior = (atomicAdd(&myw[dig[k] >> 1], 1u << sh) >> sh) & 0xFFFFu;
+        }
+        rank[k] = prior;
+        continue;
+      }
       const uint32_t peers = __match_any_sync(~0u, v ? dig[k] : 0xFFFFFFFFu);
       const int leader = __ffs(peers) - 1;
       uint32_t prior = 0;
@@ -501,12 +512,18 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
       }
     }
     __syncthreads();
-    for (uint32_t pos = tid; pos < nsub; pos += 256) {
-      const uint32_t d = sm.sdig[pos];
-      const uint64_t o = (uint64_t)sm.gofs[d] + (pos - sm.dbase[d]);
-      dst[o] = sm.skey[pos];
-      if (PASS == 1) dst_aux[o] = sm.saux[pos];
-      if (PAIRS) dst_v[o] = sm.sval[pos];
+    // write-out in staged (digit) order; unrolled so that the shared loads
+    // of all items are in flight together
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t pos = (uint32_t)tid + (uint32_t)k * 256u;
+      if (pos < nsub) {
+        const uint32_t d = sm.sdig[pos];
+        const uint64_t o = (uint64_t)sm.gofs[d] + (pos - sm.dbase[d]);
+        dst[o] = sm.skey[pos];
+        if (PASS == 1) dst_aux[o] = sm.saux[pos];
+        if (PAIRS) dst_v[o] = sm.sval[pos];
+      }
     }
     __syncthreads();
     for (uint32_t d = tid; d < D; d += 256) sm.gofs[d] += sm.dtot[d];
@@ -518,7 +535,7 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
 // k_scatter1: pass 1 (src -> tmp), digit = high bits of the bucket id
 // ---------------------------------------------------------------------------
 template <bool PAIRS>
-__global__ void __launch_bounds__(256) k_scatter1(const Seg* segs, uint32_t S,
+__global__ void __launch_bounds__(256, 2) k_scatter1(const Seg* segs, uint32_t S,
                                                   const uint32_t* tile_base, uint32_t tile_keys,
                                                   KeyBufs kb, const uint32_t* __restrict__ tpool,
                                                   const uint32_t* __restrict__ cmat) {
@@ -625,7 +642,7 @@ __global__ void __launch_bounds__(256) k_hist2(const Group* groups, uint32_t n_g
 }
 
 template <bool PAIRS>
-__global__ void __launch_bounds__(256) k_scatter2(const Group* groups, uint32_t n_groups,
+__global__ void __launch_bounds__(256, 2) k_scatter2(const Group* groups, uint32_t n_groups,
                                                   const Seg* segs, const uint32_t* g_tile_scan,
                                                   const uint64_t* total_tiles, uint32_t tile_keys,
                                                   KeyBufs kb, const uint32_t* __restrict__ cmat2) {
