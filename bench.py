@@ -8,9 +8,13 @@ device output; inputs are 800 MB each, larger than the 129 MB L2).
   value        sorted Gkeys/s over the K timed steps (device-resident inputs)
   e2e          the same through pcf_sort_keys_host: pinned host buffer ->
                device -> sort -> host, copies inside the timed region
-  roofline     the dominant kernel's algorithmic bytes per launch / its mean
-               launch time (CUDA events on the sort's stream), vs the
-               measured copy bandwidth
+  roofline     the dominant stage's algorithmic bytes per launch / its mean
+               launch time (CUDA events on the sort's stream, in two extra
+               untimed steps), vs the measured copy bandwidth; traffic from
+               the ncu capture in profiles/traffic.json when it matches the
+               current sources
+  roofline_job the whole sort's bytes (the library's pass model, and the
+               48 B/key one-level minimum) per second vs the copy bandwidth
   cpu_baseline the CPU oracle, single-threaded, on a bounded sample
 
 `--impl reference` times the CPU oracle instead (the reference arm).
@@ -42,12 +46,31 @@ CPU_SAMPLE_N = 25 * 10**6
 # algorithmic bytes per key of each kernel (keys only)
 KERNEL_BYTES = {
     "range": 8,        # read the key
-    "hist1_scan": 8,   # read the key (the bucket table hits L2)
-    "scatter1": 18,    # read the key, write the key and its 2-byte low digit
+    "hist1_scan": 12,  # read the key, write its bucket id (the table hits L2)
+    "scatter1": 22,    # read key + bucket id, write the key and its 2-byte low digit
     "hist2_scan": 2,   # read the low digit
     "scatter2": 18,    # read key + digit, write the key
     "leaf": 16,        # read and write each key finished on chip
 }
+
+
+def stage_traffic(stage, n):
+    """DRAM bytes (read + write) of one launch of `stage` at n keys, scaled
+    from the ncu capture summarised in profiles/traffic.json, or None when
+    that capture was taken on sources that have changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[stage]
+        h = hashlib.sha256()
+        for rel in rec["sources"]:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["sha256"]:
+            return None
+        return rec["dram_bytes_per_key"] * n
+    except Exception:
+        return None
 
 
 def max_over_ranks(ms, dist, device=None):
@@ -216,15 +239,16 @@ def main():
 
     def step(timing=False):
         st = {k: 0.0 for k in pcfsort.STAGES}
-        launches = 0
+        launches, moved = 0, 0
         for t, o in zip(ins, outs):
             ctx.sort_keys(t, o, key_type="f64", seed=0, stream=stream)
             s = ctx.last_stats()
             launches += s["kernel_launches"]
+            moved += s["bytes_moved"]
             if timing:
                 for k, v in ctx.stage_ms().items():
                     st[k] += v
-        return st, launches
+        return st, launches, moved
 
     for _ in range(args.warmup):
         step()
@@ -235,29 +259,34 @@ def main():
         ok = torch.where(b < 0, b ^ low63, b)
         assert bool((ok[1:] >= ok[:-1]).all()), "output not sorted"
 
-    ctx.enable_timing(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    stages = {k: 0.0 for k in pcfsort.STAGES}
-    launches = 0
+    launches, moved = 0, 0
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            st, nl = step(timing=True)
+            _, nl, mv = step()
             launches += nl
-            for k in stages:
-                stages[k] += st[k]
+            moved += mv
         e1.record(stream)
         torch.cuda.synchronize(dev)
-    ctx.enable_timing(False)
     ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     if dist:
         dist.barrier()
     keys_per_step = 4 * n * world
     value = job_value(4 * n, world, args.steps, ms)
+    # stage breakdown (CUDA events on the sort's stream), untimed steps
+    ctx.enable_timing(True)
+    t_steps = 2
+    stages = {k: 0.0 for k in pcfsort.STAGES}
+    for _ in range(t_steps):
+        st, _, _ = step(timing=True)
+        for k in stages:
+            stages[k] += st[k]
+    ctx.enable_timing(False)
 
     # end to end: pinned host buffer -> device -> sort -> host, per array
     pinned = [torch.from_numpy(x.copy()).pin_memory() for x in host_keys]
@@ -277,14 +306,15 @@ def main():
     peak, peak_kind = peaks()
     per_launch = {}
     for k, b in KERNEL_BYTES.items():
-        ms_k = stages[k] / (args.steps * 4)
+        ms_k = stages[k] / (t_steps * 4)
         if ms_k > 0:
             per_launch[k] = (ms_k, b)
     dom = max(per_launch, key=lambda k: per_launch[k][0])
     dom_ms, dom_b = per_launch[dom]
-    # keys processed by one launch of the dominant kernel: all N (global
-    # passes; the leaf kernel sees every key of this workload too)
+    # keys processed by one launch of the dominant stage: all n (every key of
+    # this workload passes through the global passes and the on-chip finish)
     achieved = dom_b * n / (dom_ms / 1e3) / 1e9
+    step_s = ms / args.steps / 1e3
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -299,8 +329,15 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "bytes_per_key": dom_b},
-        "stage_ms_per_array": {k: v / (args.steps * 4) for k, v in stages.items()},
+                     "traffic": stage_traffic(dom, n), "bytes_per_key": dom_b},
+        # the whole sort against the copy peak: the bytes the passes it ran
+        # must move (the library's pass model), and the 48 B/key minimum of
+        # one bucketing level (range 8, predict 8, move 16, finish 16)
+        "roofline_job": {"bytes_measured_passes": moved / args.steps,
+                         "frac_measured_passes": moved / args.steps / step_s / 1e9 / peak,
+                         "bytes_algorithmic": 48 * 4 * n,
+                         "frac_algorithmic": 48 * 4 * n / step_s / 1e9 / peak},
+        "stage_ms_per_array": {k: v / (t_steps * 4) for k, v in stages.items()},
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -597,7 +597,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                        as<uint32_t>(ctx->cmat1), L.dmax1));
     tm.mark(3);
     ctx->stats.global_passes += 1;
-    ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 /*hist1*/ + 8 + 10 /*scatter1*/) +
+    ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 + 4 /*hist1*/ + 12 + 10 /*scatter1*/) +
                               (pairs ? n_level * 8 : 0);
     // pass 2
     if (L.two_pass) {
@@ -662,6 +662,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
     if (stw & STATUS_INTERNAL) return PCF_ERR_INTERNAL;
     ctx->stats.leaf_buckets += lo.n_leaf;
+    uint64_t level_fb_keys = 0;
     // standard sort of the large failure-guard / degenerate buckets
     if (lo.n_fb) {
       const uint32_t nf = lo.n_fb;
@@ -673,8 +674,13 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
         rb[i + 1] = rb[i] + (uint32_t)((items[i].n + kRangeTile - 1) / kRangeTile);
         mb[i + 1] = mb[i] + (uint32_t)((items[i].n + kMergeTile - 1) / kMergeTile);
         max_n = std::max<uint64_t>(max_n, items[i].n);
-        ctx->stats.fallback_keys += items[i].n;
+        level_fb_keys += items[i].n;
       }
+      ctx->stats.fallback_keys += level_fb_keys;
+      // block sort, then merge passes up to the largest item, then the copy
+      uint32_t passes = 2;
+      for (uint64_t run = kMergeTile; run < max_n; run *= 2) ++passes;
+      ctx->stats.bytes_moved += level_fb_keys * (pairs ? 24 : 16) * passes;
       ctx->stats.fallback_buckets += nf;
       const size_t need2 = (nf + 1) * 8 + 64;
       CK(ensure(ctx->fb_bases, need2));
@@ -699,6 +705,9 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       CK(cudaStreamSynchronize(st));
       tm.mark(7);
     }
+    // keys finished on chip (or copied as one value) this level: read and
+    // written once
+    ctx->stats.bytes_moved += (n_level - lo.plan.n_keys - level_fb_keys) * (pairs ? 24 : 16);
     // the next level
     const PlanTotals& pt = lo.plan;
     LevelPlan N;

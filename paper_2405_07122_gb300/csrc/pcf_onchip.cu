@@ -15,9 +15,9 @@
 //     or |c| < tau, else a further Learned-Sort step (pushed on a per-warp
 //     stack of pending calls);
 //   - Standard-Sort: a new bucket of at most 32 keys by ranking each of its
-//     keys among the bucket's; a whole call by ranking (at most 16 keys, or
-//     32 for key-value sorts), a bitonic network across the warp's registers
-//     (keys only, at most 256) or a merge sort (key-value, stable).
+//     keys among the bucket's; a whole call by ranking (at most 32 keys), a
+//     bitonic network across the warp's registers (keys only, at most 64) or
+//     a merge sort (larger, or key-value: stable).
 // The leaf records are first listed by size class; the warps of a launch
 // take the buckets of one class in turn (the class's slice size bounds the
 // keys of a bucket; three classes up to 1024 keys).
@@ -29,7 +29,7 @@ namespace onchip {
 
 constexpr uint32_t kWarps = 4;   // independent warps per CTA
 constexpr uint32_t kRank = 32;     // key-value Standard-Sorts up to this size rank each key
-constexpr uint32_t kRankKeys = 16; // ... keys-only ones (a bitonic network above)
+constexpr uint32_t kRankKeys = 32; // ... keys-only ones (a bitonic network up to 64 above)
 
 struct Item {  // a pending call on [o, o + n) of the warp's buffers
   uint16_t o, n;
@@ -282,16 +282,10 @@ __device__ void std_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) 
   if (c <= 1) return;
   if (c <= (PAIRS ? kRank : kRankKeys)) {
     rank_sort<PAIRS>(w, o, c, lane);
-  } else if (PAIRS || c > 256) {
+  } else if (PAIRS || c > 64) {
     merge_sort<PAIRS>(w, o, c, lane);
-  } else if (c <= 32) {
-    bitonic_sort<1>(w.A, o, c, lane);
-  } else if (c <= 64) {
-    bitonic_sort<2>(w.A, o, c, lane);
-  } else if (c <= 128) {
-    bitonic_sort<4>(w.A, o, c, lane);
   } else {
-    bitonic_sort<8>(w.A, o, c, lane);
+    bitonic_sort<2>(w.A, o, c, lane);
   }
 }
 
@@ -357,27 +351,27 @@ __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, 
   }
   __syncwarp();
   // the bucket of every key, and the bucket sizes
-  for (uint32_t i0 = 0; i0 < n; i0 += 128) {
-    uint64_t x[4];
-    uint32_t bn[4], amb = 0;
+  for (uint32_t i0 = 0; i0 < n; i0 += 64) {
+    uint64_t x[2];
+    uint32_t bn[2], amb = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
       const uint32_t i = i0 + u * 32 + lane;
       x[u] = i < n ? bits_of_ord(w.A[o + i], kt) : bm.lo_bits;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
       bool a;
       bn[u] = bin_fast(bm, x[u], a);
       amb |= (uint32_t)a << u;
     }
     if (amb) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 2; ++u)
         if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
       const uint32_t i = i0 + u * 32 + lane;
       if (i < n) {
         const uint32_t j = w.tab[bn[u]];
