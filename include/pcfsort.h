@@ -71,16 +71,13 @@ typedef struct {
 
 /* Implementation knobs.  They change speed only, never the result or the
  * model: max_digit_bits = widest bucket-id digit scattered per global pass
- * (4..11); tile_log2 = log2 of keys per count tile of a global pass (12..18);
- * leaf_cap = the largest bucket finished on chip (64..1024, power of two);
- * onchip_window = keys of the windows in which on-chip buckets are grouped
- * per thread block (1024..8192, power of two).  Zero fields keep the
- * current value.  Default: {11, 14, 1024, 1024}. */
+ * (4..12); tile_log2 = log2 of keys per count tile of a global pass (12..18);
+ * leaf_cap = the largest bucket finished on chip (64..1024, power of two).
+ * Zero fields keep the current value.  Default: {11, 14, 1024}. */
 typedef struct {
   uint32_t max_digit_bits;
   uint32_t tile_log2;
   uint32_t leaf_cap;
-  uint32_t onchip_window;
 } pcf_tuning;
 
 typedef struct pcf_ctx pcf_ctx;

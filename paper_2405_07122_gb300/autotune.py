@@ -1,9 +1,8 @@
 """Autotuner for the speed-only knobs of the library (pcf_tuning).
 
 The knobs are the widest bucket-id digit scattered per global pass
-(max_digit_bits), the keys per count tile (tile_log2), the largest bucket
-finished on chip (leaf_cap) and the keys per on-chip window of one thread
-block (onchip_window).  None of them changes alpha, beta,
+(max_digit_bits), the keys per count tile (tile_log2) and the largest
+bucket finished on chip (leaf_cap).  None of them changes alpha, beta,
 gamma, delta, tau or the output, so the tuner may pick any of them; it times
 each candidate on a sample of the caller's workload with CUDA events and keeps
 the fastest.  Results are cached in a JSON file keyed by workload class.
@@ -17,8 +16,7 @@ from . import pcfsort
 DEFAULT_GRID = {
     "max_digit_bits": (10, 11),
     "tile_log2": (14, 15),
-    "leaf_cap": (256, 512, 1024),
-    "onchip_window": (2048, 4096),
+    "leaf_cap": (512, 1024),
 }
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")

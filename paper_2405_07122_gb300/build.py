@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpcfsort.so")
-SOURCES = ["pcf_level.cu", "pcf_leaf.cu", "pcf_chunk.cu", "pcf_onchip.cu", "pcf_host.cu", "pcf_static.cu"]
+SOURCES = ["pcf_level.cu", "pcf_onchip.cu", "pcf_fallback.cu", "pcf_host.cu", "pcf_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fno-fast-math",

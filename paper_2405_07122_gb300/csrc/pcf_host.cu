@@ -68,7 +68,7 @@ struct pcf_ctx {
   int device = 0;
   int num_sms = 0;
   Policy policy{3, 3, 3, 3, 4, 0, 100};
-  pcf_tuning tuning{11, 14, 1024, 1024};
+  pcf_tuning tuning{11, 14, 1024};
   std::string last_err;
   pcf_call_stats stats{};
   bool timing = false;
@@ -285,33 +285,6 @@ struct LevelPlan {
   DevPlan dp{};
 };
 
-struct LeafGeom {
-  uint32_t tmax, gmax, warps, grid;
-};
-
-LeafGeom leaf_geom(pcf_ctx* ctx, bool pairs) {
-  LeafGeom g;
-  const uint32_t cap = ctx->tuning.leaf_cap;
-  uint32_t tmax = 2, gmax = 2;
-  for (uint64_t n = 2; n <= cap; ++n) {
-    if (n < ctx->policy.tau) continue;
-    Params pr = params_of(ctx->policy, n);
-    tmax = std::max(tmax, pr.beta + 1);
-    gmax = std::max(gmax, pr.gamma + 1);
-  }
-  g.tmax = (tmax + 3) & ~3u;
-  g.gmax = (gmax + 3) & ~3u;
-  const size_t per = leaf_smem_per_warp(cap, pairs, g.tmax, g.gmax);
-  uint32_t warps = 8;
-  while (warps > 1 && per * warps > 110 * 1024) warps /= 2;
-  g.warps = warps;
-  const size_t cta = per * warps;
-  uint32_t per_sm = (uint32_t)std::max<size_t>(1, (227 * 1024) / (cta + 1024));
-  per_sm = std::min(per_sm, 2048u / (32 * warps));
-  g.grid = (uint32_t)ctx->num_sms * per_sm;
-  return g;
-}
-
 // alpha, beta, gamma, delta of every on-chip size n <= cap, so the leaf
 // kernel looks them up instead of evaluating floor(n^{p/q}) per bucket.
 cudaError_t ensure_ptab(pcf_ctx* ctx, cudaStream_t st) {
@@ -397,7 +370,6 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   CK(ensure(ctx->misc, 256));
   const uint32_t tile_keys = 1u << ctx->tuning.tile_log2;
   const uint32_t cap = ctx->tuning.leaf_cap;
-  const LeafGeom lg = leaf_geom(ctx, pairs);
   CK(ensure_ptab(ctx, st));
   const uint16_t* ptab = as<uint16_t>(ctx->ptab);
   Timer tm(ctx, st);
@@ -807,14 +779,11 @@ pcf_status pcf_ctx_set_tuning(pcf_ctx* ctx, const pcf_tuning* t) {
   if (t->max_digit_bits) n.max_digit_bits = t->max_digit_bits;
   if (t->tile_log2) n.tile_log2 = t->tile_log2;
   if (t->leaf_cap) n.leaf_cap = t->leaf_cap;
-  if (t->onchip_window) n.onchip_window = t->onchip_window;
-  if (n.max_digit_bits < 4 || n.max_digit_bits > 11) return PCF_ERR_INVALID_ARG;
+  if (n.max_digit_bits < 4 || n.max_digit_bits > kMaxDigitBits) return PCF_ERR_INVALID_ARG;
   if (n.tile_log2 < 12 || n.tile_log2 > 18) return PCF_ERR_INVALID_ARG;
   if (n.leaf_cap < 64 || n.leaf_cap > 1024 || (n.leaf_cap & (n.leaf_cap - 1))) return PCF_ERR_INVALID_ARG;
-  if (n.onchip_window < 1024 || n.onchip_window > 8192 ||
-      (n.onchip_window & (n.onchip_window - 1)))
-    return PCF_ERR_INVALID_ARG;
-  // the on-chip window (keys, values and tables) must fit one block's shared memory
+  // the largest on-chip slice (keys, values and tables) must fit one block's
+  // shared memory
   if (onchip_smem_bytes(n.leaf_cap, ctx->policy, true) > 227 * 1024)
     return PCF_ERR_INVALID_ARG;
   ctx->tuning = n;

@@ -50,18 +50,8 @@ struct Group {
   uint32_t pad;
 };
 
-// A bucket finished in shared memory, or a (sub)array queued for the next
-// global level: Learned-Sort(keys [off, off+n)) at `depth`.
-struct WorkItem {
-  uint64_t off;
-  uint64_t start;
-  uint64_t seed;
-  uint32_t n;
-  uint32_t depth;
-};
-
 // Every bucket of a level, in memory order (bucket index order): written by
-// k_buckets, read by the on-chip kernel.
+// k_buckets, read by the on-chip kernels and the next level's planning.
 enum : uint32_t {
   BK_LEAF = 1u,  // finished on chip
   BK_STD = 2u,   // ... by Standard-Sort (|c| >= delta or |c| < tau)
@@ -138,7 +128,7 @@ struct KeyBufs {
   const uint32_t* jbuf; // bucket id of every key of the level (written by k_hist1)
 };
 
-// ---- kernel launchers (pcf_kernels.cu) ----
+// ---- kernel launchers ----
 struct LaunchCfg {
   cudaStream_t stream;
   uint32_t kt;
@@ -216,19 +206,6 @@ cudaError_t launch_copy_segs(const LaunchCfg& c, const Seg* segs, uint32_t S,
                              const uint32_t* range_base, uint32_t n_tiles, const uint64_t* src,
                              uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v,
                              uint32_t status_mask);
-cudaError_t launch_leaf(const LaunchCfg& c, const WorkItem* items, const uint32_t* n_items,
-                        uint32_t* cursor, const uint64_t* src, uint64_t* dst,
-                        const uint32_t* src_v, uint32_t* dst_v, Policy P, const uint16_t* ptab,
-                        uint32_t cap, uint32_t tmax, uint32_t gmax, uint32_t warps_per_cta,
-                        uint32_t grid);
-size_t leaf_smem_per_warp(uint32_t cap, bool pairs, uint32_t tmax, uint32_t gmax);
-// on-chip finish of the leaf buckets whose records are br[0..nb): windows of
-// `window` keys starting at wbase, covering span keys
-cudaError_t launch_chunk(const LaunchCfg& c, const BRec* br, uint32_t nb, uint64_t wbase,
-                         uint64_t span, uint32_t window, uint32_t leaf_cap, const uint64_t* X,
-                         const uint32_t* Xv, uint64_t* out, uint32_t* out_v, Policy P,
-                         const uint16_t* ptab, uint32_t* first_scratch);
-size_t chunk_smem_bytes(uint32_t window, uint32_t leaf_cap, const Policy& P, bool pairs);
 // on-chip finish, one warp per bucket: every BK_LEAF record of br[0..nb)
 // (any order), keys X -> out at the record's offset
 struct OnchipGeo {

@@ -699,11 +699,21 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
   __shared__ uint32_t tv[PAIRS ? kTiny : 1][PAIRS ? 256 : 1];
   const uint64_t B = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = B < n_buckets;
+  // the segments this block's buckets fall in: one search per bound, then
+  // each thread searches that short window
+  __shared__ uint32_t s_win[2];
+  {
+    const uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x;
+    if (threadIdx.x == 0) s_win[0] = upper_bound_dev(bucket_base, S + 1, b0) - 1;
+    if (threadIdx.x == 32)
+      s_win[1] = upper_bound_dev(bucket_base, S + 1, min(b0 + blockDim.x, n_buckets) - 1);
+  }
+  __syncthreads();
   uint32_t s = 0, size = 0;
   uint64_t off = 0;  // start of the bucket, also when empty (records stay ordered)
   bool v = false;
   if (in) {
-    s = upper_bound_dev(bucket_base, S + 1, B) - 1;
+    s = s_win[0] + upper_bound_dev(bucket_base + s_win[0], s_win[1] - s_win[0] + 1, B) - 1;
     const Seg& sg = segs[s];
     off = sg.off;
     if (sg.status == SEG_BUCKET && sg.b2 == 0) {

@@ -37,7 +37,7 @@ class Policy(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("max_digit_bits", ctypes.c_uint32), ("tile_log2", ctypes.c_uint32),
-                ("leaf_cap", ctypes.c_uint32), ("onchip_window", ctypes.c_uint32)]
+                ("leaf_cap", ctypes.c_uint32)]
 
 
 class CallStats(ctypes.Structure):
@@ -150,15 +150,14 @@ class Context:
         self._check(lib().pcf_ctx_set_policy(self._h, ctypes.byref(
             Policy(a_num, b_num, c_num, d_num, den, tau))))
 
-    def set_tuning(self, max_digit_bits=0, tile_log2=0, leaf_cap=0, onchip_window=0):
+    def set_tuning(self, max_digit_bits=0, tile_log2=0, leaf_cap=0):
         self._check(lib().pcf_ctx_set_tuning(self._h, ctypes.byref(
-            Tuning(max_digit_bits, tile_log2, leaf_cap, onchip_window))))
+            Tuning(max_digit_bits, tile_log2, leaf_cap))))
 
     def tuning(self):
         t = Tuning()
         self._check(lib().pcf_ctx_get_tuning(self._h, ctypes.byref(t)))
-        return dict(max_digit_bits=t.max_digit_bits, tile_log2=t.tile_log2, leaf_cap=t.leaf_cap,
-                    onchip_window=t.onchip_window)
+        return dict(max_digit_bits=t.max_digit_bits, tile_log2=t.tile_log2, leaf_cap=t.leaf_cap)
 
     def reserve(self, n_total: int, pairs: bool = False):
         self._check(lib().pcf_ctx_reserve(self._h, n_total, 1 if pairs else 0))
