@@ -297,14 +297,18 @@ __device__ void std_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) 
 template <bool PAIRS>
 __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                            uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
-                           uint32_t& top, uint32_t lane) {
+                           uint32_t& top, uint32_t lane, bool root, uint64_t rmn, uint64_t rmx) {
   const uint32_t o = it.o, n = it.n;
-  // range
-  uint64_t mn = ~0ull, mx = 0ull;
-  for (uint32_t i = lane; i < n; i += 32) {
-    const uint64_t v = w.A[o + i];
-    mn = v < mn ? v : mn;
-    mx = v > mx ? v : mx;
+  // range (a root call's per-lane range was taken while its keys loaded)
+  uint64_t mn = rmn, mx = rmx;
+  if (!root) {
+    mn = ~0ull;
+    mx = 0ull;
+    for (uint32_t i = lane; i < n; i += 32) {
+      const uint64_t v = w.A[o + i];
+      mn = v < mn ? v : mn;
+      mx = v > mx ? v : mx;
+    }
   }
 #pragma unroll
   for (int d = 16; d; d >>= 1) {
@@ -508,8 +512,12 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
   for (uint32_t li = gw; li < nitems; li += nw) {
     const BRec r = br[list[li]];
     const uint32_t off = r.off, n = r.n;
+    uint64_t rmn = ~0ull, rmx = 0ull;
     for (uint32_t i = lane; i < n; i += 32) {
-      w.A[i] = ord_of(__ldg(X + off + i), kt);
+      const uint64_t v = ord_of(__ldg(X + off + i), kt);
+      w.A[i] = v;
+      rmn = v < rmn ? v : rmn;
+      rmx = v > rmx ? v : rmx;
       if (PAIRS) w.Av[i] = __ldg(Xv + off + i);
     }
     __syncwarp();
@@ -528,12 +536,14 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
         w.stk[0] = it;
       }
       __syncwarp();
+      bool root = true;
       while (top > 0 && ok) {
         --top;
         const Item it = w.stk[top];
         __syncwarp();
         if (it.std) std_sort<PAIRS>(w, it.o, it.n, lane);
-        else ok = learn_step<PAIRS>(w, geo, it, r.seed, kt, P, ptab, top, lane);
+        else ok = learn_step<PAIRS>(w, geo, it, r.seed, kt, P, ptab, top, lane, root, rmn, rmx);
+        root = false;
       }
     }
     if (!ok) {
@@ -549,42 +559,82 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Buckets of more than 256 keys (keys only): the four warps of a CTA share
-// one bucket, so that its critical path is a quarter as long.  The same
-// steps as learn_step; scans and Standard-Sorts of whole calls run in warp 0.
+// Buckets of more than 256 keys (keys only): the two warps of a CTA share
+// one bucket, so that its critical path is about half as long, and twice as
+// many buckets as four-warp CTAs would allow stay in flight per SM.  The
+// same steps as learn_step; scans and Standard-Sorts of whole calls run in
+// warp 0.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kCta = kWarps * 32;
+constexpr uint32_t kCta = 64;
 
 struct CtaShared {
-  uint64_t mn[kWarps], mx[kWarps];
+  uint64_t mn[kCta / 32], mx[kCta / 32];
+  uint32_t wsum[kCta / 32];
   uint32_t top, flag, ovf;
 };
 
+// Scan of src[0..m) into dst by the CTA (each thread a contiguous run, one
+// barrier; src may be dst).  EXCL: exclusive sums.  Otherwise the inclusive
+// sums b_k turned into the bucket table floor(b_k gamma / alpha).
+template <bool EXCL>
+__device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uint32_t m,
+                                         uint32_t alpha, uint32_t gamma, CtaShared& sh) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t r = (m + kCta - 1) / kCta;
+  const uint32_t a = min(m, tid * r), b = min(m, a + r);
+  uint32_t sum = 0;
+  for (uint32_t k = a; k < b; ++k) sum += src[k];
+  const uint32_t inc = wscan(sum, lane);
+  if (lane == 31) sh.wsum[wid] = inc;
+  __syncthreads();
+  uint32_t run = inc - sum;
+#pragma unroll
+  for (uint32_t k = 0; k < kCta / 32; ++k) run += k < wid ? sh.wsum[k] : 0u;
+  for (uint32_t k = a; k < b; ++k) {
+    const uint32_t v = src[k];
+    if (EXCL) {
+      dst[k] = run;
+      run += v;
+    } else {
+      run += v;
+      dst[k] = bucket_of_count(run, alpha, gamma);
+    }
+  }
+}
+
+// Samples per thread drawn before the model is ready (alpha <= this many
+// times the CTA size for every call of at most 1024 keys under the default
+// policy; any further samples are drawn after it).
+constexpr uint32_t kSampRegs = 3;
+
+// root: the range was reduced into sh.mn / sh.mx while the keys were loaded
 __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                                uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
-                               CtaShared& sh) {
+                               CtaShared& sh, bool root) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t o = it.o, n = it.n;
   uint64_t mn = ~0ull, mx = 0ull;
-  for (uint32_t i = tid; i < n; i += kCta) {
-    const uint64_t v = w.A[o + i];
-    mn = v < mn ? v : mn;
-    mx = v > mx ? v : mx;
+  if (!root) {
+    for (uint32_t i = tid; i < n; i += kCta) {
+      const uint64_t v = w.A[o + i];
+      mn = v < mn ? v : mn;
+      mx = v > mx ? v : mx;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+      const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+      const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+      mn = a < mn ? a : mn;
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) {
+      sh.mn[wid] = mn;
+      sh.mx[wid] = mx;
+    }
+    __syncthreads();
   }
 #pragma unroll
-  for (int d = 16; d; d >>= 1) {
-    const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
-    const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
-    mn = a < mn ? a : mn;
-    mx = b > mx ? b : mx;
-  }
-  if (lane == 0) {
-    sh.mn[wid] = mn;
-    sh.mx[wid] = mx;
-  }
-  __syncthreads();
-#pragma unroll
-  for (uint32_t k = 0; k < kWarps; ++k) {
+  for (uint32_t k = 0; k < kCta / 32; ++k) {
     mn = sh.mn[k] < mn ? sh.mn[k] : mn;
     mx = sh.mx[k] > mx ? sh.mx[k] : mx;
   }
@@ -595,32 +645,39 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     sh.flag = (uint32_t)make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
   for (uint32_t k = tid; k <= beta; k += kCta) w.tab[k] = 0;
   for (uint32_t k = tid; k <= gamma; k += kCta) w.cnt[k] = 0;
+  // the sample positions and keys do not depend on the model: draw them
+  // while thread 0 builds it
+  const uint64_t state = sample_state(seed, it.depth, it.start, n);
+  uint64_t sx[kSampRegs];
+#pragma unroll
+  for (uint32_t u = 0; u < kSampRegs; ++u) {
+    const uint32_t s = tid + u * kCta;
+    sx[u] = s < alpha ? bits_of_ord(w.A[o + (uint32_t)sample_index(state, s, n)], kt) : 0ull;
+  }
   __syncthreads();
   if (sh.flag) {  // R5: a degenerate range goes to Standard-Sort
     if (wid == 0) std_sort<false>(w, o, n, lane);
     return;
   }
   const BinModel bm = *w.bm;
-  const uint64_t state = sample_state(seed, it.depth, it.start, n);
-  for (uint32_t s = tid; s < alpha; s += kCta) {
-    const uint32_t idx = (uint32_t)sample_index(state, s, n);
-    const uint64_t x = bits_of_ord(w.A[o + idx], kt);
+#pragma unroll
+  for (uint32_t u = 0; u < kSampRegs; ++u) {
+    if (tid + u * kCta < alpha) {
+      bool amb;
+      uint32_t bn = bin_fast(bm, sx[u], amb);
+      if (amb) bn = bin_exact_of(bm, sx[u]);
+      atomicAdd(&w.tab[bn], 1u);
+    }
+  }
+  for (uint32_t s = tid + kSampRegs * kCta; s < alpha; s += kCta) {
+    const uint64_t x = bits_of_ord(w.A[o + (uint32_t)sample_index(state, s, n)], kt);
     bool amb;
     uint32_t bn = bin_fast(bm, x, amb);
     if (amb) bn = bin_exact_of(bm, x);
     atomicAdd(&w.tab[bn], 1u);
   }
   __syncthreads();
-  if (wid == 0) {
-    uint32_t carry = 0;
-    for (uint32_t k0 = 0; k0 <= beta; k0 += 32) {
-      const uint32_t k = k0 + lane;
-      const uint32_t v = k <= beta ? w.tab[k] : 0u;
-      const uint32_t inc = wscan(v, lane) + carry;
-      if (k <= beta) w.tab[k] = bucket_of_count(inc, alpha, gamma);
-      carry = __shfl_sync(~0u, inc, 31);
-    }
-  }
+  cta_scan<false>(w.tab, w.tab, beta + 1, alpha, gamma, sh);
   __syncthreads();
   for (uint32_t i0 = 0; i0 < n; i0 += 2 * kCta) {
     uint64_t x[2];
@@ -652,16 +709,8 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     }
   }
   __syncthreads();
-  if (wid == 0) {
-    uint32_t carry = 0;
-    for (uint32_t k0 = 0; k0 <= gamma; k0 += 32) {
-      const uint32_t k = k0 + lane;
-      const uint32_t v = k <= gamma ? w.cnt[k] : 0u;
-      const uint32_t inc = wscan(v, lane) + carry;
-      if (k <= gamma) w.cur[k] = inc - v;
-      carry = __shfl_sync(~0u, inc, 31);
-    }
-  }
+  // bucket starts into cur (cnt keeps the sizes)
+  cta_scan<true>(w.cnt, w.cur, gamma + 1, 0, 0, sh);
   __syncthreads();
   for (uint32_t i = tid; i < n; i += kCta) {
     const uint32_t j = w.J[i];
@@ -696,7 +745,7 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   }
 }
 
-__global__ void __launch_bounds__(kCta, 8) k_onchip_cta(const BRec* __restrict__ br,
+__global__ void __launch_bounds__(kCta, 16) k_onchip_cta(const BRec* __restrict__ br,
                                                         const uint32_t* __restrict__ list,
                                                         const uint32_t* __restrict__ count,
                                                         OnchipGeo geo,
@@ -712,7 +761,26 @@ __global__ void __launch_bounds__(kCta, 8) k_onchip_cta(const BRec* __restrict__
   for (uint32_t li = blockIdx.x; li < nitems; li += gridDim.x) {
     const BRec r = br[list[li]];
     const uint32_t off = r.off, n = r.n;
-    for (uint32_t i = tid; i < n; i += kCta) w.A[i] = ord_of(__ldg(X + off + i), kt);
+    {
+      uint64_t mn = ~0ull, mx = 0ull;
+      for (uint32_t i = tid; i < n; i += kCta) {
+        const uint64_t v = ord_of(__ldg(X + off + i), kt);
+        w.A[i] = v;
+        mn = v < mn ? v : mn;
+        mx = v > mx ? v : mx;
+      }
+#pragma unroll
+      for (int d = 16; d; d >>= 1) {
+        const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+        const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+      }
+      if (lane == 0) {
+        sh.mn[wid] = mn;
+        sh.mx[wid] = mx;
+      }
+    }
     if (tid == 0) {
       Item it;
       it.o = 0;
@@ -735,7 +803,7 @@ __global__ void __launch_bounds__(kCta, 8) k_onchip_cta(const BRec* __restrict__
         __syncthreads();
         if (wid == 0) std_sort<false>(w, it.o, it.n, lane);
       } else {
-        learn_step_cta(w, geo, it, r.seed, kt, P, ptab, sh);
+        learn_step_cta(w, geo, it, r.seed, kt, P, ptab, sh, top == 1 && it.o == 0 && it.n == n);
       }
       __syncthreads();
     }
@@ -801,7 +869,7 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
     if (cls > 0 && !c.pairs) {
       // a CTA per bucket (one slice per CTA)
       const size_t sm1 = g.bytes;
-      const uint32_t per1 = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm1 + 1024u))));
+      const uint32_t per1 = max(1u, min(16u, (uint32_t)((227u * 1024u) / (sm1 + 1024u))));
       if ((e = cudaFuncSetAttribute(k_onchip_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm1)))
         return e;
