@@ -112,16 +112,15 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
 // Standard-Sorts (R7: any sort; the output is the unique sorted order)
 // ---------------------------------------------------------------------------
 
-// Rank of key v at position p among positions [s, e) of K: keys before p
-// that are <= v, and keys after p that are < v (equal keys keep their order).
+// Rank of key v at position p among positions [s, e) of K: the keys that
+// are smaller, or equal and earlier (equal keys keep their order).
 __device__ __forceinline__ uint32_t rank_in(const uint64_t* K, uint32_t s, uint32_t e, uint32_t p,
                                             uint64_t v) {
   uint32_t r = 0;
-  uint32_t t = s;
-#pragma unroll 4
-  for (; t < p; ++t) r += K[t] <= v ? 1u : 0u;
-#pragma unroll 4
-  for (t = p + 1; t < e; ++t) r += K[t] < v ? 1u : 0u;
+  for (uint32_t t = s; t < e; ++t) {
+    const uint64_t u = K[t];
+    r += (u < v || (u == v && t < p)) ? 1u : 0u;
+  }
   return r;
 }
 
