@@ -437,17 +437,38 @@ def run_secondary(args):
         srv = serve.SortServer(device=0, workers=4, mem_budget=64 << 30, batch_keys=1 << 27)
         rng = np.random.Generator(np.random.PCG64(8))
         handles = []
+        pending = []
+
+        def consume():
+            # the client takes each result as it completes (and lets it go),
+            # so finished outputs do not pile up on the device
+            keep = []
+            for h in pending:
+                if h.done.is_set():
+                    h.out = None
+                else:
+                    keep.append(h)
+            pending[:] = keep
+
         t0 = time.perf_counter()
         for (ta, nreq, kt, dist, _seed) in stream:
             now = time.perf_counter() - t0
             if ta > now:
                 time.sleep(ta - now)
             off = int(rng.integers(0, pool_n - nreq + 1))
-            handles.append(srv.submit(pools[(kt, dist)][off:off + nreq], kt))
+            h = srv.submit(pools[(kt, dist)][off:off + nreq], kt)
+            handles.append(h)
+            pending.append(h)
+            consume()
         for h in handles:
             h.done.wait()
+            h.out = None
         t1 = time.perf_counter()
         srv.close()
+        errors = [h.error for h in handles if h.error is not None]
+        if errors:
+            raise RuntimeError("%d of %d requests failed, first: %r" % (len(errors), len(handles),
+                                                                     errors[0]))
         keys_done = sum(h.n for h in handles)
         lat = serve.latency_summary(handles)
         line.update(metric="served sorted Gkeys/s (sustained)",

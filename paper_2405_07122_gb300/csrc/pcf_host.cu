@@ -12,6 +12,8 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <map>
+#include <mutex>
 
 #include "../../include/pcfsort.h"
 #include "pcf_internal.h"
@@ -80,11 +82,35 @@ struct pcf_ctx {
   DevBuf segs_b, pcols, pbsums;  // the other level's plan, its count columns
   DevBuf olist;                  // on-chip buckets listed by size class
   DevBuf jbuf;                   // bucket id of every key of a level
+  DevBuf small_segs;             // range records of the on-chip arrays (level 0)
   HostBuf h_stage, h_lout, h_status, h_items;
+  HostBuf h_stage_small;  // range records of the on-chip arrays (level 0)
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
   uint64_t ptab_key = 0;  // policy/cap the table was built for
   ParamCache pcache;
 };
+
+cudaError_t pcf::allow_max_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find({kernel, dev});
+  if (it != done.end()) return it->second;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (!e) e = cudaFuncGetAttributes(&fa, kernel);
+  // the limit covers the dynamic part; the kernel's static shared memory
+  // takes the rest of the block's opt-in maximum
+  if (!e)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  done[{kernel, dev}] = e;
+  return e;
+}
 
 namespace {
 
@@ -391,14 +417,17 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       plan_level(ctx->policy, ctx->tuning, ctx->pcache, all, pl);
       const uint32_t S = (uint32_t)all.size();
       size_t need = S * sizeof(Seg) + (S + 1) * 4;
-      CK(ensure_host(ctx->h_stage, need));
-      CK(ensure(ctx->segs, need));
-      memcpy(ctx->h_stage.p, pl.segs.data(), S * sizeof(Seg));
-      memcpy((char*)ctx->h_stage.p + S * sizeof(Seg), pl.range_base.data(), (S + 1) * 4);
-      CK(cudaMemcpyAsync(ctx->segs.p, ctx->h_stage.p, need, cudaMemcpyHostToDevice, st));
-      CK(launch_range(lc, as<Seg>(ctx->segs), S,
-                      (const uint32_t*)((char*)ctx->segs.p + S * sizeof(Seg)), pl.range_base[S],
-                      in_k, true));
+      // its own staging buffer: the level-0 plan below is staged while this
+      // copy may still be queued
+      CK(ensure_host(ctx->h_stage_small, need));
+      CK(ensure(ctx->small_segs, need));
+      memcpy(ctx->h_stage_small.p, pl.segs.data(), S * sizeof(Seg));
+      memcpy((char*)ctx->h_stage_small.p + S * sizeof(Seg), pl.range_base.data(), (S + 1) * 4);
+      CK(cudaMemcpyAsync(ctx->small_segs.p, ctx->h_stage_small.p, need, cudaMemcpyHostToDevice,
+                         st));
+      CK(launch_range(lc, as<Seg>(ctx->small_segs), S,
+                      (const uint32_t*)((char*)ctx->small_segs.p + S * sizeof(Seg)),
+                      pl.range_base[S], in_k, true));
     }
   }
 
@@ -845,8 +874,11 @@ static pcf_status sort_common(pcf_ctx* ctx, const void* kin, const uint32_t* vin
   if (overlap(kin, kout, n * 8)) return PCF_ERR_INVALID_ARG;
   if (pairs && overlap(vin, vout, n * 4)) return PCF_ERR_INVALID_ARG;
   if (!policy_ok(ctx->policy)) return PCF_ERR_INVALID_ARG;
-  return run_sort(ctx, (const uint64_t*)kin, vin, (uint64_t*)kout, vout, segs, (uint32_t)kt,
-                  pairs, (cudaStream_t)stream);
+  const pcf_status r = run_sort(ctx, (const uint64_t*)kin, vin, (uint64_t*)kout, vout, segs,
+                               (uint32_t)kt, pairs, (cudaStream_t)stream);
+  // a call that fails part-way returns with none of its work in flight
+  if (r != PCF_OK) cudaStreamSynchronize((cudaStream_t)stream);
+  return r;
 }
 
 pcf_status pcf_sort_keys(pcf_ctx* ctx, const void* d_in, void* d_out, uint64_t n, pcf_key_type kt,

@@ -137,6 +137,12 @@ struct LaunchCfg {
   uint64_t* launches;  // host counter of kernel launches (may be null)
 };
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum, once per device and kernel.  The limit only ever grows, so
+// callers on several host threads (each with its own context) never lower
+// it under one another's launches; a launch then needs only its own size.
+cudaError_t allow_max_smem(const void* kernel);
+
 inline void count_launch(const LaunchCfg& c, uint64_t k = 1) {
   if (c.launches) *c.launches += k;
 }

@@ -1072,7 +1072,7 @@ cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const ui
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return allow_max_smem((const void*)kernel);
 }
 
 cudaError_t launch_scatter1(const LaunchCfg& c, const Seg* segs, uint32_t S,

@@ -869,21 +869,15 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
       // a CTA per bucket (one slice per CTA)
       const size_t sm1 = g.bytes;
       const uint32_t per1 = max(1u, min(16u, (uint32_t)((227u * 1024u) / (sm1 + 1024u))));
-      if ((e = cudaFuncSetAttribute(k_onchip_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sm1)))
-        return e;
+      if ((e = allow_max_smem((const void*)k_onchip_cta))) return e;
       k_onchip_cta<<<(uint32_t)num_sms_of_current_device() * per1, kCta, sm1, c.stream>>>(
           br, list, counts + cls, g, X, out, c.kt, P, ptab, c.status);
     } else if (c.pairs) {
-      if ((e = cudaFuncSetAttribute(k_onchip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sm)))
-        return e;
+      if ((e = allow_max_smem((const void*)k_onchip<true>))) return e;
       k_onchip<true><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv, out,
                                                          out_v, c.kt, P, ptab, c.status);
     } else {
-      if ((e = cudaFuncSetAttribute(k_onchip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sm)))
-        return e;
+      if ((e = allow_max_smem((const void*)k_onchip<false>))) return e;
       k_onchip<false><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv,
                                                           out, out_v, c.kt, P, ptab, c.status);
     }

@@ -135,7 +135,7 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
   k_static_prepare<<<grid, 256, 0, st>>>(d_offsets, S, n_total, seed, P,
                                          (const uint64_t*)d_keys_in, kt == PCF_KEY_F64 ? 1u : 0u,
                                          brec, ptab, status);
-  if (cudaGetLastError() != cudaSuccess) return PCF_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return PCF_ERR_CUDA;  // nothing was launched
   uint32_t h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -151,8 +151,10 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
   lc.status = status;
   lc.launches = nullptr;
   if (launch_onchip(lc, brec, S, kStCap, (const uint64_t*)d_keys_in, nullptr,
-                    (uint64_t*)d_keys_out, nullptr, P, ptab, lists, status + 16) != cudaSuccess)
+                    (uint64_t*)d_keys_out, nullptr, P, ptab, lists, status + 16) != cudaSuccess) {
+    cudaStreamSynchronize(st);  // return with none of this call's work in flight
     return PCF_ERR_CUDA;
+  }
   if (cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return PCF_ERR_CUDA;

@@ -174,9 +174,11 @@ class SortServer:
                         out.view(torch.int64).copy_(buf_out[int(o):int(o) + r.n],
                                                     non_blocking=True)
                         r.out = out
-                stream.synchronize()
             except Exception as e:  # reported per request, the server keeps going
                 err = e
+            finally:
+                # nothing of this batch may still run when its buffers are reused
+                stream.synchronize()
             t1 = time.perf_counter()
             with self.lock:
                 for r in batch:
