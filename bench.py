@@ -395,6 +395,10 @@ def run_secondary(args):
         ko, vo = torch.empty_like(tk), torch.empty_like(tv)
         ms = timed(lambda: ctx.sort_pairs(tk, tv, ko, vo, key_type="u64"), max(1, args.steps))
         st = ctx.last_stats()
+        # sorted as unsigned keys, and equal keys in input order (payload = index)
+        flip = torch.tensor(-2**63, dtype=torch.int64, device="cuda")
+        a, b = ko[:-1] ^ flip, ko[1:] ^ flip
+        assert bool(((a < b) | ((a == b) & (vo[:-1] < vo[1:]))).all()), "pairs not stably sorted"
         line.update(metric=METRIC, value=n / ms / 1e6, ms_per_sort=ms, dtype="u64",
                     stats=st,
                     config={"workload": "PCF sort, n = 2^28 uint64 keys, Zipf(1.2) over 10^7 "
