@@ -133,15 +133,15 @@ struct BinModel {
   uint64_t lo_bits;  // raw bits of lo
   double lo_d;       // lo as binary64 (f64 keys)
   double s;          // beta / range
-  uint64_t LOw;      // X(lo) modulo 2^64 (f64) / lo (u64)
+  uint64_t LOw;      // X(lo) modulo 2^64 (f64, mode 0) / lo's 52-bit fraction (modes 1, 2) / lo (u64)
   uint64_t sig;      // significand of s << 11, in [2^63, 2^64)
   uint64_t eu;       // error bound in V units
   int32_t C;         // f64: X(y) shifts the significand by max(e,1) - C
-  int32_t w;         // u64: Dn = (x - lo) << w (w < 0: >> -w)
+  int32_t w;         // u64: Dn = (x - lo) << w (w < 0: >> -w); f64 modes 1, 2: the shift
   int32_t F;         // fractional bits of V
   uint32_t beta;
   uint32_t kt;
-  uint32_t pad;
+  uint32_t mode;     // f64: 0 general; 1 / 2: lo and hi share sign and exponent (+ / -)
 };
 
 PCF_HD double as_f64(uint64_t b) {
@@ -223,7 +223,7 @@ PCF_HD int make_bin_model(uint32_t kt, uint64_t lo_bits, uint64_t hi_bits, uint3
   M->kt = kt;
   M->beta = beta;
   M->lo_bits = lo_bits;
-  M->pad = 0;
+  M->mode = 0;
   double r;
   int32_t H;  // grid exponent: X(y) ~ y / 2^H
   if (kt == KEY_F64) {
@@ -265,12 +265,29 @@ PCF_HD int make_bin_model(uint32_t kt, uint64_t lo_bits, uint64_t hi_bits, uint3
   const int32_t ex = M->F - 52;
   e2 = ex >= 0 ? e2 * (double)(1ull << ex) : e2 / (double)(1ull << (-ex));
   M->eu = (uint64_t)e2 + 8ull;
+  // lo and hi with the same sign and exponent: so has every key between
+  // them, X(y) is its 52-bit fraction shifted by one fixed amount, and Dn is
+  // the difference of fractions shifted (the same integer as the general
+  // formula, without a per-key exponent)
+  if (kt == KEY_F64 && (lo_bits >> 52) == (hi_bits >> 52)) {
+    const uint32_t e = (uint32_t)(lo_bits >> 52) & 0x7FFu;
+    const int32_t sh = (int32_t)(e ? e : 1u) - M->C;
+    if (sh >= 0 && sh < 64) {
+      M->mode = (lo_bits >> 63) ? 2u : 1u;
+      M->LOw = lo_bits & 0x000FFFFFFFFFFFFFull;
+      M->w = sh;
+    }
+  }
   return 0;
 }
 
 // Dn of a key (see above)
 PCF_HD uint64_t bin_dn(const BinModel& M, uint64_t xbits) {
-  if (M.kt == KEY_F64) return fixed_mod(xbits, M.C) - M.LOw;
+  if (M.kt == KEY_F64) {
+    if (M.mode == 0) return fixed_mod(xbits, M.C) - M.LOw;
+    const uint64_t fx = xbits & 0x000FFFFFFFFFFFFFull;
+    return (M.mode == 1 ? fx - M.LOw : M.LOw - fx) << M.w;
+  }
   const uint64_t d = xbits - M.LOw;
   return M.w >= 0 ? (d << M.w) : (d >> (-M.w));
 }

@@ -53,8 +53,8 @@ def test_sample_index_matches_oracle(P):
 def _models(seed):
     g = np.random.Generator(np.random.PCG64(seed))
     out = []
-    for kind in ("normal", "uniform", "lognormal", "wide", "clustered", "dyadic", "u64", "u64wide",
-                 "u64small", "subnormal", "zerocross"):
+    for kind in ("normal", "uniform", "lognormal", "wide", "clustered", "clustered_neg", "narrow",
+                 "binade_cross", "dyadic", "u64", "u64wide", "u64small", "subnormal", "zerocross"):
         if kind == "normal":
             x = g.standard_normal(5000) * 10.0 ** g.uniform(-5, 5)
         elif kind == "uniform":
@@ -64,7 +64,14 @@ def _models(seed):
         elif kind == "wide":
             x = np.concatenate([g.standard_normal(2500) * 1e300, g.standard_normal(2500) * 1e-300])
         elif kind == "clustered":
+            # one sign and exponent for all keys (the models' fixed-shift mode)
             x = 1e10 + g.random(5000) * 1e-3
+        elif kind == "clustered_neg":
+            x = -(1e10 + g.random(5000) * 1e-3)
+        elif kind == "narrow":
+            x = 1.0 + g.random(5000) * 2.0 ** -30
+        elif kind == "binade_cross":
+            x = 2.0 + (g.random(5000) - 0.5) * 2.0 ** -20
         elif kind == "dyadic":
             x = g.integers(-512, 512, 5000).astype(np.float64) / 8.0
         elif kind == "u64":
