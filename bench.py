@@ -202,7 +202,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N, help="keys per array (default 10^8)")
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "small", "zipf", "batched", "serve"],
+                    choices=["plain", "small", "zipf", "batched", "serve", "dupinject"],
                     help="plain: the default 4 x 10^8 f64 line; the others are the "
                          "secondary configurations")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
@@ -403,6 +403,23 @@ def run_secondary(args):
                     stats=st,
                     config={"workload": "PCF sort, n = 2^28 uint64 keys, Zipf(1.2) over 10^7 "
                                         "hashed values, uint32 payload = index (stable pairs)"})
+    elif args.workload == "dupinject":
+        # the appendix's adversarial input at GPU scale: 5x10^7 Normal(0,1)
+        # keys plus as many copies of one value drawn in [min, max], shuffled
+        x = W.inject_duplicates(W.f64_keys("normal", 5 * 10**7, 9), seed=9)
+        n = x.size
+        t = torch.from_numpy(x).cuda()
+        o = torch.empty_like(t)
+        ms = timed(lambda: ctx.sort_keys(t, o, key_type="f64"), max(3, args.steps))
+        st = ctx.last_stats()
+        b = o.view(torch.int64)
+        flip = torch.tensor(2**63 - 1, dtype=torch.int64, device="cuda")
+        ok = torch.where(b < 0, b ^ flip, b)
+        assert bool((ok[1:] >= ok[:-1]).all()), "output not sorted"
+        line.update(metric=METRIC, value=n / ms / 1e6, ms_per_sort=ms, dtype="f64", stats=st,
+                    config={"workload": "duplicate injection (appendix): 5x10^7 Normal(0,1) "
+                                        "float64 keys + 5x10^7 copies of one value in [min, max], "
+                                        "shuffled, keys only", "n": n})
     elif args.workload == "batched":
         keys, offs, _ = W.batched_f64(2048, seed=6)
         total = int(offs[-1])
