@@ -93,6 +93,8 @@ typedef struct {
                                 histogram 12, scatter 22 and 18, on-chip 16, fallback 16
                                 per merge pass, per key; + values)                */
   uint64_t kernel_launches;  /* this library's kernel launches in the call       */
+  uint64_t fallback_splits;  /* fallback items split three ways around a value that
+                                dominates them (below / equal / above)          */
 } pcf_call_stats;
 
 /* Creates a context on `device`.  The context owns its workspace (grown on

@@ -83,6 +83,7 @@ struct pcf_ctx {
   DevBuf olist;                  // on-chip buckets listed by size class
   DevBuf jbuf;                   // bucket id of every key of a level
   DevBuf small_segs;             // range records of the on-chip arrays (level 0)
+  DevBuf fb_cnt;                 // per-tile part counts of the three-way splits
   HostBuf h_stage, h_lout, h_status, h_items;
   HostBuf h_stage_small;  // range records of the on-chip arrays (level 0)
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
@@ -367,6 +368,163 @@ struct Timer {
 };
 
 constexpr uint64_t kSpinLimit = 1ull << 24;
+
+// Rounds of three-way splits before the merge sort takes every item left.
+constexpr uint32_t kSplitRounds = 8;
+
+uint32_t tiles_of(uint64_t n, uint32_t tile) { return (uint32_t)((n + tile - 1) / tile); }
+
+// The standard sort of one level's fallback items (failure-guard buckets,
+// |c| >= delta, and degenerate ones), keys in C, scratch D (both free at
+// the items' offsets), result in out.  Per round: the range of every item
+// and the most frequent value of a sample of it; an item that one value
+// dominates is split stably into below / equal / above (the equal part is
+// final, the others go to the next round, their keys now in D, so C and D
+// swap), every other item is merge-sorted.  Equal keys keep their order
+// throughout, so the pair sorts stay stable.
+pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> work, uint64_t* C,
+                        uint32_t* Cv, uint64_t* D, uint32_t* Dv, uint64_t* out_k, uint32_t* out_v,
+                        uint32_t* tile_counter, uint64_t spin_limit) {
+  const cudaStream_t st = lc.stream;
+  const uint64_t kv = lc.pairs ? 12 : 8;  // bytes per key (+ value)
+  for (uint32_t round = 0; !work.empty(); ++round) {
+    const uint32_t nf = (uint32_t)work.size();
+    const bool try_split = round < kSplitRounds;
+    // device layout of the round: items | sort items | split items | done
+    // items (at most three parts per split item)
+    CK(ensure(ctx->fb_items, (size_t)6 * nf * sizeof(FbItem)));
+    CK(ensure(ctx->fb_bases, ((size_t)6 * nf + 4) * 4));
+    CK(ensure(ctx->fb_lohi, (size_t)9 * nf * 8 + (size_t)nf * 4 + 64));
+    FbItem* d_items = as<FbItem>(ctx->fb_items);
+    FbItem* d_items_s = d_items + nf;
+    FbItem* d_items_p = d_items + 2 * nf;
+    FbItem* d_items_d = d_items + 3 * nf;
+    uint32_t* d_rb = as<uint32_t>(ctx->fb_bases);
+    uint32_t* d_mb_s = d_rb + (nf + 1);
+    uint32_t* d_mb_p = d_mb_s + (nf + 1);
+    uint32_t* d_mb_d = d_mb_p + (nf + 1);
+    uint64_t* d_lohi = as<uint64_t>(ctx->fb_lohi);
+    uint64_t* d_pivot = d_lohi + 2 * nf;
+    uint64_t* d_lohi_s = d_pivot + nf;
+    uint64_t* d_piv_p = d_lohi_s + 2 * nf;
+    uint64_t* d_item_cnt = d_piv_p + nf;
+    uint32_t* d_dom = (uint32_t*)(d_item_cnt + 3 * nf);
+
+    std::vector<uint32_t> rb(nf + 1, 0);
+    for (uint32_t i = 0; i < nf; ++i) rb[i + 1] = rb[i] + tiles_of(work[i].n, kRangeTile);
+    std::vector<uint64_t> lohi(2 * nf);
+    for (uint32_t i = 0; i < nf; ++i) {
+      lohi[2 * i] = ~0ull;
+      lohi[2 * i + 1] = 0;
+    }
+    CK(cudaMemcpyAsync(d_items, work.data(), nf * sizeof(FbItem), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_rb, rb.data(), (nf + 1) * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_lohi, lohi.data(), nf * 16, cudaMemcpyHostToDevice, st));
+    CK(launch_fb_range(lc, d_items, nf, d_rb, rb[nf], C, d_lohi));
+    std::vector<uint64_t> pivot(nf, 0);
+    std::vector<uint32_t> dom(nf, 0);
+    if (try_split) CK(launch_fb_mode(lc, d_items, nf, C, d_lohi, d_pivot, d_dom));
+    CK(cudaMemcpyAsync(lohi.data(), d_lohi, nf * 16, cudaMemcpyDeviceToHost, st));
+    if (try_split) {
+      CK(cudaMemcpyAsync(pivot.data(), d_pivot, nf * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(dom.data(), d_dom, nf * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+
+    std::vector<FbItem> sw_items, sp_items;
+    std::vector<uint64_t> lohi_s, piv_p;
+    std::vector<uint32_t> mb_s(1, 0), mb_p(1, 0);
+    uint64_t max_n_s = 0, keys_s = 0, keys_p = 0;
+    for (uint32_t i = 0; i < nf; ++i) {
+      const FbItem& it = work[i];
+      if (dom[i]) {
+        sp_items.push_back(it);
+        piv_p.push_back(pivot[i]);
+        mb_p.push_back(mb_p.back() + tiles_of(it.n, kMergeTile));
+        keys_p += it.n;
+      } else {
+        sw_items.push_back(it);
+        lohi_s.push_back(lohi[2 * i]);
+        lohi_s.push_back(lohi[2 * i + 1]);
+        mb_s.push_back(mb_s.back() + tiles_of(it.n, kMergeTile));
+        max_n_s = std::max<uint64_t>(max_n_s, it.n);
+        keys_s += it.n;
+      }
+    }
+    ctx->stats.bytes_moved += (keys_s + keys_p) * 8;  // the range pass
+    // merge sort: block sort, the merge passes up to the largest item, the copy
+    if (const uint32_t ns = (uint32_t)sw_items.size()) {
+      uint32_t passes = 2;
+      for (uint64_t run = kMergeTile; run < max_n_s; run *= 2) ++passes;
+      ctx->stats.bytes_moved += keys_s * 2 * kv * passes;
+      CK(cudaMemcpyAsync(d_items_s, sw_items.data(), ns * sizeof(FbItem), cudaMemcpyHostToDevice,
+                         st));
+      CK(cudaMemcpyAsync(d_mb_s, mb_s.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_lohi_s, lohi_s.data(), ns * 16, cudaMemcpyHostToDevice, st));
+      CK(launch_fb_sort(lc, d_items_s, ns, d_mb_s, mb_s[ns], max_n_s, d_lohi_s, C, D, Cv, Dv,
+                        out_k, out_v));
+    }
+    std::vector<FbItem> next;
+    if (const uint32_t np = (uint32_t)sp_items.size()) {
+      const uint32_t mp = mb_p[np];
+      ctx->stats.bytes_moved += keys_p * (8 + 2 * kv);  // count, then move
+      ctx->stats.fallback_splits += np;
+      CK(ensure(ctx->fb_cnt, (size_t)3 * (mp + 1) * 4));
+      CK(ensure(ctx->sw, ((size_t)tiles_of(3 * (uint64_t)(mp + 1), kScanTile) + 8) * 8));
+      CK(cudaMemcpyAsync(d_items_p, sp_items.data(), np * sizeof(FbItem), cudaMemcpyHostToDevice,
+                         st));
+      CK(cudaMemcpyAsync(d_mb_p, mb_p.data(), (np + 1) * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_piv_p, piv_p.data(), np * 8, cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(d_item_cnt, 0, (size_t)np * 24, st));
+      uint32_t* cnt = as<uint32_t>(ctx->fb_cnt);
+      CK(launch_fb_part_count(lc, d_items_p, np, d_mb_p, mp, C, d_piv_p, cnt, d_item_cnt));
+      CK(launch_scan(lc, cnt, 3 * (uint64_t)(mp + 1), nullptr, as<uint64_t>(ctx->sw),
+                     tile_counter, 0xFFFFFFFFu, spin_limit, nullptr));
+      CK(launch_fb_part_scatter(lc, d_items_p, np, d_mb_p, mp, C, Cv, d_piv_p, cnt, D, Dv));
+      std::vector<uint64_t> part(3 * (size_t)np);
+      uint32_t stw = 0;
+      CK(cudaMemcpyAsync(part.data(), d_item_cnt, (size_t)np * 24, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&stw, lc.status, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
+      // the parts: below and above go round again (unless they are too short
+      // to need sorting), the equal part is final; every final part is in D
+      std::vector<FbItem> done;
+      std::vector<uint32_t> mb_d(1, 0);
+      for (uint32_t i = 0; i < np; ++i) {
+        const uint64_t nl = part[3 * i], ne = part[3 * i + 1], ng = part[3 * i + 2];
+        if (nl + ne + ng != sp_items[i].n || ne == 0) return PCF_ERR_INTERNAL;
+        const FbItem parts[3] = {{sp_items[i].off, nl},
+                                 {sp_items[i].off + nl, ne},
+                                 {sp_items[i].off + nl + ne, ng}};
+        for (int q = 0; q < 3; ++q) {
+          if (!parts[q].n) continue;
+          if (q != 1 && parts[q].n > 1) {
+            next.push_back(parts[q]);
+          } else {
+            done.push_back(parts[q]);
+            mb_d.push_back(mb_d.back() + tiles_of(parts[q].n, kMergeTile));
+          }
+        }
+      }
+      if (D != out_k && !done.empty()) {
+        const uint32_t nd = (uint32_t)done.size();
+        uint64_t done_keys = 0;
+        for (const FbItem& it : done) done_keys += it.n;
+        ctx->stats.bytes_moved += done_keys * 2 * kv;
+        CK(cudaMemcpyAsync(d_items_d, done.data(), nd * sizeof(FbItem), cudaMemcpyHostToDevice,
+                           st));
+        CK(cudaMemcpyAsync(d_mb_d, mb_d.data(), (nd + 1) * 4, cudaMemcpyHostToDevice, st));
+        CK(launch_fb_move(lc, d_items_d, nd, d_mb_d, mb_d[nd], D, out_k, Dv, out_v));
+      }
+    }
+    CK(cudaStreamSynchronize(st));
+    work.swap(next);
+    std::swap(C, D);
+    std::swap(Cv, Dv);
+  }
+  return PCF_OK;
+}
 
 
 // The whole sort of a batch of arrays.  Level-0 segments are the caller's
@@ -666,44 +824,19 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     uint64_t level_fb_keys = 0;
     // standard sort of the large failure-guard / degenerate buckets
     if (lo.n_fb) {
-      const uint32_t nf = lo.n_fb;
-      std::vector<FbItem> items(nf);
-      CK(cudaMemcpy(items.data(), ctx->fb.p, nf * sizeof(FbItem), cudaMemcpyDeviceToHost));
-      std::vector<uint32_t> rb(nf + 1, 0), mb(nf + 1, 0);
-      uint64_t max_n = 0;
-      for (uint32_t i = 0; i < nf; ++i) {
-        rb[i + 1] = rb[i] + (uint32_t)((items[i].n + kRangeTile - 1) / kRangeTile);
-        mb[i + 1] = mb[i] + (uint32_t)((items[i].n + kMergeTile - 1) / kMergeTile);
-        max_n = std::max<uint64_t>(max_n, items[i].n);
-        level_fb_keys += items[i].n;
-      }
+      std::vector<FbItem> items(lo.n_fb);
+      CK(cudaMemcpyAsync(items.data(), ctx->fb.p, lo.n_fb * sizeof(FbItem),
+                         cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (const FbItem& it : items) level_fb_keys += it.n;
       ctx->stats.fallback_keys += level_fb_keys;
-      // block sort, then merge passes up to the largest item, then the copy
-      uint32_t passes = 2;
-      for (uint64_t run = kMergeTile; run < max_n; run *= 2) ++passes;
-      ctx->stats.bytes_moved += level_fb_keys * (pairs ? 24 : 16) * passes;
-      ctx->stats.fallback_buckets += nf;
-      const size_t need2 = (nf + 1) * 8 + 64;
-      CK(ensure(ctx->fb_bases, need2));
-      CK(ensure(ctx->fb_lohi, nf * 16 + 16));
-      std::vector<uint64_t> lohi(2 * nf);
-      for (uint32_t i = 0; i < nf; ++i) {
-        lohi[2 * i] = ~0ull;
-        lohi[2 * i + 1] = 0;
-      }
-      CK(cudaMemcpyAsync(ctx->fb_bases.p, rb.data(), (nf + 1) * 4, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync((char*)ctx->fb_bases.p + (nf + 1) * 4, mb.data(), (nf + 1) * 4,
-                         cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(ctx->fb_lohi.p, lohi.data(), nf * 16, cudaMemcpyHostToDevice, st));
-      CK(launch_fb_range(lc, as<FbItem>(ctx->fb), nf, as<uint32_t>(ctx->fb_bases), rb[nf], X,
-                         as<uint64_t>(ctx->fb_lohi)));
+      ctx->stats.fallback_buckets += lo.n_fb;
       // scratch: the buffer that is not X (the items' ranges there are free)
       uint64_t* Y = (X == tmp_k) ? out_k : tmp_k;
       uint32_t* Yv = (X == tmp_k) ? out_v : tmp_v;
-      CK(launch_fb_sort(lc, as<FbItem>(ctx->fb), nf,
-                        (const uint32_t*)((char*)ctx->fb_bases.p + (nf + 1) * 4), mb[nf], max_n,
-                        as<uint64_t>(ctx->fb_lohi), X, Y, Xv, Yv, out_k, out_v));
-      CK(cudaStreamSynchronize(st));
+      const pcf_status fs = run_fallback(ctx, lc, std::move(items), X, Xv, Y, Yv, out_k, out_v,
+                                         tile_counter, spin_limit);
+      if (fs != PCF_OK) return fs;
       tm.mark(7);
     }
     // keys finished on chip (or copied as one value) this level: read and

@@ -230,6 +230,32 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
 cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                             const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
                             uint64_t* ord_lohi);
+// Duplicate-heavy items: a value that holds at least a quarter of a sample
+// of kModeSample keys marks the item dominant (pivot[i] = that total-order
+// value, dom[i] = 1; items with one value are never dominant).
+constexpr uint32_t kModeSample = 256;
+cudaError_t launch_fb_mode(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
+                           const uint64_t* keys, const uint64_t* ord_lohi, uint64_t* pivot,
+                           uint32_t* dom);
+// Stable three-way split of every item around its pivot (below, equal,
+// above), keys -> dst at the item's own offsets, in kMergeTile tiles:
+// counting writes cnt[3][n_tiles + 1] (the last column zero), the caller
+// scans the rows (exclusive; one scan of all three rows in a row serves, as
+// only differences within a row are used), then the scatter places every
+// key.  item_cnt[3 i + p] (zeroed by the caller) receives item i's part sizes.
+cudaError_t launch_fb_part_count(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
+                                 const uint32_t* mtile_base, uint32_t n_mtiles,
+                                 const uint64_t* keys, const uint64_t* pivot, uint32_t* cnt,
+                                 uint64_t* item_cnt);
+cudaError_t launch_fb_part_scatter(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
+                                   const uint32_t* mtile_base, uint32_t n_mtiles,
+                                   const uint64_t* keys, const uint32_t* vals,
+                                   const uint64_t* pivot, const uint32_t* cnt_ex, uint64_t* dst,
+                                   uint32_t* dst_v);
+// copies every item's keys (and values) src -> dst
+cudaError_t launch_fb_move(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
+                           const uint32_t* mtile_base, uint32_t n_mtiles, const uint64_t* src,
+                           uint64_t* dst, const uint32_t* src_v, uint32_t* dst_v);
 // sorts the items in `keys` (scratch `tmp`), leaving the result in `final`
 cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                            const uint32_t* mtile_base, uint32_t n_mtiles, uint64_t max_n,
