@@ -72,8 +72,10 @@ typedef struct {
 /* Implementation knobs.  They change speed only, never the result or the
  * model: max_digit_bits = widest bucket-id digit scattered per global pass
  * (4..12); tile_log2 = log2 of keys per count tile of a global pass (12..18);
- * leaf_cap = the largest bucket finished on chip (64..1024, power of two).
- * Zero fields keep the current value.  Default: {11, 14, 1024}. */
+ * leaf_cap = the largest bucket finished on chip (64..8192, power of two; key-
+ * value sorts use at most 1024, and a smaller one where the policy's tables
+ * would not fit shared memory).
+ * Zero fields keep the current value.  Default: {11, 14, 4096}. */
 typedef struct {
   uint32_t max_digit_bits;
   uint32_t tile_log2;

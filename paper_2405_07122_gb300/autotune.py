@@ -16,7 +16,7 @@ from . import pcfsort
 DEFAULT_GRID = {
     "max_digit_bits": (10, 11),
     "tile_log2": (14, 15),
-    "leaf_cap": (512, 1024),
+    "leaf_cap": (1024, 4096),
 }
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")

@@ -70,7 +70,7 @@ struct pcf_ctx {
   int device = 0;
   int num_sms = 0;
   Policy policy{3, 3, 3, 3, 4, 0, 100};
-  pcf_tuning tuning{11, 14, 1024};
+  pcf_tuning tuning{11, 14, 4096};
   std::string last_err;
   pcf_call_stats stats{};
   bool timing = false;
@@ -553,7 +553,10 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   CK(ensure(ctx->lout, sizeof(LevelOut) + 64));
   CK(ensure(ctx->misc, 256));
   const uint32_t tile_keys = 1u << ctx->tuning.tile_log2;
-  const uint32_t cap = ctx->tuning.leaf_cap;
+  // the largest bucket finished on chip (the alpha..delta table covers the
+  // tuning's leaf_cap, at least this)
+  const uint32_t cap = onchip_cap(ctx->tuning.leaf_cap, ctx->policy, pairs);
+  const size_t olist_per_bucket = (size_t)4 * onchip_classes(cap);
   CK(ensure_ptab(ctx, st));
   const uint16_t* ptab = as<uint16_t>(ctx->ptab);
   Timer tm(ctx, st);
@@ -609,7 +612,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     memcpy(ctx->h_items.p, recs.data(), S * sizeof(BRec));
     CK(cudaMemcpyAsync(ctx->small_items.p, ctx->h_items.p, S * sizeof(BRec),
                        cudaMemcpyHostToDevice, st));
-    CK(ensure(ctx->olist, (size_t)S * 12));
+    CK(ensure(ctx->olist, (size_t)S * olist_per_bucket));
     CK(launch_onchip(lc, as<BRec>(ctx->small_items), S, cap, in_k, in_v, out_k, out_v,
                      ctx->policy, ptab, as<uint32_t>(ctx->olist),
                      (uint32_t*)((char*)ctx->misc.p + 128)));
@@ -795,7 +798,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                       as<uint32_t>(ctx->cmat1), as<uint32_t>(ctx->cmat2), L.two_pass, cap,
                       (uint32_t)ctx->policy.tau, X, Xv, out_k, out_v, as<BRec>(ctx->leaf),
                       next_flag, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
-    CK(ensure(ctx->olist, (size_t)L.n_buckets * 12));
+    CK(ensure(ctx->olist, (size_t)L.n_buckets * olist_per_bucket));
     CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k, out_v,
                      ctx->policy, ptab, as<uint32_t>(ctx->olist),
                      (uint32_t*)((char*)ctx->misc.p + 128)));
@@ -943,11 +946,7 @@ pcf_status pcf_ctx_set_tuning(pcf_ctx* ctx, const pcf_tuning* t) {
   if (t->leaf_cap) n.leaf_cap = t->leaf_cap;
   if (n.max_digit_bits < 4 || n.max_digit_bits > kMaxDigitBits) return PCF_ERR_INVALID_ARG;
   if (n.tile_log2 < 12 || n.tile_log2 > 18) return PCF_ERR_INVALID_ARG;
-  if (n.leaf_cap < 64 || n.leaf_cap > 1024 || (n.leaf_cap & (n.leaf_cap - 1))) return PCF_ERR_INVALID_ARG;
-  // the largest on-chip slice (keys, values and tables) must fit one block's
-  // shared memory
-  if (onchip_smem_bytes(n.leaf_cap, ctx->policy, true) > 227 * 1024)
-    return PCF_ERR_INVALID_ARG;
+  if (n.leaf_cap < 64 || n.leaf_cap > 8192 || (n.leaf_cap & (n.leaf_cap - 1))) return PCF_ERR_INVALID_ARG;
   ctx->tuning = n;
   return PCF_OK;
 }

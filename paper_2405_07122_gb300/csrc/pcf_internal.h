@@ -222,8 +222,14 @@ struct OnchipGeo {
   uint32_t bytes;  // shared memory of one warp's slice
 };
 OnchipGeo onchip_geometry(uint32_t capw, const Policy& P, bool pairs);
-size_t onchip_smem_bytes(uint32_t capw, const Policy& P, bool pairs);
-// lists: 3 nb u32 of scratch; counts: 3 u32 of scratch
+// Size classes of the on-chip finish: (0, 256], (256, 512], ..., up to
+// 8192 keys; onchip_classes(cap) of them are used below leaf_cap = cap.
+constexpr uint32_t kMaxClasses = 6;
+uint32_t onchip_classes(uint32_t leaf_cap);
+// The largest bucket finished on chip: leaf_cap (key-value sorts at most
+// 1024), halved until the policy's slice fits one block's shared memory.
+uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs);
+// lists: onchip_classes(leaf_cap) nb u32 of scratch; counts: kMaxClasses u32
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts);

@@ -681,6 +681,7 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
 }
 
 constexpr uint32_t kTiny = 16;  // buckets this small are sorted by one thread
+constexpr uint32_t kStdLeafMax = 1024;
 
 template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, uint64_t n_buckets,
@@ -767,7 +768,9 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     }
     v = false;
   }
-  const bool is_fb = v && size >= sg->delta && size > leaf_cap;
+  // a failure-guard bucket is sorted on chip only up to kStdLeafMax keys
+  // (there one warp runs the Standard-Sort); larger ones go to the fallback
+  const bool is_fb = v && size >= sg->delta && size > min(leaf_cap, kStdLeafMax);
   const bool is_leaf = v && !is_fb && size <= leaf_cap;
   const bool is_next = v && !is_fb && !is_leaf;
   if (in) {

@@ -469,19 +469,24 @@ __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, 
   return ok;
 }
 
-// The leaf records of each size class, compacted (a thread per record).
-constexpr uint32_t kClasses = 3;
-__global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t b1, uint32_t b2,
+// The leaf records of each size class, compacted (a thread per record):
+// class 0 holds the buckets of at most 256 keys, class c > 0 those of
+// (128 << c, 256 << c] keys.
+__device__ __forceinline__ uint32_t size_class(uint32_t n) {
+  return n <= 256 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 8u;
+}
+
+__global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t ncls,
                              uint32_t* lists, uint32_t* counts) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31;
-  uint32_t cls = kClasses;
+  uint32_t cls = kMaxClasses;
   if (i < nb) {
     const BRec r = br[i];
-    if ((r.kind & BK_LEAF) && r.n > 0) cls = r.n <= b1 ? 0u : (r.n <= b2 ? 1u : 2u);
+    if ((r.kind & BK_LEAF) && r.n > 0) cls = min(size_class(r.n), ncls - 1);
   }
 #pragma unroll
-  for (uint32_t k = 0; k < kClasses; ++k) {
+  for (uint32_t k = 0; k < kMaxClasses; ++k) {
     const uint32_t bal = __ballot_sync(~0u, cls == k);
     if (!bal) continue;
     const int leader = __ffs(bal) - 1;
@@ -558,28 +563,30 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Buckets of more than 256 keys (keys only): the two warps of a CTA share
-// one bucket, so that its critical path is about half as long, and twice as
-// many buckets as four-warp CTAs would allow stay in flight per SM.  The
-// same steps as learn_step; scans and Standard-Sorts of whole calls run in
-// warp 0.
+// Buckets of more than 256 keys (keys only): the NT threads of a CTA share
+// one bucket.  Up to 1024 keys two warps (so that a bucket's critical path
+// is about half as long, and twice as many buckets as four-warp CTAs would
+// allow stay in flight per SM); above, NT grows with the bucket (128 threads
+// up to 2048 keys, 256 up to 4096, 512 up to 8192), so that a bucket up to
+// 8192 keys -- 128 KB of keys plus the scatter target, one CTA per SM -- is
+// still finished in shared memory instead of by another global level.  The
+// same steps as learn_step; Standard-Sorts of whole calls run in warp 0.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kCta = 64;
-
+template <uint32_t NT>
 struct CtaShared {
-  uint64_t mn[kCta / 32], mx[kCta / 32];
-  uint32_t wsum[kCta / 32];
+  uint64_t mn[NT / 32], mx[NT / 32];
+  uint32_t wsum[NT / 32];
   uint32_t top, flag, ovf;
 };
 
 // Scan of src[0..m) into dst by the CTA (each thread a contiguous run, one
 // barrier; src may be dst).  EXCL: exclusive sums.  Otherwise the inclusive
 // sums b_k turned into the bucket table floor(b_k gamma / alpha).
-template <bool EXCL>
+template <uint32_t NT, bool EXCL>
 __device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uint32_t m,
-                                         uint32_t alpha, uint32_t gamma, CtaShared& sh) {
+                                         uint32_t alpha, uint32_t gamma, CtaShared<NT>& sh) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t r = (m + kCta - 1) / kCta;
+  const uint32_t r = (m + NT - 1) / NT;
   const uint32_t a = min(m, tid * r), b = min(m, a + r);
   uint32_t sum = 0;
   for (uint32_t k = a; k < b; ++k) sum += src[k];
@@ -588,7 +595,7 @@ __device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uin
   __syncthreads();
   uint32_t run = inc - sum;
 #pragma unroll
-  for (uint32_t k = 0; k < kCta / 32; ++k) run += k < wid ? sh.wsum[k] : 0u;
+  for (uint32_t k = 0; k < NT / 32; ++k) run += k < wid ? sh.wsum[k] : 0u;
   for (uint32_t k = a; k < b; ++k) {
     const uint32_t v = src[k];
     if (EXCL) {
@@ -602,19 +609,20 @@ __device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uin
 }
 
 // Samples per thread drawn before the model is ready (alpha <= this many
-// times the CTA size for every call of at most 1024 keys under the default
+// times the CTA size for every call of its size class under the default
 // policy; any further samples are drawn after it).
 constexpr uint32_t kSampRegs = 3;
 
 // root: the range was reduced into sh.mn / sh.mx while the keys were loaded
+template <uint32_t NT>
 __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                                uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
-                               CtaShared& sh, bool root) {
+                               CtaShared<NT>& sh, bool root) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t o = it.o, n = it.n;
   uint64_t mn = ~0ull, mx = 0ull;
   if (!root) {
-    for (uint32_t i = tid; i < n; i += kCta) {
+    for (uint32_t i = tid; i < n; i += NT) {
       const uint64_t v = w.A[o + i];
       mn = v < mn ? v : mn;
       mx = v > mx ? v : mx;
@@ -633,7 +641,7 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     __syncthreads();
   }
 #pragma unroll
-  for (uint32_t k = 0; k < kCta / 32; ++k) {
+  for (uint32_t k = 0; k < NT / 32; ++k) {
     mn = sh.mn[k] < mn ? sh.mn[k] : mn;
     mx = sh.mx[k] > mx ? sh.mx[k] : mx;
   }
@@ -642,15 +650,15 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
   if (tid == 0)
     sh.flag = (uint32_t)make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
-  for (uint32_t k = tid; k <= beta; k += kCta) w.tab[k] = 0;
-  for (uint32_t k = tid; k <= gamma; k += kCta) w.cnt[k] = 0;
+  for (uint32_t k = tid; k <= beta; k += NT) w.tab[k] = 0;
+  for (uint32_t k = tid; k <= gamma; k += NT) w.cnt[k] = 0;
   // the sample positions and keys do not depend on the model: draw them
   // while thread 0 builds it
   const uint64_t state = sample_state(seed, it.depth, it.start, n);
   uint64_t sx[kSampRegs];
 #pragma unroll
   for (uint32_t u = 0; u < kSampRegs; ++u) {
-    const uint32_t s = tid + u * kCta;
+    const uint32_t s = tid + u * NT;
     sx[u] = s < alpha ? bits_of_ord(w.A[o + (uint32_t)sample_index(state, s, n)], kt) : 0ull;
   }
   __syncthreads();
@@ -661,14 +669,14 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   const BinModel bm = *w.bm;
 #pragma unroll
   for (uint32_t u = 0; u < kSampRegs; ++u) {
-    if (tid + u * kCta < alpha) {
+    if (tid + u * NT < alpha) {
       bool amb;
       uint32_t bn = bin_fast(bm, sx[u], amb);
       if (amb) bn = bin_exact_of(bm, sx[u]);
       atomicAdd(&w.tab[bn], 1u);
     }
   }
-  for (uint32_t s = tid + kSampRegs * kCta; s < alpha; s += kCta) {
+  for (uint32_t s = tid + kSampRegs * NT; s < alpha; s += NT) {
     const uint64_t x = bits_of_ord(w.A[o + (uint32_t)sample_index(state, s, n)], kt);
     bool amb;
     uint32_t bn = bin_fast(bm, x, amb);
@@ -676,14 +684,14 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     atomicAdd(&w.tab[bn], 1u);
   }
   __syncthreads();
-  cta_scan<false>(w.tab, w.tab, beta + 1, alpha, gamma, sh);
+  cta_scan<NT, false>(w.tab, w.tab, beta + 1, alpha, gamma, sh);
   __syncthreads();
-  for (uint32_t i0 = 0; i0 < n; i0 += 2 * kCta) {
+  for (uint32_t i0 = 0; i0 < n; i0 += 2 * NT) {
     uint64_t x[2];
     uint32_t bn[2], amb = 0;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const uint32_t i = i0 + u * kCta + tid;
+      const uint32_t i = i0 + u * NT + tid;
       x[u] = i < n ? bits_of_ord(w.A[o + i], kt) : bm.lo_bits;
     }
 #pragma unroll
@@ -699,7 +707,7 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const uint32_t i = i0 + u * kCta + tid;
+      const uint32_t i = i0 + u * NT + tid;
       if (i < n) {
         const uint32_t j = w.tab[bn[u]];
         w.J[i] = (uint16_t)j;
@@ -709,16 +717,16 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   }
   __syncthreads();
   // bucket starts into cur (cnt keeps the sizes)
-  cta_scan<true>(w.cnt, w.cur, gamma + 1, 0, 0, sh);
+  cta_scan<NT, true>(w.cnt, w.cur, gamma + 1, 0, 0, sh);
   __syncthreads();
-  for (uint32_t i = tid; i < n; i += kCta) {
+  for (uint32_t i = tid; i < n; i += NT) {
     const uint32_t j = w.J[i];
     const uint32_t pos = atomicAdd(&w.cur[j], 1u);
     w.B[o + pos] = w.A[o + i];
     w.Bj[pos] = (uint16_t)j;
   }
   __syncthreads();
-  for (uint32_t p = tid; p < n; p += kCta) {
+  for (uint32_t p = tid; p < n; p += NT) {
     const uint32_t j = w.Bj[p];
     const uint32_t c = w.cnt[j], e = w.cur[j], s = e - c;
     const uint64_t v = w.B[o + p];
@@ -744,7 +752,8 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   }
 }
 
-__global__ void __launch_bounds__(kCta, 16) k_onchip_cta(const BRec* __restrict__ br,
+template <uint32_t NT>
+__global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(const BRec* __restrict__ br,
                                                         const uint32_t* __restrict__ list,
                                                         const uint32_t* __restrict__ count,
                                                         OnchipGeo geo,
@@ -753,7 +762,7 @@ __global__ void __launch_bounds__(kCta, 16) k_onchip_cta(const BRec* __restrict_
                                                         const uint16_t* __restrict__ ptab,
                                                         uint32_t* status) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ CtaShared sh;
+  __shared__ CtaShared<NT> sh;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const Slice w = carve(smem_raw, geo, false);
   const uint32_t nitems = *count;
@@ -762,7 +771,7 @@ __global__ void __launch_bounds__(kCta, 16) k_onchip_cta(const BRec* __restrict_
     const uint32_t off = r.off, n = r.n;
     {
       uint64_t mn = ~0ull, mx = 0ull;
-      for (uint32_t i = tid; i < n; i += kCta) {
+      for (uint32_t i = tid; i < n; i += NT) {
         const uint64_t v = ord_of(__ldg(X + off + i), kt);
         w.A[i] = v;
         mn = v < mn ? v : mn;
@@ -802,7 +811,7 @@ __global__ void __launch_bounds__(kCta, 16) k_onchip_cta(const BRec* __restrict_
         __syncthreads();
         if (wid == 0) std_sort<false>(w, it.o, it.n, lane);
       } else {
-        learn_step_cta(w, geo, it, r.seed, kt, P, ptab, sh, top == 1 && it.o == 0 && it.n == n);
+        learn_step_cta<NT>(w, geo, it, r.seed, kt, P, ptab, sh, top == 1 && it.o == 0 && it.n == n);
       }
       __syncthreads();
     }
@@ -810,7 +819,7 @@ __global__ void __launch_bounds__(kCta, 16) k_onchip_cta(const BRec* __restrict_
       if (tid == 0) atomicOr(status, STATUS_INTERNAL);
       return;
     }
-    for (uint32_t i = tid; i < n; i += kCta) out[off + i] = bits_of_ord(w.A[i], kt);
+    for (uint32_t i = tid; i < n; i += NT) out[off + i] = bits_of_ord(w.A[i], kt);
     __syncthreads();
   }
 }
@@ -831,10 +840,6 @@ OnchipGeo onchip_geometry(uint32_t capw, const Policy& P, bool pairs) {
   return g;
 }
 
-size_t onchip_smem_bytes(uint32_t capw, const Policy& P, bool pairs) {
-  return (size_t)kWarps * onchip_geometry(capw, P, pairs).bytes;
-}
-
 static int num_sms_of_current_device() {
   static int cached[64] = {0};
   int dev = 0;
@@ -847,42 +852,78 @@ static int num_sms_of_current_device() {
   return cached[dev];
 }
 
+uint32_t onchip_classes(uint32_t leaf_cap) {
+  uint32_t k = 1;
+  for (uint32_t capw = 256; capw < leaf_cap && k < kMaxClasses; capw *= 2) ++k;
+  return k;
+}
+
+// one CTA of NT threads per bucket of the class whose slices are g.bytes
+template <uint32_t NT>
+static cudaError_t launch_cta_class(const LaunchCfg& c, const BRec* br, const uint32_t* list,
+                                    const uint32_t* count, const OnchipGeo& g, const uint64_t* X,
+                                    uint64_t* out, const Policy& P, const uint16_t* ptab) {
+  constexpr uint32_t kMaxPerSm = NT <= 64 ? 16u : 512u / NT;
+  const uint32_t per = max(1u, min(kMaxPerSm, (uint32_t)((227u * 1024u) / (g.bytes + 1024u))));
+  cudaError_t e = allow_max_smem((const void*)k_onchip_cta<NT>);
+  if (e) return e;
+  k_onchip_cta<NT><<<(uint32_t)num_sms_of_current_device() * per, NT, g.bytes, c.stream>>>(
+      br, list, count, g, X, out, c.kt, P, ptab, c.status);
+  return cudaGetLastError();
+}
+
+uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs) {
+  // key-value sorts: the warp kernel (four slices per block), up to 1024
+  // keys; keys only: one slice per block above 256 keys
+  uint32_t cap = pairs ? min(leaf_cap, 1024u) : leaf_cap;
+  while (cap > 64) {
+    const OnchipGeo g = onchip_geometry(cap, P, pairs);
+    const size_t need = (pairs || cap <= 256) ? (size_t)kWarps * g.bytes : (size_t)g.bytes;
+    if (need + 1024 <= 227u * 1024u) break;
+    cap /= 2;
+  }
+  return cap;
+}
+
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts) {
   if (!nb) return cudaSuccess;
-  // size classes (0, 256], (256, 512], (512, 1024], clipped to leaf_cap
-  cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kClasses, c.stream);
+  // size classes (0, 256], (256, 512], (512, 1024], ... clipped to leaf_cap
+  const uint32_t ncls = onchip_classes(leaf_cap);
+  cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kMaxClasses, c.stream);
   if (e) return e;
-  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, 256, 512, lists, counts);
+  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts);
   count_launch(c);
   if ((e = cudaGetLastError())) return e;
   uint32_t cls = 0;
   for (uint32_t capw = 256, lo = 0; lo < leaf_cap; capw *= 2, ++cls) {
     const uint32_t hi = min(capw, leaf_cap);
     const OnchipGeo g = onchip_geometry(hi, P, c.pairs);
-    const size_t sm = (size_t)kWarps * g.bytes;
-    const uint32_t per_sm = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm + 1024u))));
-    const uint32_t grid = (uint32_t)num_sms_of_current_device() * per_sm;
     const uint32_t* list = lists + (size_t)cls * nb;
     if (cls > 0 && !c.pairs) {
-      // a CTA per bucket (one slice per CTA)
-      const size_t sm1 = g.bytes;
-      const uint32_t per1 = max(1u, min(16u, (uint32_t)((227u * 1024u) / (sm1 + 1024u))));
-      if ((e = allow_max_smem((const void*)k_onchip_cta))) return e;
-      k_onchip_cta<<<(uint32_t)num_sms_of_current_device() * per1, kCta, sm1, c.stream>>>(
-          br, list, counts + cls, g, X, out, c.kt, P, ptab, c.status);
-    } else if (c.pairs) {
-      if ((e = allow_max_smem((const void*)k_onchip<true>))) return e;
-      k_onchip<true><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv, out,
-                                                         out_v, c.kt, P, ptab, c.status);
+      // a CTA per bucket (one slice per CTA), more threads for larger buckets
+      if (hi <= 1024) e = launch_cta_class<64>(c, br, list, counts + cls, g, X, out, P, ptab);
+      else if (hi <= 2048) e = launch_cta_class<128>(c, br, list, counts + cls, g, X, out, P, ptab);
+      else if (hi <= 4096) e = launch_cta_class<256>(c, br, list, counts + cls, g, X, out, P, ptab);
+      else e = launch_cta_class<512>(c, br, list, counts + cls, g, X, out, P, ptab);
+      if (e) return e;
     } else {
-      if ((e = allow_max_smem((const void*)k_onchip<false>))) return e;
-      k_onchip<false><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv,
-                                                          out, out_v, c.kt, P, ptab, c.status);
+      const size_t sm = (size_t)kWarps * g.bytes;
+      const uint32_t per_sm = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm + 1024u))));
+      const uint32_t grid = (uint32_t)num_sms_of_current_device() * per_sm;
+      if (c.pairs) {
+        if ((e = allow_max_smem((const void*)k_onchip<true>))) return e;
+        k_onchip<true><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv,
+                                                           out, out_v, c.kt, P, ptab, c.status);
+      } else {
+        if ((e = allow_max_smem((const void*)k_onchip<false>))) return e;
+        k_onchip<false><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv,
+                                                            out, out_v, c.kt, P, ptab, c.status);
+      }
+      if ((e = cudaGetLastError())) return e;
     }
     count_launch(c);
-    if ((e = cudaGetLastError())) return e;
     lo = hi;
   }
   return cudaSuccess;
