@@ -169,6 +169,17 @@ pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_keys_out,
 pcf_status pcf_sort_keys_host(pcf_ctx* ctx, void* h_keys, uint64_t n, pcf_key_type kt,
                               uint64_t seed, void* stream);
 
+/* Several arrays on HOST buffers: array i (ns[i] keys at h_keys[i], sorted in
+ * place, ideally pinned) is sorted exactly as pcf_sort_keys_host would sort
+ * it with seed + i.  The library uploads array i + 1 and downloads array
+ * i - 1 on two copy streams of its own while array i is sorted on `stream`
+ * (three device slots of max ns[i] keys, kept by the context).  Returns when
+ * every array is back on the host; on an error no copy is left in flight and
+ * the arrays after the failing one are unspecified. */
+pcf_status pcf_sort_keys_host_batch(pcf_ctx* ctx, void* const* h_keys, const uint64_t* ns,
+                                    uint32_t count, pcf_key_type kt, uint64_t seed,
+                                    void* stream);
+
 /* Stage timing of the last sort (milliseconds between CUDA events recorded
  * on the sort's stream) when enabled with pcf_ctx_enable_timing(ctx, 1):
  * [0] range (k_range + k_model), [1] sample + PCF table (k_sample),

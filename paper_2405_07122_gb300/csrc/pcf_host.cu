@@ -39,6 +39,37 @@ struct HostBuf {  // pinned staging
   }
 };
 
+// Copy streams and events of the pipelined host-buffer entry point (created
+// on first use, on the context's device).
+constexpr int kPipeSlots = 3;
+struct CopyPipe {
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t loaded[kPipeSlots], sorted[kPipeSlots], stored[kPipeSlots];
+  bool ready = false;
+  cudaError_t init() {
+    if (ready) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking);
+    for (int i = 0; i < kPipeSlots && !e; ++i) {
+      e = cudaEventCreateWithFlags(&loaded[i], cudaEventDisableTiming);
+      if (!e) e = cudaEventCreateWithFlags(&sorted[i], cudaEventDisableTiming);
+      if (!e) e = cudaEventCreateWithFlags(&stored[i], cudaEventDisableTiming);
+    }
+    ready = !e;
+    return e;
+  }
+  ~CopyPipe() {
+    if (!ready) return;
+    cudaStreamDestroy(in);
+    cudaStreamDestroy(out);
+    for (int i = 0; i < kPipeSlots; ++i) {
+      cudaEventDestroy(loaded[i]);
+      cudaEventDestroy(sorted[i]);
+      cudaEventDestroy(stored[i]);
+    }
+  }
+};
+
 }  // namespace
 
 namespace {
@@ -89,6 +120,8 @@ struct pcf_ctx {
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
   uint64_t ptab_key = 0;  // policy/cap the table was built for
   ParamCache pcache;
+  DevBuf pipe_keys;  // kPipeSlots arrays of the pipelined host entry point
+  CopyPipe pipe;
 };
 
 cudaError_t pcf::allow_max_smem(const void* kernel) {
@@ -1060,6 +1093,67 @@ pcf_status pcf_sort_keys_host(pcf_ctx* ctx, void* h_keys, uint64_t n, pcf_key_ty
   if (s != PCF_OK) return s;
   CK(cudaMemcpyAsync(h_keys, ctx->host_keys.p, n * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  return PCF_OK;
+}
+
+// Several arrays on HOST buffers, each sorted as pcf_sort_keys_host would
+// sort it (seed + i for array i), with the copies of one array overlapping
+// the sorts of its neighbours: three device slots rotate through upload
+// (copy stream "in"), sort (the caller's stream) and download (copy stream
+// "out"), ordered by events.  Host buffers should be pinned for the copies
+// to overlap.
+pcf_status pcf_sort_keys_host_batch(pcf_ctx* ctx, void* const* h_keys, const uint64_t* ns,
+                                    uint32_t count, pcf_key_type kt, uint64_t seed,
+                                    void* stream) {
+  if (!ctx || (count && (!h_keys || !ns))) return PCF_ERR_INVALID_ARG;
+  if (kt != PCF_KEY_F64 && kt != PCF_KEY_U64) return PCF_ERR_INVALID_ARG;
+  uint64_t max_n = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (ns[i] > 0xFFFFFFFFull || (ns[i] && !h_keys[i])) return PCF_ERR_INVALID_ARG;
+    max_n = std::max(max_n, ns[i]);
+  }
+  if (max_n == 0) return PCF_OK;
+  CK(cudaSetDevice(ctx->device));
+  CK(ctx->pipe.init());
+  const size_t slot_bytes = (max_n * 8 + 255) & ~(size_t)255;
+  CK(ensure(ctx->pipe_keys, slot_bytes * kPipeSlots));
+  cudaStream_t st = (cudaStream_t)stream;
+  CopyPipe& cp = ctx->pipe;
+  auto slot_ptr = [&](uint32_t i) { return (char*)ctx->pipe_keys.p + (i % kPipeSlots) * slot_bytes; };
+  // upload of array i into its slot, once the download of array i - 3 (the
+  // slot's previous array) has left it
+  auto upload = [&](uint32_t i) -> cudaError_t {
+    const int k = (int)(i % kPipeSlots);
+    cudaError_t e = cudaSuccess;
+    if (i >= (uint32_t)kPipeSlots) e = cudaStreamWaitEvent(cp.in, cp.stored[k], 0);
+    if (!e && ns[i]) e = cudaMemcpyAsync(slot_ptr(i), h_keys[i], ns[i] * 8, cudaMemcpyHostToDevice,
+                                         cp.in);
+    if (!e) e = cudaEventRecord(cp.loaded[k], cp.in);
+    return e;
+  };
+  pcf_status status = PCF_OK;
+  cudaError_t e = upload(0);
+  for (uint32_t i = 0; i < count && !e && status == PCF_OK; ++i) {
+    const int k = (int)(i % kPipeSlots);
+    if (i + 1 < count && (e = upload(i + 1))) break;
+    if ((e = cudaStreamWaitEvent(st, cp.loaded[k], 0))) break;
+    std::vector<InSeg> segs{InSeg{0, ns[i], 0, seed + i, 0}};
+    status = sort_common(ctx, slot_ptr(i), nullptr, slot_ptr(i), nullptr, segs, ns[i], kt, false,
+                         stream);
+    if (status != PCF_OK) break;
+    if ((e = cudaEventRecord(cp.sorted[k], st))) break;
+    if ((e = cudaStreamWaitEvent(cp.out, cp.sorted[k], 0))) break;
+    if (ns[i] && (e = cudaMemcpyAsync(h_keys[i], slot_ptr(i), ns[i] * 8, cudaMemcpyDeviceToHost,
+                                      cp.out)))
+      break;
+    if ((e = cudaEventRecord(cp.stored[k], cp.out))) break;
+  }
+  // return with no copy of this call in flight, whatever happened
+  const cudaError_t e_in = cudaStreamSynchronize(cp.in);
+  const cudaError_t e_out = cudaStreamSynchronize(cp.out);
+  if (status != PCF_OK) return status;
+  if (!e) e = e_in ? e_in : e_out;
+  CK(e);
   return PCF_OK;
 }
 

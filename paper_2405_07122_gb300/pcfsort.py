@@ -77,6 +77,7 @@ def lib():
             "pcf_sort_segmented": [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_u64), _u32,
                                    ctypes.c_int, _u64, _vp],
             "pcf_sort_keys_host": [_vp, _vp, _u64, ctypes.c_int, _u64, _vp],
+            "pcf_sort_keys_host_batch": [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _vp],
             "pcf_sort_segmented_static": [_vp, _vp, _vp, _u32, _u64, ctypes.c_int, _u64, _vp],
             "pcf_debug_scan": [_vp, _vp, _u64, _u32, _u64, _vp],
             "pcf_debug_level0": [_vp, _vp, _u64, ctypes.c_int, _u64, ctypes.POINTER(_u64),
@@ -218,6 +219,30 @@ class Context:
             kt = _kt(key_type or ("f64" if host_keys.dtype == np.float64 else "u64"))
         self._check(lib().pcf_sort_keys_host(self._h, ptr, n, kt, seed, _stream_ptr(stream)))
         return host_keys
+
+    def sort_keys_host_batch(self, host_arrays, key_type=None, seed=0, stream=None):
+        """End-to-end for several host tensors/arrays (ideally pinned), each
+        sorted in place (array i with seed + i); copies overlap the sorts."""
+        ptrs, ns, kts = [], [], set()
+        for h in host_arrays:
+            if hasattr(h, "data_ptr"):
+                ptrs.append(h.data_ptr())
+                ns.append(h.numel())
+                kts.add("f64" if str(h.dtype) == "torch.float64" else "u64")
+            else:
+                ptrs.append(h.ctypes.data)
+                ns.append(h.size)
+                kts.add("f64" if h.dtype == np.float64 else "u64")
+        if not ptrs:
+            return host_arrays
+        if key_type is None and len(kts) != 1:
+            raise ValueError("arrays of different key types")
+        kt = _kt(key_type or kts.pop())
+        P = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        N = (_u64 * len(ns))(*ns)
+        self._check(lib().pcf_sort_keys_host_batch(self._h, P, N, len(ptrs), kt, seed,
+                                                   _stream_ptr(stream)))
+        return host_arrays
 
     # -- self-test hooks ----------------------------------------------------
     def debug_scan(self, data_u32, withhold_tile=0xFFFFFFFF, spin_limit=0, stream=None):

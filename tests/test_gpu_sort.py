@@ -256,6 +256,29 @@ def test_host_end_to_end(ctx):
     assert same_bits(h.numpy(), ref)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_batch_pipelined(ctx, pinned):
+    # more arrays than the three device slots, sizes from empty to 2^21,
+    # each sorted in place exactly as the single-array host call would
+    sizes = [1 << 21, 0, 1, 5000, 300001, 1 << 20, 99, 777777]
+    xs = [W.f64_keys(W.DISTRIBUTIONS[i % len(W.DISTRIBUTIONS)], n, 40 + i)
+          for i, n in enumerate(sizes)]
+    hs = [torch.from_numpy(x.copy()) for x in xs]
+    if pinned:
+        hs = [h.pin_memory() for h in hs]
+    ctx.sort_keys_host_batch(hs, key_type="f64", seed=3)
+    for i, (x, h) in enumerate(zip(xs, hs)):
+        ref, _ = oracle.sort(x, seed=3 + i)
+        assert same_bits(h.numpy(), ref), i
+    # u64 keys, and a second call on the same context (slots reused)
+    us = [W.zipf_u64(n, seed=50 + n % 7, n_values=1000) for n in (123457, 4096, 1 << 19, 2, 65536)]
+    hu = [torch.from_numpy(u.view(np.int64).copy()).pin_memory() for u in us]
+    ctx.sort_keys_host_batch(hu, key_type="u64")
+    for u, h in zip(us, hu):
+        ref, _ = oracle.sort(u)
+        assert same_bits(h.numpy().view(np.uint64), ref)
+
+
 @pytest.mark.parametrize("dist", ["normal"])
 def test_full_size_config2(ctx, dist):
     # n = 10^8 (the benchmark's array size): exact comparison with the oracle
