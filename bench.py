@@ -237,7 +237,9 @@ def main():
     outs = [torch.empty_like(t) for t in ins]
     ctx = pcfsort.Context(local)
     ctx.reserve(n)
-    stream = torch.cuda.current_stream(dev)
+    # the sorts' own stream (created non-blocking by torch): on the legacy
+    # default stream every launch would also order against other streams
+    stream = torch.cuda.Stream(dev)
 
     def step(timing=False):
         st = {k: 0.0 for k in pcfsort.STAGES}

@@ -33,6 +33,7 @@ struct DevBuf {
 
 struct HostBuf {  // pinned staging
   void* p = nullptr;
+  void* dp = nullptr;  // its device view
   size_t cap = 0;
   ~HostBuf() {
     if (p) cudaFreeHost(p);
@@ -117,6 +118,7 @@ struct pcf_ctx {
   DevBuf fb_cnt;                 // per-tile part counts of the three-way splits
   HostBuf h_stage, h_lout, h_status, h_items;
   HostBuf h_stage_small;  // range records of the on-chip arrays (level 0)
+  HostBuf h_fb;           // fallback items and their tables, both ways
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
   uint64_t ptab_key = 0;  // policy/cap the table was built for
   ParamCache pcache;
@@ -188,14 +190,26 @@ cudaError_t ensure_host(HostBuf& b, size_t bytes) {
   if (b.p) cudaFreeHost(b.p);
   b.p = nullptr;
   b.cap = 0;
+  b.dp = nullptr;
   size_t want = bytes + bytes / 4;
   cudaError_t e = cudaMallocHost(&b.p, want);
   if (e != cudaSuccess) {
     b.p = nullptr;
     return e;
   }
+  e = cudaHostGetDevicePointer(&b.dp, b.p, 0);
+  if (e != cudaSuccess) {
+    cudaFreeHost(b.p);
+    b.p = b.dp = nullptr;
+    return e;
+  }
   b.cap = want;
   return cudaSuccess;
+}
+
+// Device view of a pointer into a pinned staging buffer.
+void* dview(const HostBuf& b, const void* hp) {
+  return (char*)b.dp + ((const char*)hp - (const char*)b.p);
 }
 
 template <typename T>
@@ -442,6 +456,28 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
     uint64_t* d_piv_p = d_lohi_s + 2 * nf;
     uint64_t* d_item_cnt = d_piv_p + nf;
     uint32_t* d_dom = (uint32_t*)(d_item_cnt + 3 * nf);
+    // host side of the round's transfers: one pinned arena, filled in order
+    // (every use of the previous round's ended at its last synchronisation)
+    CK(ensure_host(ctx->h_fb, (size_t)256 * nf + 1024));
+    size_t aoff = 0;
+    auto put = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      char* h = (char*)ctx->h_fb.p + aoff;
+      memcpy(h, src, bytes);
+      aoff += (bytes + 15) & ~(size_t)15;
+      return launch_xfer(st, dst, dview(ctx->h_fb, h), bytes);
+    };
+    std::vector<std::pair<void*, std::pair<const char*, size_t>>> gets;
+    auto get = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      char* h = (char*)ctx->h_fb.p + aoff;
+      aoff += (bytes + 15) & ~(size_t)15;
+      gets.push_back({dst, {h, bytes}});
+      return launch_xfer(st, dview(ctx->h_fb, h), src, bytes);
+    };
+    // after a synchronisation: the gets land in their host vectors
+    auto land = [&]() {
+      for (auto& g : gets) memcpy(g.first, g.second.first, g.second.second);
+      gets.clear();
+    };
 
     std::vector<uint32_t> rb(nf + 1, 0);
     for (uint32_t i = 0; i < nf; ++i) rb[i + 1] = rb[i] + tiles_of(work[i].n, kRangeTile);
@@ -450,19 +486,20 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
       lohi[2 * i] = ~0ull;
       lohi[2 * i + 1] = 0;
     }
-    CK(cudaMemcpyAsync(d_items, work.data(), nf * sizeof(FbItem), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_rb, rb.data(), (nf + 1) * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_lohi, lohi.data(), nf * 16, cudaMemcpyHostToDevice, st));
+    CK(put(d_items, work.data(), nf * sizeof(FbItem)));
+    CK(put(d_rb, rb.data(), (nf + 1) * 4));
+    CK(put(d_lohi, lohi.data(), nf * 16));
     CK(launch_fb_range(lc, d_items, nf, d_rb, rb[nf], C, d_lohi));
     std::vector<uint64_t> pivot(nf, 0);
     std::vector<uint32_t> dom(nf, 0);
     if (try_split) CK(launch_fb_mode(lc, d_items, nf, C, d_lohi, d_pivot, d_dom));
-    CK(cudaMemcpyAsync(lohi.data(), d_lohi, nf * 16, cudaMemcpyDeviceToHost, st));
+    CK(get(lohi.data(), d_lohi, nf * 16));
     if (try_split) {
-      CK(cudaMemcpyAsync(pivot.data(), d_pivot, nf * 8, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(dom.data(), d_dom, nf * 4, cudaMemcpyDeviceToHost, st));
+      CK(get(pivot.data(), d_pivot, nf * 8));
+      CK(get(dom.data(), d_dom, nf * 4));
     }
     CK(cudaStreamSynchronize(st));
+    land();
 
     std::vector<FbItem> sw_items, sp_items;
     std::vector<uint64_t> lohi_s, piv_p;
@@ -490,10 +527,9 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
       uint32_t passes = 2;
       for (uint64_t run = kMergeTile; run < max_n_s; run *= 2) ++passes;
       ctx->stats.bytes_moved += keys_s * 2 * kv * passes;
-      CK(cudaMemcpyAsync(d_items_s, sw_items.data(), ns * sizeof(FbItem), cudaMemcpyHostToDevice,
-                         st));
-      CK(cudaMemcpyAsync(d_mb_s, mb_s.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(d_lohi_s, lohi_s.data(), ns * 16, cudaMemcpyHostToDevice, st));
+      CK(put(d_items_s, sw_items.data(), ns * sizeof(FbItem)));
+      CK(put(d_mb_s, mb_s.data(), (ns + 1) * 4));
+      CK(put(d_lohi_s, lohi_s.data(), ns * 16));
       CK(launch_fb_sort(lc, d_items_s, ns, d_mb_s, mb_s[ns], max_n_s, d_lohi_s, C, D, Cv, Dv,
                         out_k, out_v));
     }
@@ -504,10 +540,9 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
       ctx->stats.fallback_splits += np;
       CK(ensure(ctx->fb_cnt, (size_t)3 * (mp + 1) * 4));
       CK(ensure(ctx->sw, ((size_t)tiles_of(3 * (uint64_t)(mp + 1), kScanTile) + 8) * 8));
-      CK(cudaMemcpyAsync(d_items_p, sp_items.data(), np * sizeof(FbItem), cudaMemcpyHostToDevice,
-                         st));
-      CK(cudaMemcpyAsync(d_mb_p, mb_p.data(), (np + 1) * 4, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(d_piv_p, piv_p.data(), np * 8, cudaMemcpyHostToDevice, st));
+      CK(put(d_items_p, sp_items.data(), np * sizeof(FbItem)));
+      CK(put(d_mb_p, mb_p.data(), (np + 1) * 4));
+      CK(put(d_piv_p, piv_p.data(), np * 8));
       CK(cudaMemsetAsync(d_item_cnt, 0, (size_t)np * 24, st));
       uint32_t* cnt = as<uint32_t>(ctx->fb_cnt);
       CK(launch_fb_part_count(lc, d_items_p, np, d_mb_p, mp, C, d_piv_p, cnt, d_item_cnt));
@@ -516,9 +551,10 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
       CK(launch_fb_part_scatter(lc, d_items_p, np, d_mb_p, mp, C, Cv, d_piv_p, cnt, D, Dv));
       std::vector<uint64_t> part(3 * (size_t)np);
       uint32_t stw = 0;
-      CK(cudaMemcpyAsync(part.data(), d_item_cnt, (size_t)np * 24, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(&stw, lc.status, 4, cudaMemcpyDeviceToHost, st));
+      CK(get(part.data(), d_item_cnt, (size_t)np * 24));
+      CK(get(&stw, lc.status, 4));
       CK(cudaStreamSynchronize(st));
+      land();
       if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
       // the parts: below and above go round again (unless they are too short
       // to need sorting), the equal part is final; every final part is in D
@@ -545,9 +581,8 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
         uint64_t done_keys = 0;
         for (const FbItem& it : done) done_keys += it.n;
         ctx->stats.bytes_moved += done_keys * 2 * kv;
-        CK(cudaMemcpyAsync(d_items_d, done.data(), nd * sizeof(FbItem), cudaMemcpyHostToDevice,
-                           st));
-        CK(cudaMemcpyAsync(d_mb_d, mb_d.data(), (nd + 1) * 4, cudaMemcpyHostToDevice, st));
+        CK(put(d_items_d, done.data(), nd * sizeof(FbItem)));
+        CK(put(d_mb_d, mb_d.data(), (nd + 1) * 4));
         CK(launch_fb_move(lc, d_items_d, nd, d_mb_d, mb_d[nd], D, out_k, Dv, out_v));
       }
     }
@@ -617,8 +652,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       CK(ensure(ctx->small_segs, need));
       memcpy(ctx->h_stage_small.p, pl.segs.data(), S * sizeof(Seg));
       memcpy((char*)ctx->h_stage_small.p + S * sizeof(Seg), pl.range_base.data(), (S + 1) * 4);
-      CK(cudaMemcpyAsync(ctx->small_segs.p, ctx->h_stage_small.p, need, cudaMemcpyHostToDevice,
-                         st));
+      CK(launch_xfer(st, ctx->small_segs.p, ctx->h_stage_small.dp, need));
       CK(launch_range(lc, as<Seg>(ctx->small_segs), S,
                       (const uint32_t*)((char*)ctx->small_segs.p + S * sizeof(Seg)),
                       pl.range_base[S], in_k, true));
@@ -643,8 +677,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     CK(ensure(ctx->small_items, need));
     CK(ensure_host(ctx->h_items, need));
     memcpy(ctx->h_items.p, recs.data(), S * sizeof(BRec));
-    CK(cudaMemcpyAsync(ctx->small_items.p, ctx->h_items.p, S * sizeof(BRec),
-                       cudaMemcpyHostToDevice, st));
+    CK(launch_xfer(st, ctx->small_items.p, ctx->h_items.dp, S * sizeof(BRec)));
     CK(ensure(ctx->olist, (size_t)S * olist_per_bucket));
     CK(launch_onchip(lc, as<BRec>(ctx->small_items), S, cap, in_k, in_v, out_k, out_v,
                      ctx->policy, ptab, as<uint32_t>(ctx->olist),
@@ -654,7 +687,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   };
   if (big.empty()) {
     if (kt == KEY_F64) {
-      CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+      CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
       CK(cudaStreamSynchronize(st));
       if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
     }
@@ -696,7 +729,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     memcpy(hs + PL.o_t1, pl.tile1_base.data(), (S + 1) * 4);
     memcpy(hs + PL.o_gb, pl.group_base.data(), (S + 1) * 8);
     memcpy(hs + PL.o_bb, pl.bucket_base.data(), (S + 1) * 8);
-    CK(cudaMemcpyAsync(pbuf[cur]->p, hs, PL.bytes, cudaMemcpyHostToDevice, st));
+    CK(launch_xfer(st, pbuf[cur]->p, ctx->h_stage.dp, PL.bytes));
     L.S = S;
     for (auto& sg : big) L.n_level += sg.n;
     L.wb = big.front().off;
@@ -731,7 +764,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     // range, model
     CK(launch_range(lc, d_segs, S, L.dp.rb, L.n_range, src, first && kt == KEY_F64));
     if (first && kt == KEY_F64) {
-      CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+      CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
       CK(cudaStreamSynchronize(st));
       if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
     }
@@ -849,8 +882,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                         ctx->policy, dbits, tile_keys, ndp, as<uint32_t>(ctx->pcols),
                         as<uint32_t>(ctx->pbsums), d_lo, as<uint64_t>(ctx->sw), tile_counter,
                         spin_limit, &totals[2]));
-    CK(cudaMemcpyAsync(ctx->h_lout.p, d_lo, sizeof(LevelOut), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+    CK(launch_xfer(st, ctx->h_lout.dp, d_lo, sizeof(LevelOut)));
+    CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
     CK(cudaStreamSynchronize(st));
     const LevelOut lo = *(LevelOut*)ctx->h_lout.p;
     const uint32_t stw = *(uint32_t*)ctx->h_status.p;
@@ -861,9 +894,10 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     // standard sort of the large failure-guard / degenerate buckets
     if (lo.n_fb) {
       std::vector<FbItem> items(lo.n_fb);
-      CK(cudaMemcpyAsync(items.data(), ctx->fb.p, lo.n_fb * sizeof(FbItem),
-                         cudaMemcpyDeviceToHost, st));
+      CK(ensure_host(ctx->h_fb, (size_t)lo.n_fb * sizeof(FbItem)));
+      CK(launch_xfer(st, ctx->h_fb.dp, ctx->fb.p, lo.n_fb * sizeof(FbItem)));
       CK(cudaStreamSynchronize(st));
+      memcpy(items.data(), ctx->h_fb.p, lo.n_fb * sizeof(FbItem));
       for (const FbItem& it : items) level_fb_keys += it.n;
       ctx->stats.fallback_keys += level_fb_keys;
       ctx->stats.fallback_buckets += lo.n_fb;
@@ -906,7 +940,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     src_v = Xv;
     first = false;
   }
-  CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+  CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
   CK(cudaStreamSynchronize(st));
   const uint32_t stw = *(uint32_t*)ctx->h_status.p;
   if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
@@ -1199,7 +1233,7 @@ pcf_status pcf_debug_scan(pcf_ctx* ctx, uint32_t* d_data, uint64_t n, uint32_t w
   CK(cudaMemsetAsync(lc.status, 0, 4, st));
   CK(launch_scan(lc, d_data, n, nullptr, as<uint64_t>(ctx->sw), as<uint32_t>(ctx->misc),
                  withhold_tile, spin_limit ? spin_limit : kSpinLimit, nullptr));
-  CK(cudaMemcpyAsync(ctx->h_status.p, lc.status, 4, cudaMemcpyDeviceToHost, st));
+  CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
   CK(cudaStreamSynchronize(st));
   const uint32_t w = *(uint32_t*)ctx->h_status.p;
   if (w & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;

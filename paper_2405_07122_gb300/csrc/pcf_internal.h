@@ -167,6 +167,12 @@ cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tp
 cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
                          uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
                          const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout);
+// Small host <-> device transfers of a sort, copied by the SMs through the
+// device view of pinned host memory.  A copy-engine transfer would queue
+// behind any large copy in the same direction already issued on another
+// stream (a caller's bulk upload or download), stalling the sort for its
+// whole duration.
+cudaError_t launch_xfer(cudaStream_t st, void* dst, const void* src, size_t bytes);
 cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const uint64_t* n_dev,
                         uint64_t* status_words, uint32_t* tile_counter, uint32_t withhold,
                         uint64_t spin_limit, uint64_t* total_out, bool inclusive = false);

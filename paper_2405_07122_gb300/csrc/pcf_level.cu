@@ -1057,6 +1057,32 @@ cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const 
   return cudaGetLastError();
 }
 
+// Byte copy by the SMs (one side pinned host memory, seen through its
+// device pointer): 16-byte words when both ends allow it.
+__global__ void k_xfer(uint8_t* __restrict__ dst, const uint8_t* __restrict__ src, size_t n,
+                       int wide) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nt = (size_t)gridDim.x * blockDim.x;
+  if (wide) {
+    const size_t nw = n / 16;
+    for (size_t i = t; i < nw; i += nt)
+      reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+    for (size_t i = nw * 16 + t; i < n; i += nt) dst[i] = src[i];
+  } else {
+    for (size_t i = t; i < n; i += nt) dst[i] = src[i];
+  }
+}
+
+cudaError_t launch_xfer(cudaStream_t st, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return cudaSuccess;
+  const int wide = (((uintptr_t)dst | (uintptr_t)src) & 15) == 0;
+  const size_t units = wide ? bytes / 16 + 1 : bytes;
+  const size_t blocks = (units + 255) / 256;
+  const uint32_t grid = (uint32_t)(blocks < 256 ? blocks : 256);
+  k_xfer<<<grid, 256, 0, st>>>((uint8_t*)dst, (const uint8_t*)src, bytes, wide);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const uint64_t* n_dev,
                         uint64_t* status_words, uint32_t* tile_counter, uint32_t withhold,
                         uint64_t spin_limit, uint64_t* total_out, bool inclusive) {
