@@ -71,7 +71,8 @@ typedef struct {
 
 /* Implementation knobs.  They change speed only, never the result or the
  * model: max_digit_bits = widest bucket-id digit scattered per global pass
- * (4..12); tile_log2 = log2 of keys per count tile of a global pass (12..18);
+ * (4..12); tile_log2 = log2 of keys per count tile of pass 1 (12..18; pass 2
+ * uses tiles 4x larger);
  * leaf_cap = the largest bucket finished on chip (64..8192, power of two; key-
  * value sorts use at most 1024, and a smaller one where the policy's tables
  * would not fit shared memory).

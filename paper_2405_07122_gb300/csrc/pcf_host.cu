@@ -827,12 +827,16 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     ctx->stats.global_passes += 1;
     ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 + 4 /*hist1*/ + 12 + 10 /*scatter1*/) +
                               (pairs ? n_level * 8 : 0);
-    // pass 2
+    // pass 2: count tiles 4x larger than pass 1's.  Its digit is the wider
+    // one, and larger tiles keep its count matrix (written and read with a
+    // stride of one row per digit) small; the plan's bounds, taken with
+    // pass 1's tile size, still hold (there are fewer tiles)
     if (L.two_pass) {
+      const uint32_t tile_keys2 = tile_keys << 2;
       CK(ensure(ctx->groups, L.n_groups * sizeof(Group)));
       CK(ensure(ctx->gtiles, L.n_groups * 4));
       CK(ensure(ctx->gcent, L.n_groups * 4));
-      CK(launch_groups(lc, d_segs, S, L.dp.gb, L.n_groups, as<uint32_t>(ctx->cmat1), tile_keys,
+      CK(launch_groups(lc, d_segs, S, L.dp.gb, L.n_groups, as<uint32_t>(ctx->cmat1), tile_keys2,
                        as<Group>(ctx->groups), as<uint32_t>(ctx->gtiles),
                        as<uint32_t>(ctx->gcent)));
       CK(launch_scan(lc, as<uint32_t>(ctx->gtiles), L.n_groups, nullptr, as<uint64_t>(ctx->sw),
@@ -843,14 +847,14 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       CK(ensure(ctx->cmat2, L.cmat2_bound * 4));
       CK(cudaMemsetAsync(ctx->cmat2.p, 0, L.cmat2_bound * 4, st));
       CK(launch_hist2(lc, as<Group>(ctx->groups), (uint32_t)L.n_groups, d_segs,
-                      as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)L.tiles2_bound, tile_keys,
+                      as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)L.tiles2_bound, tile_keys2,
                       kb.tmp_aux, as<uint32_t>(ctx->cmat2), L.dmax2));
       CK(launch_scan(lc, as<uint32_t>(ctx->cmat2), L.cmat2_bound, &totals[1],
                      as<uint64_t>(ctx->sw), tile_counter, 0xFFFFFFFFu, spin_limit, nullptr));
       tm.mark(4);
       CK(launch_scatter2(lc, as<Group>(ctx->groups), (uint32_t)L.n_groups, d_segs,
                          as<uint32_t>(ctx->gtiles), &totals[0], (uint32_t)L.tiles2_bound,
-                         tile_keys, kb, as<uint32_t>(ctx->cmat2), L.dmax2));
+                         tile_keys2, kb, as<uint32_t>(ctx->cmat2), L.dmax2));
       // segments whose bucket id has one digit were already bucketed by pass 1
       CK(launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, P1, P2, P1v, P2v, kCopyOneDigit));
       tm.mark(5);
