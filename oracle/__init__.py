@@ -71,6 +71,10 @@ def lib():
         L.orc_level0.argtypes = [_u64p, _u32p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
                                  ctypes.POINTER(Policy), _u64p, _u64p, _u64p, _u64p, _u64p,
                                  ctypes.POINTER(ctypes.c_int)]
+        L.orc_bucket_sizes.restype = ctypes.c_int
+        L.orc_bucket_sizes.argtypes = [_u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _u64p,
+                                       ctypes.POINTER(ctypes.c_int)]
         L.brute_insertion_sort.restype = None
         L.brute_insertion_sort.argtypes = [_u64p, _u32p, ctypes.c_uint64, ctypes.c_int]
         L.brute_cumulative_counts.restype = None
@@ -179,6 +183,20 @@ def level0(keys: np.ndarray, vals: np.ndarray = None, seed: int = 0, policy: Pol
     return dict(alpha=int(p6[0]), beta=int(p6[1]), gamma=int(p6[2]), delta=int(p6[3]),
                 lo_bits=int(p6[4]), hi_bits=int(p6[5]), status=status.value,
                 sample_idx=sidx, b=b, T=T, counts=counts, keys=k.view(keys.dtype), vals=v)
+
+
+def bucket_sizes(keys: np.ndarray, seed: int, alpha: int, beta: int, gamma: int):
+    """One model-based bucketing (Alg. 1 + Sec. 3.3) with alpha, beta, gamma
+    given, as in the experiment of Sec. 4.2: (bucket sizes |c_0|..|c_gamma|,
+    status) with status 0 bucketed, 1 single value, 2 degenerate range."""
+    k = _bits(keys).copy()
+    counts = np.zeros(gamma + 1, dtype=np.uint64)
+    status = ctypes.c_int(0)
+    rc = lib().orc_bucket_sizes(_p64(k), k.size, _kt(keys), seed, alpha, beta, gamma,
+                                _p64(counts), ctypes.byref(status))
+    if rc:
+        raise RuntimeError("orc_bucket_sizes failed: %d" % rc)
+    return counts, status.value
 
 
 def insertion_sort(keys: np.ndarray, vals: np.ndarray = None):

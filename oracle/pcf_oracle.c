@@ -316,10 +316,22 @@ static void policy_params(const orc_policy* P, uint64_t n, orc_level* L) {
   if (L->beta < 1) L->beta = 1;
 }
 
-/* Buckets keys[0..n) in place (stable), filling L.  aux/auxv: scratch of n. */
+/* Buckets keys[0..n) in place (stable), filling L.  aux/auxv: scratch of n.
+ * fixed3: alpha, beta, gamma given (the bucketing-failure experiment of
+ * Sec. 4.2), else the policy's (delta is then 0: unused by one step). */
+static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint64_t* keys,
+                          uint32_t* vals, uint64_t n, int kt, uint64_t seed, uint64_t depth,
+                          uint64_t start, orc_level* L, uint64_t* aux, uint32_t* auxv);
+
 static int bucketize(const orc_policy* P, uint64_t* keys, uint32_t* vals, uint64_t n, int kt,
                      uint64_t seed, uint64_t depth, uint64_t start, orc_level* L,
                      uint64_t* aux, uint32_t* auxv) {
+  return bucketize_with(P, NULL, keys, vals, n, kt, seed, depth, start, L, aux, auxv);
+}
+
+static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint64_t* keys,
+                          uint32_t* vals, uint64_t n, int kt, uint64_t seed, uint64_t depth,
+                          uint64_t start, orc_level* L, uint64_t* aux, uint32_t* auxv) {
   memset(L, 0, sizeof *L);
   /* x_min, x_max over the whole (sub)array, Sec. 3.3 */
   uint64_t lo = keys[0], hi = keys[0];
@@ -329,7 +341,14 @@ static int bucketize(const orc_policy* P, uint64_t* keys, uint32_t* vals, uint64
   }
   L->lo_bits = lo;
   L->hi_bits = hi;
-  policy_params(P, n, L);
+  if (fixed3) {
+    L->alpha = fixed3[0];
+    L->beta = fixed3[1];
+    L->gamma = fixed3[2];
+    L->delta = 0;
+  } else {
+    policy_params(P, n, L);
+  }
   if (lo == hi) {
     L->status = 1;
     return ORC_OK;
@@ -504,6 +523,37 @@ int orc_level0(uint64_t* keys, uint32_t* vals, uint64_t n, int kt, uint64_t seed
     memcpy(T, L.T, (L.beta + 1) * sizeof(uint64_t));
     memcpy(counts, L.counts, (L.gamma + 1) * sizeof(uint64_t));
   }
+  level_free(&L);
+  return ORC_OK;
+}
+
+/* One model-based bucketing of keys[0..n) with alpha, beta, gamma given
+ * (Sec. 4.2: alpha = floor(n^a) ... varied over a grid): the bucket sizes
+ * counts[0..gamma] and *status (0 bucketed, 1 single value, 2 degenerate).
+ * Keys are not modified. */
+int orc_bucket_sizes(const uint64_t* keys, uint64_t n, int kt, uint64_t seed, uint64_t alpha,
+                     uint64_t beta, uint64_t gamma, uint64_t* counts, int* status) {
+  if (n < 2 || alpha < 1 || beta < 1 || gamma < 1 || has_nan(keys, n, kt)) return ORC_ERR_ARG;
+  uint64_t* k = (uint64_t*)malloc(n * sizeof(uint64_t));
+  uint64_t* aux = (uint64_t*)malloc(n * sizeof(uint64_t));
+  if (!k || !aux) {
+    free(k);
+    free(aux);
+    return ORC_ERR_OOM;
+  }
+  memcpy(k, keys, n * sizeof(uint64_t));
+  const uint64_t fixed3[3] = {alpha, beta, gamma};
+  orc_level L;
+  int rc = bucketize_with(NULL, fixed3, k, NULL, n, kt, seed, 0, 0, &L, aux, NULL);
+  free(k);
+  free(aux);
+  if (rc) {
+    level_free(&L);
+    return rc;
+  }
+  *status = L.status;
+  if (L.status == 0) memcpy(counts, L.counts, (gamma + 1) * sizeof(uint64_t));
+  else memset(counts, 0, (gamma + 1) * sizeof(uint64_t));
   level_free(&L);
   return ORC_OK;
 }
