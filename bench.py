@@ -204,7 +204,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N, help="keys per array (default 10^8)")
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "small", "zipf", "batched", "serve", "dupinject"],
+                    choices=["plain", "small", "zipf", "batched", "serve", "dupinject",
+                             "failsweep"],
                     help="plain: the default 4 x 10^8 f64 line; the others are the "
                          "secondary configurations")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
@@ -429,6 +430,39 @@ def run_secondary(args):
                     config={"workload": "duplicate injection (appendix): 5x10^7 Normal(0,1) "
                                         "float64 keys + 5x10^7 copies of one value in [min, max], "
                                         "shuffled, keys only", "n": n})
+    elif args.workload == "failsweep":
+        # Sec. 4.2: level-0 bucketing of R = 100 uniform arrays of 10^6 keys
+        # at every grid setting of the six heat maps (two of a, b, c, d
+        # varied over 0.05..0.95, the others 0.75), failure = a bucket of
+        # more than delta keys
+        from paper_2405_07122_gb300 import failsweep as F
+        n, R = 10**6, 100
+        x = np.concatenate([W.f64_keys("uniform", n, 1000 + r) for r in range(R)])
+        keys = torch.from_numpy(x).cuda()
+        offs = np.arange(R + 1, dtype=np.uint64) * n
+        F.heat_map(ctx, keys, offs, n, ("a", "b"), grid=[0.75])  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        maps = {ax: F.heat_map(ctx, keys, offs, n, ax) for ax in F.MAPS}
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        settings = len(F.MAPS) * len(F.GRID) ** 2
+        summary = {}
+        for ax, pts in maps.items():
+            inside, viol = F.agreement(pts)
+            # one row per value of the second axis (0.95 first), one digit per
+            # value of the first: failure frequency x 10 (X = every array)
+            rows = ["".join("X" if pts[(xv, yv)][0] >= 1.0 else str(int(pts[(xv, yv)][0] * 10))
+                            for xv in F.GRID) for yv in reversed(F.GRID)]
+            summary["".join(ax)] = {"bound_le_half": inside, "of_those_failing_often": viol,
+                                    "freq_x10_rows_y_desc": rows}
+        line.update(metric="bucketed Gkeys/s (failure sweep)",
+                    value=settings * R * n / secs / 1e9, ms_per_setting=secs * 1e3 / settings,
+                    dtype="f64", maps=summary,
+                    config={"workload": "Sec. 4.2 bucketing-failure sweep: 6 heat maps x 19 x 19 "
+                                        "settings, each bucketing 100 Uniform[0,1) arrays of "
+                                        "10^6 float64 keys (level 0 of Algorithm 1)",
+                            "settings": settings, "arrays_per_setting": R})
     elif args.workload == "batched":
         keys, offs, _ = W.batched_f64(2048, seed=6)
         total = int(offs[-1])

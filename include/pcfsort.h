@@ -181,6 +181,26 @@ pcf_status pcf_sort_keys_host_batch(pcf_ctx* ctx, void* const* h_keys, const uin
                                     uint32_t count, pcf_key_type kt, uint64_t seed,
                                     void* stream);
 
+/* Level-0 model-based bucketing only (Alg. 1's bucketing step with the PCF
+ * model of Sec. 3.3), with alpha, beta, gamma given instead of the policy's:
+ * the experiment of Sec. 4.2 that checks Lemma pcf-divide-success-prob
+ * (bucketing fails when some bucket holds more than delta keys).  Array s is
+ * keys [h_offsets[s], h_offsets[s+1]) of d_keys (S+1 non-decreasing HOST
+ * offsets, h_offsets[0] = 0, every array at least 2 keys), sampled exactly
+ * as pcf_sort_segmented samples its level 0 (seed + s).
+ *   h_max[s]  (HOST, S entries): max_j |c_j| over its gamma + 1 buckets; n_s
+ *             when the array is not bucketed (one value, or a degenerate
+ *             range: Alg. 1 sends it to Standard-Sort whole).
+ *   d_counts  (DEVICE, optional, S x (gamma + 1) u32, array-major): the bucket
+ *             sizes |c_0| .. |c_gamma| of each bucketed array (zeros for the
+ *             others); NULL uses context scratch.
+ * Limits: 1 <= alpha < 2^32, 1 <= beta < 2^32 - 1, 1 <= gamma < 2^24.  Keys
+ * are only read.  PCF_ERR_INVALID_KEY on a NaN key. */
+pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_offsets,
+                            uint32_t S, pcf_key_type kt, uint64_t seed, uint64_t alpha,
+                            uint64_t beta, uint64_t gamma, uint32_t* d_counts, uint64_t* h_max,
+                            void* stream);
+
 /* Stage timing of the last sort (milliseconds between CUDA events recorded
  * on the sort's stream) when enabled with pcf_ctx_enable_timing(ctx, 1):
  * [0] range (k_range + k_model), [1] sample + PCF table (k_sample),

@@ -116,6 +116,7 @@ struct pcf_ctx {
   DevBuf jbuf;                   // bucket id of every key of a level
   DevBuf small_segs;             // range records of the on-chip arrays (level 0)
   DevBuf fb_cnt;                 // per-tile part counts of the three-way splits
+  DevBuf bcounts, bmax;          // bucket sizes of the bucketing-only entry point
   HostBuf h_stage, h_lout, h_status, h_items;
   HostBuf h_stage_small;  // range records of the on-chip arrays (level 0)
   HostBuf h_fb;           // fallback items and their tables, both ways
@@ -249,8 +250,10 @@ struct Plan {
 // Plans one global level.  When every segment's bucket id fits one digit
 // (<= max_digit_bits) the level scatters once; otherwise twice, and
 // segments with a one-digit id copy themselves in the second pass.
+// fixed: alpha..delta of every segment instead of the policy's (the
+// bucketing-only entry point)
 void plan_level(const Policy& P, const pcf_tuning& tu, ParamCache& pc,
-                const std::vector<InSeg>& in, Plan& pl) {
+                const std::vector<InSeg>& in, Plan& pl, const Params* fixed = nullptr) {
   const uint32_t tile_keys = 1u << tu.tile_log2;
   const uint32_t S = (uint32_t)in.size();
   const uint32_t dbits = std::min(tu.max_digit_bits, kMaxDigitBits);
@@ -266,7 +269,7 @@ void plan_level(const Policy& P, const pcf_tuning& tu, ParamCache& pc,
   std::vector<Params> prs(S);
   for (uint32_t s = 0; s < S; ++s) {
     Params tmp;
-    prs[s] = pc.get(P, in[s].n, tmp);
+    prs[s] = fixed ? *fixed : pc.get(P, in[s].n, tmp);
     if (std::max(1u, bits_of(prs[s].gamma)) > dbits) pl.two_pass = true;
   }
   for (uint32_t s = 0; s < S; ++s) {
@@ -1192,6 +1195,106 @@ pcf_status pcf_sort_keys_host_batch(pcf_ctx* ctx, void* const* h_keys, const uin
   if (status != PCF_OK) return status;
   if (!e) e = e_in ? e_in : e_out;
   CK(e);
+  return PCF_OK;
+}
+
+// Level-0 model-based bucketing only, with alpha, beta, gamma given: the
+// bucket sizes of each array and the largest of them (the experiment of
+// Sec. 4.2 behind Lemma pcf-divide-success-prob).  The same kernels as a
+// sort's level 0 (range, model, sample + table, k_hist1), then a count.
+pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_offsets,
+                            uint32_t S, pcf_key_type kt, uint64_t seed, uint64_t alpha,
+                            uint64_t beta, uint64_t gamma, uint32_t* d_counts, uint64_t* h_max,
+                            void* stream) {
+  if (!ctx || !d_keys || !h_offsets || !h_max || S == 0) return PCF_ERR_INVALID_ARG;
+  if (kt != PCF_KEY_F64 && kt != PCF_KEY_U64) return PCF_ERR_INVALID_ARG;
+  if (alpha < 1 || beta < 1 || gamma < 1 || alpha > 0xFFFFFFFFull || beta >= 0xFFFFFFFFull ||
+      gamma >= (1ull << (2 * kMaxDigitBits)))
+    return PCF_ERR_INVALID_ARG;
+  if (((uintptr_t)d_keys & 7) || h_offsets[0] != 0) return PCF_ERR_INVALID_ARG;
+  std::vector<InSeg> segs(S);
+  for (uint32_t s = 0; s < S; ++s) {
+    const uint64_t a = h_offsets[s], b = h_offsets[s + 1];
+    if (b < a + 2 || b - a > 0xFFFFFFFFull) return PCF_ERR_INVALID_ARG;
+    segs[s] = InSeg{a, b - a, 0, seed + s, 0};
+  }
+  const uint64_t n_total = h_offsets[S];
+  if (n_total > 0xFFFFFFFFull) return PCF_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  LaunchCfg lc;
+  lc.stream = st;
+  lc.kt = (uint32_t)kt;
+  lc.pairs = false;
+  lc.launches = &ctx->stats.kernel_launches;
+  ctx->stats = pcf_call_stats{};
+  CK(ensure(ctx->status, 64));
+  lc.status = as<uint32_t>(ctx->status);
+  CK(cudaMemsetAsync(lc.status, 0, 4, st));
+  CK(ensure_host(ctx->h_status, 64));
+  CK(ensure(ctx->misc, 256));
+  Params fixed;
+  fixed.alpha = (uint32_t)alpha;
+  fixed.beta = (uint32_t)beta;
+  fixed.gamma = (uint32_t)gamma;
+  fixed.delta = 0;
+  Plan pl;
+  plan_level(ctx->policy, ctx->tuning, ctx->pcache, segs, pl, &fixed);
+  const PlanLayout PL = plan_layout(S);
+  CK(ensure_host(ctx->h_stage, PL.bytes));
+  CK(ensure(ctx->segs, PL.bytes));
+  char* hs = (char*)ctx->h_stage.p;
+  memcpy(hs, pl.segs.data(), S * sizeof(Seg));
+  memcpy(hs + PL.o_rb, pl.range_base.data(), (S + 1) * 4);
+  memcpy(hs + PL.o_k1, pl.k1_base.data(), (S + 1) * 4);
+  memcpy(hs + PL.o_t1, pl.tile1_base.data(), (S + 1) * 4);
+  memcpy(hs + PL.o_gb, pl.group_base.data(), (S + 1) * 8);
+  memcpy(hs + PL.o_bb, pl.bucket_base.data(), (S + 1) * 8);
+  CK(launch_xfer(st, ctx->segs.p, ctx->h_stage.dp, PL.bytes));
+  const DevPlan dp = dev_plan(ctx->segs.p, PL);
+  const uint32_t tile_keys = 1u << ctx->tuning.tile_log2;
+  const uint64_t spin_limit = kSpinLimit;
+  CK(launch_range(lc, dp.segs, S, dp.rb, pl.range_base[S], (const uint64_t*)d_keys,
+                  kt == PCF_KEY_F64));
+  if (kt == PCF_KEY_F64) {
+    CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
+    CK(cudaStreamSynchronize(st));
+    if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+  }
+  CK(launch_model(lc, dp.segs, S));
+  CK(ensure(ctx->tpool, pl.tpool * 4));
+  CK(cudaMemsetAsync(ctx->tpool.p, 0, pl.tpool * 4, st));
+  const uint64_t scan_max = std::max(pl.cmat1, pl.tpool);
+  CK(ensure(ctx->sw, ((scan_max + kScanTile - 1) / kScanTile + 8) * 8));
+  uint32_t* tile_counter = as<uint32_t>(ctx->misc);
+  CK(launch_sample(lc, dp.segs, S, dp.k1, pl.k1_base[S], (const uint64_t*)d_keys,
+                   as<uint32_t>(ctx->tpool)));
+  CK(launch_table(lc, dp.segs, S, as<uint32_t>(ctx->tpool), pl.tpool, as<uint64_t>(ctx->sw),
+                  tile_counter, spin_limit));
+  CK(ensure(ctx->cmat1, pl.cmat1 * 4));
+  CK(cudaMemsetAsync(ctx->cmat1.p, 0, pl.cmat1 * 4, st));
+  CK(ensure(ctx->jbuf, n_total * 4));
+  CK(launch_hist1(lc, dp.segs, S, dp.t1, pl.tile1_base[S], tile_keys, (const uint64_t*)d_keys,
+                  as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1,
+                  as<uint32_t>(ctx->jbuf)));
+  const size_t n_counts = (size_t)S * (gamma + 1);
+  uint32_t* counts = d_counts;
+  if (!counts) {
+    CK(ensure(ctx->bcounts, n_counts * 4));
+    counts = as<uint32_t>(ctx->bcounts);
+  }
+  CK(cudaMemsetAsync(counts, 0, n_counts * 4, st));
+  CK(ensure(ctx->bmax, (size_t)S * 8));
+  CK(launch_bucket_sizes(lc, dp.segs, S, dp.t1, pl.tile1_base[S], tile_keys,
+                         as<uint32_t>(ctx->jbuf), counts, as<uint64_t>(ctx->bmax)));
+  CK(ensure_host(ctx->h_items, (size_t)S * 8));
+  CK(launch_xfer(st, ctx->h_items.dp, ctx->bmax.p, (size_t)S * 8));
+  CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t w = *(uint32_t*)ctx->h_status.p;
+  if (w & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+  if (w & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
+  memcpy(h_max, ctx->h_items.p, (size_t)S * 8);
   return PCF_OK;
 }
 

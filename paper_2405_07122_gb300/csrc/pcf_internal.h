@@ -167,6 +167,12 @@ cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tp
 cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
                          uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
                          const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout);
+// Level-0 bucket sizes of every segment (ids from k_hist1's jbuf): counts
+// (zeroed by the caller) at bucket_base, and out_max[s] = max_j |c_j| (n
+// for a segment that was not bucketed).
+cudaError_t launch_bucket_sizes(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                                const uint32_t* tile_base, uint32_t n_tiles, uint32_t tile_keys,
+                                const uint32_t* jbuf, uint32_t* counts, uint64_t* out_max);
 // Small host <-> device transfers of a sort, copied by the SMs through the
 // device view of pinned host memory.  A copy-engine transfer would queue
 // behind any large copy in the same direction already issued on another

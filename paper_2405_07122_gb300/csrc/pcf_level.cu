@@ -1057,6 +1057,75 @@ cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Level-0 bucket sizes only (the bucketing-failure experiment of Sec. 4.2):
+// every key's bucket id j (stored by k_hist1) counted per segment, then the
+// largest count of each segment.  Few buckets: a shared-memory histogram per
+// tile first (the counters would otherwise be hot); many: global atomics.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSizeBinsSmem = 8192;
+
+__global__ void __launch_bounds__(256) k_bucket_sizes(const Seg* segs, uint32_t S,
+                                                      const uint32_t* tile_base,
+                                                      uint32_t tile_keys,
+                                                      const uint32_t* __restrict__ jbuf,
+                                                      uint32_t* counts) {
+  __shared__ uint32_t h[kSizeBinsSmem];
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
+  const Seg& g = segs[s];
+  if (g.status != SEG_BUCKET) return;  // uniform across the block
+  const uint32_t nb = g.gamma + 1;
+  uint32_t* c = counts + g.bucket_base;
+  const uint64_t base = g.off + (uint64_t)(t - tile_base[s]) * tile_keys;
+  const uint64_t end = min(g.off + g.n, base + tile_keys);
+  if (nb <= kSizeBinsSmem) {
+    for (uint32_t k = threadIdx.x; k < nb; k += 256) h[k] = 0;
+    __syncthreads();
+    for (uint64_t i = base + threadIdx.x; i < end; i += 256) atomicAdd(&h[jbuf[i]], 1u);
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < nb; k += 256)
+      if (h[k]) atomicAdd(&c[k], h[k]);
+  } else {
+    for (uint64_t i = base + threadIdx.x; i < end; i += 256) atomicAdd(&c[jbuf[i]], 1u);
+  }
+}
+
+// a block per segment: max_j |c_j|, or n when the segment was not bucketed
+__global__ void __launch_bounds__(256) k_bucket_max(const Seg* segs, const uint32_t* counts,
+                                                    uint64_t* out) {
+  __shared__ uint32_t wm[8];
+  const Seg& g = segs[blockIdx.x];
+  if (g.status != SEG_BUCKET) {
+    if (threadIdx.x == 0) out[blockIdx.x] = g.n;
+    return;
+  }
+  const uint32_t* c = counts + g.bucket_base;
+  uint32_t m = 0;
+  for (uint32_t k = threadIdx.x; k <= g.gamma; k += 256) m = max(m, c[k]);
+  for (int d = 16; d; d >>= 1) m = max(m, __shfl_xor_sync(~0u, m, d));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = max(m, wm[w]);
+    out[blockIdx.x] = m;
+  }
+}
+
+cudaError_t launch_bucket_sizes(const LaunchCfg& c, const Seg* segs, uint32_t S,
+                                const uint32_t* tile_base, uint32_t n_tiles, uint32_t tile_keys,
+                                const uint32_t* jbuf, uint32_t* counts, uint64_t* out_max) {
+  if (n_tiles) {
+    k_bucket_sizes<<<n_tiles, 256, 0, c.stream>>>(segs, S, tile_base, tile_keys, jbuf, counts);
+    count_launch(c);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+  }
+  k_bucket_max<<<S, 256, 0, c.stream>>>(segs, counts, out_max);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
 // Byte copy by the SMs (one side pinned host memory, seen through its
 // device pointer): 16-byte words when both ends allow it.
 __global__ void k_xfer(uint8_t* __restrict__ dst, const uint8_t* __restrict__ src, size_t n,

@@ -78,6 +78,8 @@ def lib():
                                    ctypes.c_int, _u64, _vp],
             "pcf_sort_keys_host": [_vp, _vp, _u64, ctypes.c_int, _u64, _vp],
             "pcf_sort_keys_host_batch": [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _vp],
+            "pcf_bucket_sizes": [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _u64, _u64, _u64, _vp,
+                                 _vp, _vp],
             "pcf_sort_segmented_static": [_vp, _vp, _vp, _u32, _u64, ctypes.c_int, _u64, _vp],
             "pcf_debug_scan": [_vp, _vp, _u64, _u32, _u64, _vp],
             "pcf_debug_level0": [_vp, _vp, _u64, ctypes.c_int, _u64, ctypes.POINTER(_u64),
@@ -243,6 +245,22 @@ class Context:
         self._check(lib().pcf_sort_keys_host_batch(self._h, P, N, len(ptrs), kt, seed,
                                                    _stream_ptr(stream)))
         return host_arrays
+
+    def bucket_sizes(self, keys, offsets, alpha, beta, gamma, key_type=None, seed=0,
+                     counts_out=None, stream=None):
+        """Level-0 bucketing only (alpha, beta, gamma given) of the arrays
+        keys[offsets[s]:offsets[s+1]] of a CUDA tensor: numpy u64 array of
+        max_j |c_j| per array; counts_out (CUDA int32/uint32 tensor of
+        S * (gamma + 1)) receives the bucket sizes when given."""
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+        S = offs.size - 1
+        kt = _kt(key_type or ("f64" if str(keys.dtype) == "torch.float64" else "u64"))
+        out = np.zeros(S, dtype=np.uint64)
+        self._check(lib().pcf_bucket_sizes(
+            self._h, keys.data_ptr(), offs.ctypes.data_as(ctypes.POINTER(_u64)), S, kt, seed,
+            alpha, beta, gamma, None if counts_out is None else counts_out.data_ptr(),
+            out.ctypes.data_as(ctypes.POINTER(_u64)), _stream_ptr(stream)))
+        return out
 
     # -- self-test hooks ----------------------------------------------------
     def debug_scan(self, data_u32, withhold_tile=0xFFFFFFFF, spin_limit=0, stream=None):
