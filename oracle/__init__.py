@@ -20,11 +20,16 @@ KEY_U64 = 1
 OK, ERR_ARG, ERR_NAN, ERR_OOM = 0, 1, 2, 3
 
 
+MODEL_PCF, MODEL_SPLINE = 0, 1
+
+
 class Policy(ctypes.Structure):
-    """alpha = floor(n^(a_num/den)), ... delta = floor(n^(d_num/den)); tau."""
+    """alpha = floor(n^(a_num/den)), ... delta = floor(n^(d_num/den)); tau;
+    model: the CDF model (MODEL_PCF, Sec. 3.3, or MODEL_SPLINE, App. A.5)."""
     _fields_ = [("a_num", ctypes.c_uint32), ("b_num", ctypes.c_uint32),
                 ("c_num", ctypes.c_uint32), ("d_num", ctypes.c_uint32),
-                ("den", ctypes.c_uint32), ("tau", ctypes.c_uint64)]
+                ("den", ctypes.c_uint32), ("tau", ctypes.c_uint64),
+                ("model", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -37,9 +42,9 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-def paper_policy(tau: int = 100) -> Policy:
+def paper_policy(tau: int = 100, model: int = MODEL_PCF) -> Policy:
     """alpha = beta = gamma = delta = floor(n^{3/4}), tau = 100 (Sec. 4 setup)."""
-    return Policy(3, 3, 3, 3, 4, tau)
+    return Policy(3, 3, 3, 3, 4, tau, model)
 
 
 _lib = None
@@ -73,8 +78,8 @@ def lib():
                                  ctypes.POINTER(ctypes.c_int)]
         L.orc_bucket_sizes.restype = ctypes.c_int
         L.orc_bucket_sizes.argtypes = [_u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
-                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _u64p,
-                                       ctypes.POINTER(ctypes.c_int)]
+                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_uint32, _u64p, ctypes.POINTER(ctypes.c_int)]
         L.brute_insertion_sort.restype = None
         L.brute_insertion_sort.argtypes = [_u64p, _u32p, ctypes.c_uint64, ctypes.c_int]
         L.brute_cumulative_counts.restype = None
@@ -185,14 +190,16 @@ def level0(keys: np.ndarray, vals: np.ndarray = None, seed: int = 0, policy: Pol
                 sample_idx=sidx, b=b, T=T, counts=counts, keys=k.view(keys.dtype), vals=v)
 
 
-def bucket_sizes(keys: np.ndarray, seed: int, alpha: int, beta: int, gamma: int):
-    """One model-based bucketing (Alg. 1 + Sec. 3.3) with alpha, beta, gamma
-    given, as in the experiment of Sec. 4.2: (bucket sizes |c_0|..|c_gamma|,
-    status) with status 0 bucketed, 1 single value, 2 degenerate range."""
+def bucket_sizes(keys: np.ndarray, seed: int, alpha: int, beta: int, gamma: int,
+                 model: int = MODEL_PCF):
+    """One model-based bucketing (Alg. 1 + Sec. 3.3, or the spline model of
+    App. A.5) with alpha, beta, gamma given, as in the experiment of Sec. 4.2:
+    (bucket sizes |c_0|..|c_gamma|, status) with status 0 bucketed, 1 single
+    value, 2 degenerate range."""
     k = _bits(keys).copy()
     counts = np.zeros(gamma + 1, dtype=np.uint64)
     status = ctypes.c_int(0)
-    rc = lib().orc_bucket_sizes(_p64(k), k.size, _kt(keys), seed, alpha, beta, gamma,
+    rc = lib().orc_bucket_sizes(_p64(k), k.size, _kt(keys), seed, alpha, beta, gamma, model,
                                 _p64(counts), ctypes.byref(status))
     if rc:
         raise RuntimeError("orc_bucket_sizes failed: %d" % rc)

@@ -40,6 +40,16 @@
  *      (-0 < +0); u64 keys compare as unsigned.
  *   R8 The fallback test is |c_j| >= delta with the parent's delta (Alg. 1).
  *   R9 NaN keys are rejected (the paper's domain is a subset of the reals).
+ *
+ * Spline Learned Sort (App. A.5, policy model 1): the same training (b as
+ * above); a key in bin k at relative position f in [t_k, t_{k+1}) gets
+ * F(x) = (b_{k-1} + f (b_k - b_{k-1})) / alpha with b_{-1} = 0.
+ *   R13 In binary64, round-to-nearest, no contraction, in this order:
+ *      p = RN(RN(x - lo) * s) (R3's value), k = clamp(floor(p), 0, beta),
+ *      f = p - k when 0 < p < beta (exact), else 0;
+ *      y = RN(b_{k-1} + RN(f * (b_k - b_{k-1})));
+ *      bucket = min(floor(RN(y * g)), gamma) with g = RN(gamma / alpha)
+ *      (floor(F gamma) of Alg. 1 with one division per model, not per key).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -58,6 +68,7 @@ typedef struct {
   uint32_t a_num, b_num, c_num, d_num; /* exponents of alpha, beta, gamma, delta ... */
   uint32_t den;                        /* ... as a_num/den etc.                        */
   uint64_t tau;                        /* small-input threshold                        */
+  uint32_t model;                      /* CDF model: 0 PCF (Sec. 3.3), 1 spline (A.5)  */
 } orc_policy;
 
 typedef struct {
@@ -319,19 +330,46 @@ static void policy_params(const orc_policy* P, uint64_t n, orc_level* L) {
 /* Buckets keys[0..n) in place (stable), filling L.  aux/auxv: scratch of n.
  * fixed3: alpha, beta, gamma given (the bucketing-failure experiment of
  * Sec. 4.2), else the policy's (delta is then 0: unused by one step). */
-static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint64_t* keys,
-                          uint32_t* vals, uint64_t n, int kt, uint64_t seed, uint64_t depth,
-                          uint64_t start, orc_level* L, uint64_t* aux, uint32_t* auxv);
+static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint32_t model,
+                          uint64_t* keys, uint32_t* vals, uint64_t n, int kt, uint64_t seed,
+                          uint64_t depth, uint64_t start, orc_level* L, uint64_t* aux,
+                          uint32_t* auxv);
 
 static int bucketize(const orc_policy* P, uint64_t* keys, uint32_t* vals, uint64_t n, int kt,
                      uint64_t seed, uint64_t depth, uint64_t start, orc_level* L,
                      uint64_t* aux, uint32_t* auxv) {
-  return bucketize_with(P, NULL, keys, vals, n, kt, seed, depth, start, L, aux, auxv);
+  return bucketize_with(P, NULL, P->model, keys, vals, n, kt, seed, depth, start, L, aux, auxv);
 }
 
-static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint64_t* keys,
-                          uint32_t* vals, uint64_t n, int kt, uint64_t seed, uint64_t depth,
-                          uint64_t start, orc_level* L, uint64_t* aux, uint32_t* auxv) {
+/* Spline model (App. A.5, R13): the bucket of key x from b (beta + 1). */
+static uint64_t spline_bucket(const orc_binfn* f, uint64_t xbits, const uint64_t* b,
+                              uint64_t gamma, double g) {
+  const double d = f->kt == ORC_KEY_F64 ? as_double(xbits) - f->lo
+                                        : (double)(xbits - f->lo_bits);
+  const double p = d * f->s;
+  uint64_t k;
+  double fr;
+  if (!(p < (double)f->beta)) {
+    k = f->beta;
+    fr = 0.0;
+  } else if (!(p > 0.0)) {
+    k = 0;
+    fr = 0.0;
+  } else {
+    k = (uint64_t)floor(p);
+    fr = p - (double)k;
+  }
+  const uint64_t bkm1 = k ? b[k - 1] : 0;
+  const double y = (double)bkm1 + fr * (double)(b[k] - bkm1);
+  const double z = y * g;
+  if (!(z < (double)gamma)) return gamma;
+  return z > 0.0 ? (uint64_t)floor(z) : 0;
+}
+
+static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint32_t model,
+                          uint64_t* keys, uint32_t* vals, uint64_t n, int kt, uint64_t seed,
+                          uint64_t depth, uint64_t start, orc_level* L, uint64_t* aux,
+                          uint32_t* auxv) {
   memset(L, 0, sizeof *L);
   /* x_min, x_max over the whole (sub)array, Sec. 3.3 */
   uint64_t lo = keys[0], hi = keys[0];
@@ -376,22 +414,33 @@ static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint64_t*
   for (uint64_t k = 0; k <= L->beta; ++k)
     L->T[k] = (uint64_t)(((unsigned __int128)L->b[k] * L->gamma) / L->alpha);
 
-  /* inference + Append: a stable counting scatter */
-  for (uint64_t i = 0; i < n; ++i) L->counts[L->T[binfn_eval(&f, keys[i])]] += 1;
+  /* inference (PCF: the table; spline: interpolated, R13) + Append: a
+     stable counting scatter */
+  const double g = (double)L->gamma / (double)L->alpha;
+  uint64_t* jk = (uint64_t*)malloc(n * sizeof(uint64_t));
   uint64_t* pos = (uint64_t*)malloc((L->gamma + 1) * sizeof(uint64_t));
-  if (!pos) return ORC_ERR_OOM;
+  if (!jk || !pos) {
+    free(jk);
+    free(pos);
+    return ORC_ERR_OOM;
+  }
+  for (uint64_t i = 0; i < n; ++i) {
+    jk[i] = model ? spline_bucket(&f, keys[i], L->b, L->gamma, g) : L->T[binfn_eval(&f, keys[i])];
+    L->counts[jk[i]] += 1;
+  }
   uint64_t acc = 0;
   for (uint64_t j = 0; j <= L->gamma; ++j) {
     pos[j] = acc;
     acc += L->counts[j];
   }
   for (uint64_t i = 0; i < n; ++i) {
-    uint64_t j = L->T[binfn_eval(&f, keys[i])];
+    const uint64_t j = jk[i];
     aux[pos[j]] = keys[i];
     if (vals) auxv[pos[j]] = vals[i];
     pos[j] += 1;
   }
   free(pos);
+  free(jk);
   memcpy(keys, aux, n * sizeof(uint64_t));
   if (vals) memcpy(vals, auxv, n * sizeof(uint32_t));
   L->status = 0;
@@ -468,7 +517,7 @@ int orc_sort(uint64_t* keys, uint32_t* vals, uint64_t n, int kt, uint64_t seed,
   memset(stats, 0, sizeof *stats);
   if (kt != ORC_KEY_F64 && kt != ORC_KEY_U64) return ORC_ERR_ARG;
   if (!P || P->den == 0 || P->a_num == 0 || P->a_num > P->den || P->b_num > P->den ||
-      P->c_num > P->den || P->d_num == 0 || P->d_num >= P->den)
+      P->c_num > P->den || P->d_num == 0 || P->d_num >= P->den || P->model > 1)
     return ORC_ERR_ARG;
   if (n == 0) return ORC_OK;
   if (!keys) return ORC_ERR_ARG;
@@ -528,11 +577,13 @@ int orc_level0(uint64_t* keys, uint32_t* vals, uint64_t n, int kt, uint64_t seed
 }
 
 /* One model-based bucketing of keys[0..n) with alpha, beta, gamma given
- * (Sec. 4.2: alpha = floor(n^a) ... varied over a grid): the bucket sizes
- * counts[0..gamma] and *status (0 bucketed, 1 single value, 2 degenerate).
+ * (Sec. 4.2: alpha = floor(n^a) ... varied over a grid) and the CDF model
+ * (0 PCF, 1 spline): the bucket sizes counts[0..gamma] and *status (0
+ * bucketed, 1 single value, 2 degenerate).
  * Keys are not modified. */
 int orc_bucket_sizes(const uint64_t* keys, uint64_t n, int kt, uint64_t seed, uint64_t alpha,
-                     uint64_t beta, uint64_t gamma, uint64_t* counts, int* status) {
+                     uint64_t beta, uint64_t gamma, uint32_t model, uint64_t* counts,
+                     int* status) {
   if (n < 2 || alpha < 1 || beta < 1 || gamma < 1 || has_nan(keys, n, kt)) return ORC_ERR_ARG;
   uint64_t* k = (uint64_t*)malloc(n * sizeof(uint64_t));
   uint64_t* aux = (uint64_t*)malloc(n * sizeof(uint64_t));
@@ -544,7 +595,7 @@ int orc_bucket_sizes(const uint64_t* keys, uint64_t n, int kt, uint64_t seed, ui
   memcpy(k, keys, n * sizeof(uint64_t));
   const uint64_t fixed3[3] = {alpha, beta, gamma};
   orc_level L;
-  int rc = bucketize_with(NULL, fixed3, k, NULL, n, kt, seed, 0, 0, &L, aux, NULL);
+  int rc = bucketize_with(NULL, fixed3, model, k, NULL, n, kt, seed, 0, 0, &L, aux, NULL);
   free(k);
   free(aux);
   if (rc) {
