@@ -149,14 +149,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_gkeys(keys_list):
+def cpu_oracle_gkeys(keys_list, model="pcf"):
     """Single-threaded oracle on the first CPU_SAMPLE_N keys of each array."""
     import oracle
+    pol = oracle.paper_policy(model=oracle.MODEL_SPLINE if model == "spline" else oracle.MODEL_PCF)
     total, secs = 0, 0.0
     for x in keys_list:
         s = np.ascontiguousarray(x[:CPU_SAMPLE_N])
         t0 = time.perf_counter()
-        oracle.sort(s)
+        oracle.sort(s, policy=pol)
         secs += time.perf_counter() - t0
         total += s.size
     return total / secs / 1e9, total, secs
@@ -203,6 +204,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N, help="keys per array (default 10^8)")
+    ap.add_argument("--model", default="pcf", choices=["pcf", "spline"],
+                    help="CDF model of the plain workload: the PCF of Sec. 3.3 (default) "
+                         "or the spline of App. A.5 (Spline Learned Sort)")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "small", "zipf", "batched", "serve", "dupinject",
                              "failsweep"],
@@ -237,6 +241,8 @@ def main():
     ins = [torch.from_numpy(x).to(dev) for x in host_keys]
     outs = [torch.empty_like(t) for t in ins]
     ctx = pcfsort.Context(local)
+    if args.model != "pcf":
+        ctx.set_policy(model=args.model)
     ctx.reserve(n)
     # the sorts' own stream (created non-blocking by torch): on the legacy
     # default stream every launch would also order against other streams
@@ -330,7 +336,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if n == N else WORKLOAD.replace("10^8", str(n)),
+        "config": {"workload": (WORKLOAD if n == N else WORKLOAD.replace("10^8", str(n)))
+                   .replace("plain PCF sort", "plain PCF sort" if args.model == "pcf"
+                            else "Spline Learned Sort (App. A.5)"),
                    "n_per_array": n, "arrays_per_step": 4,
                    "l2": "inputs larger than L2 (800 MB per array, L2 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -351,7 +359,7 @@ def main():
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, total, secs = cpu_oracle_gkeys(host_keys)
+        v, total, secs = cpu_oracle_gkeys(host_keys, args.model)
         line["cpu_baseline"] = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
                                 "sample": "first %d keys of each of the 4 arrays (%d keys, %.1f s)"
                                           % (CPU_SAMPLE_N, total, secs)}

@@ -59,13 +59,22 @@ typedef enum {
   PCF_ERR_INTERNAL = 6     /* an internal consistency check failed                     */
 } pcf_status;
 
+/* CDF model of every bucketing step: the piecewise-constant PCF of Sec. 3.3
+ * (F(x) = b_k / alpha in bin k), or the piecewise-linear spline through the
+ * same counts of Spline Learned Sort (App. A.5: F(x) = (b_{k-1} + f (b_k -
+ * b_{k-1})) / alpha, f the key's position in its bin).  Binary64 evaluation,
+ * the order of operations stated in the library's design notes. */
+typedef enum { PCF_MODEL_PCF = 0, PCF_MODEL_SPLINE = 1 } pcf_model;
+
 /* Parameters of Algorithm 1: alpha = floor(n^(a_num/den)), beta = ...(b_num),
  * gamma = ...(c_num), delta = ...(d_num), recomputed for every (sub)array
- * from its own n; tau is the small-input threshold.  Supported: den in 1..4,
- * 1 <= a_num, b_num, c_num <= den, 1 <= d_num < den (0 < d < 1, as
- * Lemma nlogn requires), 16 <= tau <= 65535.  Default: {3,3,3,3,4,100}. */
+ * from its own n; tau is the small-input threshold; model a pcf_model.
+ * Supported: den in 1..4, 1 <= a_num, b_num, c_num <= den, 1 <= d_num < den
+ * (0 < d < 1, as Lemma nlogn requires), 16 <= tau <= 65535.
+ * Default: {3,3,3,3,4,PCF_MODEL_PCF,100}. */
 typedef struct {
   uint32_t a_num, b_num, c_num, d_num, den;
+  uint32_t model;
   uint64_t tau;
 } pcf_policy;
 

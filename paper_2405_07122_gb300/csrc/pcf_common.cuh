@@ -87,9 +87,13 @@ PCF_HD uint64_t root_floor(uint64_t n, uint32_t p, uint32_t q) {
   return m;
 }
 
+// CDF model of a bucketing step: the PCF of Sec. 3.3, or the piecewise
+// linear spline through the same counts (Spline Learned Sort, App. A.5).
+enum : uint32_t { MODEL_PCF = 0, MODEL_SPLINE = 1 };
+
 struct Policy {
   uint32_t a_num, b_num, c_num, d_num, den;
-  uint32_t pad;
+  uint32_t model;  // MODEL_*
   uint64_t tau;
 };
 
@@ -142,6 +146,9 @@ struct BinModel {
   uint32_t beta;
   uint32_t kt;
   uint32_t mode;     // f64: 0 general; 1 / 2: lo and hi share sign and exponent (+ / -)
+  uint32_t spline;   // 1: the spline model (bucket ids from spline_bucket)
+  uint32_t gamma;    // spline: the bucket count - 1 ...
+  double g;          // ... and RN(gamma / alpha)
 };
 
 PCF_HD double as_f64(uint64_t b) {
@@ -167,6 +174,13 @@ PCF_HD double dsub(double a, double b) {
   return __dsub_rn(a, b);
 #else
   return a - b;
+#endif
+}
+PCF_HD double dadd(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
 #endif
 }
 PCF_HD double dmul(double a, double b) {
@@ -224,6 +238,9 @@ PCF_HD int make_bin_model(uint32_t kt, uint64_t lo_bits, uint64_t hi_bits, uint3
   M->beta = beta;
   M->lo_bits = lo_bits;
   M->mode = 0;
+  M->spline = 0;
+  M->gamma = 0;
+  M->g = 0.0;
   double r;
   int32_t H;  // grid exponent: X(y) ~ y / 2^H
   if (kt == KEY_F64) {
@@ -364,6 +381,58 @@ PCF_HD bool bin_fast_decides(const BinModel& M, uint64_t xbits) {
 PCF_HD uint32_t bucket_of_count(uint32_t bk, uint32_t alpha, uint32_t gamma) {
   if (alpha == gamma) return bk;
   return (uint32_t)(((uint64_t)bk * gamma) / alpha);
+}
+
+// --------------------------------------------------------------------------
+// Spline model (App. A.5).  For x in bin k at relative position f in
+// [t_k, t_{k+1}), F(x) = (b_{k-1} + f (b_k - b_{k-1})) / alpha with
+// b_{-1} = 0, and the bucket is floor(F gamma).  Binary64, round to nearest,
+// no contraction, in this order:
+//   p = RN(RN(x - lo) s)   (the bin's own value: k = clamp(floor(p), 0, beta))
+//   f = p - k for 0 < p < beta (exact), else 0
+//   y = RN(b_{k-1} + RN(f (b_k - b_{k-1})))
+//   j = min(floor(RN(y g)), gamma),  g = RN(gamma / alpha)
+// j does not decrease with x (each step is monotone, and y never passes b_k
+// inside bin k), so buckets stay ordered (Sec. 3.2).
+// --------------------------------------------------------------------------
+PCF_HD void spline_set(BinModel* M, uint32_t alpha, uint32_t gamma) {
+  M->spline = 1;
+  M->gamma = gamma;
+  M->g = ddiv((double)gamma, (double)alpha);
+}
+
+// bin of x and its position in it (the first two steps above)
+PCF_HD uint32_t spline_bin(const BinModel& M, uint64_t xbits, double* f) {
+  const double d = M.kt == KEY_F64 ? dsub(as_f64(xbits), M.lo_d) : u64_to_f64(xbits - M.lo_bits);
+  const double p = dmul(d, M.s);
+  if (!(p < (double)M.beta)) {
+    *f = 0.0;
+    return M.beta;
+  }
+  if (!(p > 0.0)) {
+    *f = 0.0;
+    return 0u;
+  }
+#ifdef __CUDA_ARCH__
+  const uint32_t k = __double2uint_rd(p);
+#else
+  const uint32_t k = (uint32_t)__builtin_floor(p);
+#endif
+  *f = dsub(p, (double)k);
+  return k;
+}
+
+// bucket of x from its bin k, position f and the cumulative counts
+// b_{k-1} (0 for k = 0) and b_k
+PCF_HD uint32_t spline_bucket(const BinModel& M, double f, uint32_t bkm1, uint32_t bk) {
+  const double y = dadd((double)bkm1, dmul(f, (double)(bk - bkm1)));
+  const double z = dmul(y, M.g);
+  if (!(z < (double)M.gamma)) return M.gamma;
+#ifdef __CUDA_ARCH__
+  return z > 0.0 ? __double2uint_rd(z) : 0u;
+#else
+  return z > 0.0 ? (uint32_t)__builtin_floor(z) : 0u;
+#endif
 }
 
 }  // namespace pcf

@@ -224,6 +224,7 @@ bool policy_ok(const Policy& P) {
   if (P.c_num < 1 || P.c_num > P.den) return false;
   if (P.d_num < 1 || P.d_num >= P.den) return false;
   if (P.tau < 16 || P.tau > 65535) return false;
+  if (P.model != MODEL_PCF && P.model != MODEL_SPLINE) return false;
   return true;
 }
 
@@ -616,6 +617,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   lc.kt = kt;
   lc.pairs = pairs;
   lc.launches = &ctx->stats.kernel_launches;
+  lc.model = ctx->policy.model;
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
   CK(cudaMemsetAsync(lc.status, 0, 4, st));
@@ -1006,7 +1008,7 @@ pcf_status pcf_ctx_destroy(pcf_ctx* ctx) {
 
 pcf_status pcf_ctx_set_policy(pcf_ctx* ctx, const pcf_policy* p) {
   if (!ctx || !p) return PCF_ERR_INVALID_ARG;
-  Policy P{p->a_num, p->b_num, p->c_num, p->d_num, p->den, 0, p->tau};
+  Policy P{p->a_num, p->b_num, p->c_num, p->d_num, p->den, p->model, p->tau};
   if (!policy_ok(P)) return PCF_ERR_INVALID_ARG;
   ctx->policy = P;
   return PCF_OK;
@@ -1227,6 +1229,7 @@ pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_
   lc.kt = (uint32_t)kt;
   lc.pairs = false;
   lc.launches = &ctx->stats.kernel_launches;
+  lc.model = ctx->policy.model;
   ctx->stats = pcf_call_stats{};
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);

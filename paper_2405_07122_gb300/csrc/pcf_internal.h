@@ -132,6 +132,7 @@ struct KeyBufs {
 struct LaunchCfg {
   cudaStream_t stream;
   uint32_t kt;
+  uint32_t model = MODEL_PCF;  // the policy's CDF model
   bool pairs;
   uint32_t* status;  // device status word
   uint64_t* launches;  // host counter of kernel launches (may be null)

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_range(Seg* segs, uint32_t S, const uint
 // ---------------------------------------------------------------------------
 // k_model: Alg. 1's early exits and the bin constants
 // ---------------------------------------------------------------------------
-__global__ void k_model(Seg* segs, uint32_t S, uint32_t kt) {
+__global__ void k_model(Seg* segs, uint32_t S, uint32_t kt, uint32_t model) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   Seg& g = segs[s];
@@ -110,6 +110,7 @@ __global__ void k_model(Seg* segs, uint32_t S, uint32_t kt) {
   }
   const uint64_t lo = bits_of_ord(g.ord_lo, kt), hi = bits_of_ord(g.ord_hi, kt);
   g.status = make_bin_model(kt, lo, hi, g.beta, &g.bm) ? SEG_DEGEN : SEG_BUCKET;
+  if (g.status == SEG_BUCKET && model == MODEL_SPLINE) spline_set(&g.bm, g.alpha, g.gamma);
 }
 
 // ---------------------------------------------------------------------------
@@ -229,6 +230,24 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
   if (g.status != SEG_BUCKET) {
     // not bucketed: keep the count matrix consistent (all keys in digit 0)
     if (threadIdx.x == 0) hist[0] = (uint32_t)(end - base);
+  } else if (bm.spline) {
+    // spline model: the bin and the position in it in binary64, then
+    // b_{k-1} and b_k from the table pool (inclusive scan values)
+    const uint32_t* T = tpool + g.T_off;
+    const uint32_t tb = g.tbase;
+    for (uint64_t i0 = base; i0 < end; i0 += 256) {
+      const uint64_t i = i0 + threadIdx.x;
+      const bool v = i < end;
+      uint32_t j = 0;
+      if (v) {
+        double f;
+        const uint32_t k = spline_bin(bm, ld_nc(keys + i), &f);
+        const uint32_t bk = __ldg(T + k) - tb, bkm1 = k ? __ldg(T + k - 1) - tb : 0u;
+        j = spline_bucket(bm, f, bkm1, bk);
+        jout[i] = j;
+      }
+      hist_inc(hist, j >> b2, v, agg);
+    }
   } else {
     const uint32_t* T = tpool + g.T_off;
     const uint32_t tb = g.tbase, al = g.alpha, ga = g.gamma;
@@ -1023,7 +1042,7 @@ cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32
 
 cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S) {
   if (!S) return cudaSuccess;
-  k_model<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, c.kt);
+  k_model<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, c.kt, c.model);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -293,7 +293,7 @@ __device__ void std_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) 
 // are finished here (ranked) when small, else pushed.  Returns false when
 // the per-warp stack would overflow.
 // ---------------------------------------------------------------------------
-template <bool PAIRS>
+template <bool PAIRS, bool SPLINE>
 __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                            uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
                            uint32_t& top, uint32_t lane, bool root, uint64_t rmn, uint64_t rmx) {
@@ -319,8 +319,12 @@ __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, 
   if (mn == mx) return true;  // one value: sorted
   const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
   const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
+  constexpr bool spline = SPLINE;
   int degen = 0;
-  if (lane == 0) degen = make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
+  if (lane == 0) {
+    degen = make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
+    if (!degen && spline) spline_set(w.bm, alpha, gamma);
+  }
   degen = __shfl_sync(~0u, degen, 0);
   if (degen) {  // R5: a degenerate range goes to Standard-Sort
     std_sort<PAIRS>(w, o, n, lane);
@@ -348,13 +352,22 @@ __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, 
       const uint32_t k = k0 + lane;
       const uint32_t v = k <= beta ? w.tab[k] : 0u;
       const uint32_t inc = wscan(v, lane) + carry;
-      if (k <= beta) w.tab[k] = bucket_of_count(inc, alpha, gamma);
+      if (k <= beta) w.tab[k] = spline ? inc : bucket_of_count(inc, alpha, gamma);
       carry = __shfl_sync(~0u, inc, 31);
     }
   }
   __syncwarp();
   // the bucket of every key, and the bucket sizes
-  for (uint32_t i0 = 0; i0 < n; i0 += 64) {
+  if (spline) {
+    for (uint32_t i = lane; i < n; i += 32) {
+      double f;
+      const uint32_t k = spline_bin(bm, bits_of_ord(w.A[o + i], kt), &f);
+      const uint32_t j = spline_bucket(bm, f, k ? w.tab[k - 1] : 0u, w.tab[k]);
+      w.J[i] = (uint16_t)j;
+      atomicAdd(&w.cnt[j], 1u);
+    }
+  }
+  for (uint32_t i0 = 0; i0 < (spline ? 0u : n); i0 += 64) {
     uint64_t x[2];
     uint32_t bn[2], amb = 0;
 #pragma unroll
@@ -497,7 +510,7 @@ __global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t 
   }
 }
 
-template <bool PAIRS>
+template <bool PAIRS, bool SPLINE>
 __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restrict__ br,
                                                            const uint32_t* __restrict__ list,
                                                            const uint32_t* __restrict__ count,
@@ -546,7 +559,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
         const Item it = w.stk[top];
         __syncwarp();
         if (it.std) std_sort<PAIRS>(w, it.o, it.n, lane);
-        else ok = learn_step<PAIRS>(w, geo, it, r.seed, kt, P, ptab, top, lane, root, rmn, rmx);
+        else ok = learn_step<PAIRS, SPLINE>(w, geo, it, r.seed, kt, P, ptab, top, lane, root, rmn, rmx);
         root = false;
       }
     }
@@ -581,10 +594,12 @@ struct CtaShared {
 
 // Scan of src[0..m) into dst by the CTA (each thread a contiguous run, one
 // barrier; src may be dst).  EXCL: exclusive sums.  Otherwise the inclusive
-// sums b_k turned into the bucket table floor(b_k gamma / alpha).
+// sums b_k, turned into the bucket table floor(b_k gamma / alpha) unless raw
+// (the spline model reads b_k itself).
 template <uint32_t NT, bool EXCL>
 __device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uint32_t m,
-                                         uint32_t alpha, uint32_t gamma, CtaShared<NT>& sh) {
+                                         uint32_t alpha, uint32_t gamma, CtaShared<NT>& sh,
+                                         bool raw = false) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t r = (m + NT - 1) / NT;
   const uint32_t a = min(m, tid * r), b = min(m, a + r);
@@ -603,7 +618,7 @@ __device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uin
       run += v;
     } else {
       run += v;
-      dst[k] = bucket_of_count(run, alpha, gamma);
+      dst[k] = raw ? run : bucket_of_count(run, alpha, gamma);
     }
   }
 }
@@ -614,7 +629,7 @@ __device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uin
 constexpr uint32_t kSampRegs = 3;
 
 // root: the range was reduced into sh.mn / sh.mx while the keys were loaded
-template <uint32_t NT>
+template <uint32_t NT, bool SPLINE>
 __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                                uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
                                CtaShared<NT>& sh, bool root) {
@@ -648,8 +663,11 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   if (mn == mx) return;  // one value: sorted
   const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
   const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
-  if (tid == 0)
+  constexpr bool spline = SPLINE;
+  if (tid == 0) {
     sh.flag = (uint32_t)make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
+    if (!sh.flag && spline) spline_set(w.bm, alpha, gamma);
+  }
   for (uint32_t k = tid; k <= beta; k += NT) w.tab[k] = 0;
   for (uint32_t k = tid; k <= gamma; k += NT) w.cnt[k] = 0;
   // the sample positions and keys do not depend on the model: draw them
@@ -684,9 +702,18 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     atomicAdd(&w.tab[bn], 1u);
   }
   __syncthreads();
-  cta_scan<NT, false>(w.tab, w.tab, beta + 1, alpha, gamma, sh);
+  cta_scan<NT, false>(w.tab, w.tab, beta + 1, alpha, gamma, sh, spline);
   __syncthreads();
-  for (uint32_t i0 = 0; i0 < n; i0 += 2 * NT) {
+  if (spline) {
+    for (uint32_t i = tid; i < n; i += NT) {
+      double f;
+      const uint32_t k = spline_bin(bm, bits_of_ord(w.A[o + i], kt), &f);
+      const uint32_t j = spline_bucket(bm, f, k ? w.tab[k - 1] : 0u, w.tab[k]);
+      w.J[i] = (uint16_t)j;
+      atomicAdd(&w.cnt[j], 1u);
+    }
+  }
+  for (uint32_t i0 = 0; i0 < (spline ? 0u : n); i0 += 2 * NT) {
     uint64_t x[2];
     uint32_t bn[2], amb = 0;
 #pragma unroll
@@ -752,7 +779,7 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   }
 }
 
-template <uint32_t NT>
+template <uint32_t NT, bool SPLINE>
 __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(const BRec* __restrict__ br,
                                                         const uint32_t* __restrict__ list,
                                                         const uint32_t* __restrict__ count,
@@ -811,7 +838,8 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
         __syncthreads();
         if (wid == 0) std_sort<false>(w, it.o, it.n, lane);
       } else {
-        learn_step_cta<NT>(w, geo, it, r.seed, kt, P, ptab, sh, top == 1 && it.o == 0 && it.n == n);
+        learn_step_cta<NT, SPLINE>(w, geo, it, r.seed, kt, P, ptab, sh,
+                                   top == 1 && it.o == 0 && it.n == n);
       }
       __syncthreads();
     }
@@ -859,16 +887,40 @@ uint32_t onchip_classes(uint32_t leaf_cap) {
 }
 
 // one CTA of NT threads per bucket of the class whose slices are g.bytes
-template <uint32_t NT>
-static cudaError_t launch_cta_class(const LaunchCfg& c, const BRec* br, const uint32_t* list,
+template <uint32_t NT, bool SPLINE>
+static cudaError_t launch_cta_model(const LaunchCfg& c, const BRec* br, const uint32_t* list,
                                     const uint32_t* count, const OnchipGeo& g, const uint64_t* X,
                                     uint64_t* out, const Policy& P, const uint16_t* ptab) {
   constexpr uint32_t kMaxPerSm = NT <= 64 ? 16u : 512u / NT;
   const uint32_t per = max(1u, min(kMaxPerSm, (uint32_t)((227u * 1024u) / (g.bytes + 1024u))));
-  cudaError_t e = allow_max_smem((const void*)k_onchip_cta<NT>);
+  cudaError_t e = allow_max_smem((const void*)k_onchip_cta<NT, SPLINE>);
   if (e) return e;
-  k_onchip_cta<NT><<<(uint32_t)num_sms_of_current_device() * per, NT, g.bytes, c.stream>>>(
-      br, list, count, g, X, out, c.kt, P, ptab, c.status);
+  k_onchip_cta<NT, SPLINE><<<(uint32_t)num_sms_of_current_device() * per, NT, g.bytes,
+                             c.stream>>>(br, list, count, g, X, out, c.kt, P, ptab, c.status);
+  return cudaGetLastError();
+}
+
+template <uint32_t NT>
+static cudaError_t launch_cta_class(const LaunchCfg& c, const BRec* br, const uint32_t* list,
+                                    const uint32_t* count, const OnchipGeo& g, const uint64_t* X,
+                                    uint64_t* out, const Policy& P, const uint16_t* ptab) {
+  return P.model == MODEL_SPLINE
+             ? launch_cta_model<NT, true>(c, br, list, count, g, X, out, P, ptab)
+             : launch_cta_model<NT, false>(c, br, list, count, g, X, out, P, ptab);
+}
+
+template <bool PAIRS, bool SPLINE>
+static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const uint32_t* list,
+                                     const uint32_t* count, const OnchipGeo& g, const uint64_t* X,
+                                     const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
+                                     const Policy& P, const uint16_t* ptab) {
+  const size_t sm = (size_t)kWarps * g.bytes;
+  const uint32_t per_sm = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm + 1024u))));
+  const uint32_t grid = (uint32_t)num_sms_of_current_device() * per_sm;
+  cudaError_t e = allow_max_smem((const void*)k_onchip<PAIRS, SPLINE>);
+  if (e) return e;
+  k_onchip<PAIRS, SPLINE><<<grid, kWarps * 32, sm, c.stream>>>(br, list, count, g, X, Xv, out,
+                                                               out_v, c.kt, P, ptab, c.status);
   return cudaGetLastError();
 }
 
@@ -909,19 +961,18 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
       else e = launch_cta_class<512>(c, br, list, counts + cls, g, X, out, P, ptab);
       if (e) return e;
     } else {
-      const size_t sm = (size_t)kWarps * g.bytes;
-      const uint32_t per_sm = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm + 1024u))));
-      const uint32_t grid = (uint32_t)num_sms_of_current_device() * per_sm;
-      if (c.pairs) {
-        if ((e = allow_max_smem((const void*)k_onchip<true>))) return e;
-        k_onchip<true><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv,
-                                                           out, out_v, c.kt, P, ptab, c.status);
-      } else {
-        if ((e = allow_max_smem((const void*)k_onchip<false>))) return e;
-        k_onchip<false><<<grid, kWarps * 32, sm, c.stream>>>(br, list, counts + cls, g, X, Xv,
-                                                            out, out_v, c.kt, P, ptab, c.status);
-      }
-      if ((e = cudaGetLastError())) return e;
+      const bool sp = P.model == MODEL_SPLINE;
+      if (c.pairs)
+        e = sp ? launch_warp_model<true, true>(c, br, list, counts + cls, g, X, Xv, out, out_v, P,
+                                               ptab)
+               : launch_warp_model<true, false>(c, br, list, counts + cls, g, X, Xv, out, out_v,
+                                                P, ptab);
+      else
+        e = sp ? launch_warp_model<false, true>(c, br, list, counts + cls, g, X, Xv, out, out_v,
+                                                P, ptab)
+               : launch_warp_model<false, false>(c, br, list, counts + cls, g, X, Xv, out, out_v,
+                                                 P, ptab);
+      if (e) return e;
     }
     count_launch(c);
     lo = hi;
