@@ -29,7 +29,7 @@ class Policy(ctypes.Structure):
     _fields_ = [("a_num", ctypes.c_uint32), ("b_num", ctypes.c_uint32),
                 ("c_num", ctypes.c_uint32), ("d_num", ctypes.c_uint32),
                 ("den", ctypes.c_uint32), ("tau", ctypes.c_uint64),
-                ("model", ctypes.c_uint32)]
+                ("model", ctypes.c_uint32), ("range_mode", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -42,9 +42,13 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-def paper_policy(tau: int = 100, model: int = MODEL_PCF) -> Policy:
-    """alpha = beta = gamma = delta = floor(n^{3/4}), tau = 100 (Sec. 4 setup)."""
-    return Policy(3, 3, 3, 3, 4, tau, model)
+RANGE_ARRAY, RANGE_SAMPLE = 0, 1
+
+
+def paper_policy(tau: int = 100, model: int = MODEL_PCF, range_mode: int = RANGE_ARRAY) -> Policy:
+    """alpha = beta = gamma = delta = floor(n^{3/4}), tau = 100 (Sec. 4 setup);
+    range_mode RANGE_SAMPLE bins over the samples' range (reading R14)."""
+    return Policy(3, 3, 3, 3, 4, tau, model, range_mode)
 
 
 _lib = None
@@ -79,7 +83,8 @@ def lib():
         L.orc_bucket_sizes.restype = ctypes.c_int
         L.orc_bucket_sizes.argtypes = [_u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
                                        ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
-                                       ctypes.c_uint32, _u64p, ctypes.POINTER(ctypes.c_int)]
+                                       ctypes.c_uint32, ctypes.c_uint32, _u64p,
+                                       ctypes.POINTER(ctypes.c_int)]
         L.brute_insertion_sort.restype = None
         L.brute_insertion_sort.argtypes = [_u64p, _u32p, ctypes.c_uint64, ctypes.c_int]
         L.brute_cumulative_counts.restype = None
@@ -191,7 +196,7 @@ def level0(keys: np.ndarray, vals: np.ndarray = None, seed: int = 0, policy: Pol
 
 
 def bucket_sizes(keys: np.ndarray, seed: int, alpha: int, beta: int, gamma: int,
-                 model: int = MODEL_PCF):
+                 model: int = MODEL_PCF, range_mode: int = 0):
     """One model-based bucketing (Alg. 1 + Sec. 3.3, or the spline model of
     App. A.5) with alpha, beta, gamma given, as in the experiment of Sec. 4.2:
     (bucket sizes |c_0|..|c_gamma|, status) with status 0 bucketed, 1 single
@@ -200,7 +205,7 @@ def bucket_sizes(keys: np.ndarray, seed: int, alpha: int, beta: int, gamma: int,
     counts = np.zeros(gamma + 1, dtype=np.uint64)
     status = ctypes.c_int(0)
     rc = lib().orc_bucket_sizes(_p64(k), k.size, _kt(keys), seed, alpha, beta, gamma, model,
-                                _p64(counts), ctypes.byref(status))
+                                range_mode, _p64(counts), ctypes.byref(status))
     if rc:
         raise RuntimeError("orc_bucket_sizes failed: %d" % rc)
     return counts, status.value

@@ -50,6 +50,15 @@
  *      y = RN(b_{k-1} + RN(f * (b_k - b_{k-1})));
  *      bucket = min(floor(RN(y * g)), gamma) with g = RN(gamma / alpha)
  *      (floor(F gamma) of Alg. 1 with one division per model, not per key).
+ *
+ * Sample range (policy range_mode 1; SURVEY reading D9, a cheaper variant
+ * of Sec. 3.3's whole-array range):
+ *   R14 lo, hi = the minimum and maximum of the alpha sampled keys (R2's
+ *      indices).  If they are equal, or R5 finds that range degenerate, the
+ *      (sub)array's own range is used instead, with R4 and R5 as usual.  A
+ *      key below lo gets bin 0 (and, in the spline, position 0); a key above
+ *      hi gets R3's value (RN(x - lo) is then at least RN(hi - lo), so the
+ *      clamp at beta keeps bins monotone).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -69,6 +78,7 @@ typedef struct {
   uint32_t den;                        /* ... as a_num/den etc.                        */
   uint64_t tau;                        /* small-input threshold                        */
   uint32_t model;                      /* CDF model: 0 PCF (Sec. 3.3), 1 spline (A.5)  */
+  uint32_t range_mode;                 /* 0: the (sub)array's range; 1: the sample's (R14) */
 } orc_policy;
 
 typedef struct {
@@ -191,6 +201,7 @@ static double as_double(uint64_t bits) {
 typedef struct {
   int kt;
   uint64_t lo_bits;
+  uint64_t lo_ord; /* lo in the total order: keys below it get bin 0 (R14) */
   double lo; /* f64 keys only */
   double s;  /* beta / range */
   uint64_t beta;
@@ -201,6 +212,7 @@ static int binfn_make(orc_binfn* f, int kt, uint64_t lo_bits, uint64_t hi_bits, 
   double r;
   f->kt = kt;
   f->lo_bits = lo_bits;
+  f->lo_ord = ord_key(lo_bits, kt);
   f->beta = beta;
   if (kt == ORC_KEY_F64) {
     f->lo = as_double(lo_bits);
@@ -216,6 +228,7 @@ static int binfn_make(orc_binfn* f, int kt, uint64_t lo_bits, uint64_t hi_bits, 
 }
 
 static uint64_t binfn_eval(const orc_binfn* f, uint64_t xbits) {
+  if (ord_key(xbits, f->kt) < f->lo_ord) return 0; /* only with a sample range */
   double d;
   if (f->kt == ORC_KEY_F64) d = as_double(xbits) - f->lo;
   else d = (double)(xbits - f->lo_bits);
@@ -349,7 +362,10 @@ static uint64_t spline_bucket(const orc_binfn* f, uint64_t xbits, const uint64_t
   const double p = d * f->s;
   uint64_t k;
   double fr;
-  if (!(p < (double)f->beta)) {
+  if (ord_key(xbits, f->kt) < f->lo_ord) { /* below a sample range (R14) */
+    k = 0;
+    fr = 0.0;
+  } else if (!(p < (double)f->beta)) {
     k = f->beta;
     fr = 0.0;
   } else if (!(p > 0.0)) {
@@ -371,14 +387,6 @@ static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint32_t 
                           uint64_t depth, uint64_t start, orc_level* L, uint64_t* aux,
                           uint32_t* auxv) {
   memset(L, 0, sizeof *L);
-  /* x_min, x_max over the whole (sub)array, Sec. 3.3 */
-  uint64_t lo = keys[0], hi = keys[0];
-  for (uint64_t i = 1; i < n; ++i) {
-    if (ord_key(keys[i], kt) < ord_key(lo, kt)) lo = keys[i];
-    if (ord_key(keys[i], kt) > ord_key(hi, kt)) hi = keys[i];
-  }
-  L->lo_bits = lo;
-  L->hi_bits = hi;
   if (fixed3) {
     L->alpha = fixed3[0];
     L->beta = fixed3[1];
@@ -387,14 +395,39 @@ static int bucketize_with(const orc_policy* P, const uint64_t* fixed3, uint32_t 
   } else {
     policy_params(P, n, L);
   }
-  if (lo == hi) {
-    L->status = 1;
-    return ORC_OK;
-  }
   orc_binfn f;
-  if (binfn_make(&f, kt, lo, hi, L->beta)) {
-    L->status = 2;
-    return ORC_OK;
+  uint64_t lo = keys[0], hi = keys[0];
+  int have_model = 0;
+  if (P && P->range_mode == 1) {
+    /* R14: the range of the alpha samples */
+    const uint64_t st0 = orc_sample_state(seed, depth, start, n);
+    lo = hi = keys[orc_sample_index(st0, 0, n)];
+    for (uint64_t j = 1; j < L->alpha; ++j) {
+      const uint64_t x = keys[orc_sample_index(st0, j, n)];
+      if (ord_key(x, kt) < ord_key(lo, kt)) lo = x;
+      if (ord_key(x, kt) > ord_key(hi, kt)) hi = x;
+    }
+    have_model = lo != hi && !binfn_make(&f, kt, lo, hi, L->beta);
+  }
+  if (!have_model) {
+    /* x_min, x_max over the whole (sub)array, Sec. 3.3 */
+    lo = hi = keys[0];
+    for (uint64_t i = 1; i < n; ++i) {
+      if (ord_key(keys[i], kt) < ord_key(lo, kt)) lo = keys[i];
+      if (ord_key(keys[i], kt) > ord_key(hi, kt)) hi = keys[i];
+    }
+  }
+  L->lo_bits = lo;
+  L->hi_bits = hi;
+  if (!have_model) {
+    if (lo == hi) {
+      L->status = 1;
+      return ORC_OK;
+    }
+    if (binfn_make(&f, kt, lo, hi, L->beta)) {
+      L->status = 2;
+      return ORC_OK;
+    }
   }
   L->sample_idx = (uint64_t*)malloc(L->alpha * sizeof(uint64_t));
   L->b = (uint64_t*)calloc(L->beta + 1, sizeof(uint64_t));
@@ -517,7 +550,8 @@ int orc_sort(uint64_t* keys, uint32_t* vals, uint64_t n, int kt, uint64_t seed,
   memset(stats, 0, sizeof *stats);
   if (kt != ORC_KEY_F64 && kt != ORC_KEY_U64) return ORC_ERR_ARG;
   if (!P || P->den == 0 || P->a_num == 0 || P->a_num > P->den || P->b_num > P->den ||
-      P->c_num > P->den || P->d_num == 0 || P->d_num >= P->den || P->model > 1)
+      P->c_num > P->den || P->d_num == 0 || P->d_num >= P->den || P->model > 1 ||
+      P->range_mode > 1)
     return ORC_ERR_ARG;
   if (n == 0) return ORC_OK;
   if (!keys) return ORC_ERR_ARG;
@@ -577,13 +611,14 @@ int orc_level0(uint64_t* keys, uint32_t* vals, uint64_t n, int kt, uint64_t seed
 }
 
 /* One model-based bucketing of keys[0..n) with alpha, beta, gamma given
- * (Sec. 4.2: alpha = floor(n^a) ... varied over a grid) and the CDF model
- * (0 PCF, 1 spline): the bucket sizes counts[0..gamma] and *status (0
- * bucketed, 1 single value, 2 degenerate).
+ * (Sec. 4.2: alpha = floor(n^a) ... varied over a grid), the CDF model
+ * (0 PCF, 1 spline) and the range (0 the array's, 1 the sample's, R14): the
+ * bucket sizes counts[0..gamma] and *status (0 bucketed, 1 single value, 2
+ * degenerate).
  * Keys are not modified. */
 int orc_bucket_sizes(const uint64_t* keys, uint64_t n, int kt, uint64_t seed, uint64_t alpha,
-                     uint64_t beta, uint64_t gamma, uint32_t model, uint64_t* counts,
-                     int* status) {
+                     uint64_t beta, uint64_t gamma, uint32_t model, uint32_t range_mode,
+                     uint64_t* counts, int* status) {
   if (n < 2 || alpha < 1 || beta < 1 || gamma < 1 || has_nan(keys, n, kt)) return ORC_ERR_ARG;
   uint64_t* k = (uint64_t*)malloc(n * sizeof(uint64_t));
   uint64_t* aux = (uint64_t*)malloc(n * sizeof(uint64_t));
@@ -595,7 +630,11 @@ int orc_bucket_sizes(const uint64_t* keys, uint64_t n, int kt, uint64_t seed, ui
   memcpy(k, keys, n * sizeof(uint64_t));
   const uint64_t fixed3[3] = {alpha, beta, gamma};
   orc_level L;
-  int rc = bucketize_with(NULL, fixed3, model, k, NULL, n, kt, seed, 0, 0, &L, aux, NULL);
+  orc_policy rp;
+  memset(&rp, 0, sizeof rp);
+  rp.model = model;
+  rp.range_mode = range_mode;
+  int rc = bucketize_with(&rp, fixed3, model, k, NULL, n, kt, seed, 0, 0, &L, aux, NULL);
   free(k);
   free(aux);
   if (rc) {
