@@ -149,10 +149,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_gkeys(keys_list, model="pcf"):
+def cpu_oracle_gkeys(keys_list, model="pcf", range_mode="array"):
     """Single-threaded oracle on the first CPU_SAMPLE_N keys of each array."""
     import oracle
-    pol = oracle.paper_policy(model=oracle.MODEL_SPLINE if model == "spline" else oracle.MODEL_PCF)
+    pol = oracle.paper_policy(
+        model=oracle.MODEL_SPLINE if model == "spline" else oracle.MODEL_PCF,
+        range_mode=oracle.RANGE_SAMPLE if range_mode == "sample" else oracle.RANGE_ARRAY)
     total, secs = 0, 0.0
     for x in keys_list:
         s = np.ascontiguousarray(x[:CPU_SAMPLE_N])
@@ -207,6 +209,9 @@ def main():
     ap.add_argument("--model", default="pcf", choices=["pcf", "spline"],
                     help="CDF model of the plain workload: the PCF of Sec. 3.3 (default) "
                          "or the spline of App. A.5 (Spline Learned Sort)")
+    ap.add_argument("--range", default="array", choices=["array", "sample"],
+                    help="range the bins span in the plain workload: the (sub)array's "
+                         "(Sec. 3.3, default) or the alpha samples' (one pass fewer per level)")
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "small", "zipf", "batched", "serve", "dupinject",
                              "failsweep"],
@@ -241,8 +246,8 @@ def main():
     ins = [torch.from_numpy(x).to(dev) for x in host_keys]
     outs = [torch.empty_like(t) for t in ins]
     ctx = pcfsort.Context(local)
-    if args.model != "pcf":
-        ctx.set_policy(model=args.model)
+    if args.model != "pcf" or args.range != "array":
+        ctx.set_policy(model=args.model, range_mode=args.range)
     ctx.reserve(n)
     # the sorts' own stream (created non-blocking by torch): on the legacy
     # default stream every launch would also order against other streams
@@ -338,7 +343,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": (WORKLOAD if n == N else WORKLOAD.replace("10^8", str(n)))
                    .replace("plain PCF sort", "plain PCF sort" if args.model == "pcf"
-                            else "Spline Learned Sort (App. A.5)"),
+                            else "Spline Learned Sort (App. A.5)")
+                   + ("" if args.range == "array" else ", bins over the samples' range"),
                    "n_per_array": n, "arrays_per_step": 4,
                    "l2": "inputs larger than L2 (800 MB per array, L2 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -359,7 +365,7 @@ def main():
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, total, secs = cpu_oracle_gkeys(host_keys, args.model)
+        v, total, secs = cpu_oracle_gkeys(host_keys, args.model, args.range)
         line["cpu_baseline"] = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
                                 "sample": "first %d keys of each of the 4 arrays (%d keys, %.1f s)"
                                           % (CPU_SAMPLE_N, total, secs)}

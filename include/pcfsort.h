@@ -66,16 +66,24 @@ typedef enum {
  * the order of operations stated in the library's design notes. */
 typedef enum { PCF_MODEL_PCF = 0, PCF_MODEL_SPLINE = 1 } pcf_model;
 
+/* Range the bins span in every bucketing step: the (sub)array's own minimum
+ * and maximum (Sec. 3.3: one full pass per step), or the alpha sampled keys'
+ * (no full pass; keys outside that range take the end bins; where the
+ * samples are all equal or their range is degenerate, the array's range is
+ * used).  The output is the same either way. */
+typedef enum { PCF_RANGE_ARRAY = 0, PCF_RANGE_SAMPLE = 1 } pcf_range;
+
 /* Parameters of Algorithm 1: alpha = floor(n^(a_num/den)), beta = ...(b_num),
  * gamma = ...(c_num), delta = ...(d_num), recomputed for every (sub)array
- * from its own n; tau is the small-input threshold; model a pcf_model.
- * Supported: den in 1..4, 1 <= a_num, b_num, c_num <= den, 1 <= d_num < den
- * (0 < d < 1, as Lemma nlogn requires), 16 <= tau <= 65535.
- * Default: {3,3,3,3,4,PCF_MODEL_PCF,100}. */
+ * from its own n; tau is the small-input threshold; model a pcf_model;
+ * range_mode a pcf_range.  Supported: den in 1..4, 1 <= a_num, b_num, c_num
+ * <= den, 1 <= d_num < den (0 < d < 1, as Lemma nlogn requires),
+ * 16 <= tau <= 65535.  Default: {3,3,3,3,4,PCF_MODEL_PCF,100,PCF_RANGE_ARRAY}. */
 typedef struct {
   uint32_t a_num, b_num, c_num, d_num, den;
   uint32_t model;
   uint64_t tau;
+  uint32_t range_mode;
 } pcf_policy;
 
 /* Implementation knobs.  They change speed only, never the result or the

@@ -91,10 +91,17 @@ PCF_HD uint64_t root_floor(uint64_t n, uint32_t p, uint32_t q) {
 // linear spline through the same counts (Spline Learned Sort, App. A.5).
 enum : uint32_t { MODEL_PCF = 0, MODEL_SPLINE = 1 };
 
+// Range the bins span: the (sub)array's min and max (Sec. 3.3), or the
+// alpha samples' (reading R14: one pass fewer per level; keys outside take
+// the end bins).
+enum : uint32_t { RANGE_ARRAY = 0, RANGE_SAMPLE = 1 };
+
 struct Policy {
   uint32_t a_num, b_num, c_num, d_num, den;
   uint32_t model;  // MODEL_*
   uint64_t tau;
+  uint32_t range_mode;  // RANGE_*
+  uint32_t pad;
 };
 
 struct Params {
@@ -149,6 +156,9 @@ struct BinModel {
   uint32_t spline;   // 1: the spline model (bucket ids from spline_bucket)
   uint32_t gamma;    // spline: the bucket count - 1 ...
   double g;          // ... and RN(gamma / alpha)
+  uint32_t clamp;    // 1: [lo, hi] is the samples' range, keys may lie outside (R14)
+  uint32_t pad;
+  uint64_t ord_lo, ord_hi;  // clamp: lo and hi in the total order
 };
 
 PCF_HD double as_f64(uint64_t b) {
@@ -241,6 +251,10 @@ PCF_HD int make_bin_model(uint32_t kt, uint64_t lo_bits, uint64_t hi_bits, uint3
   M->spline = 0;
   M->gamma = 0;
   M->g = 0.0;
+  M->clamp = 0;
+  M->pad = 0;
+  M->ord_lo = ord_of(lo_bits, kt);
+  M->ord_hi = ord_of(hi_bits, kt);
   double r;
   int32_t H;  // grid exponent: X(y) ~ y / 2^H
   if (kt == KEY_F64) {
@@ -323,6 +337,7 @@ PCF_HD uint32_t bin_exact_v(uint32_t kt, uint64_t lo_bits, double lo_d, double s
 #endif
 }
 PCF_HD uint32_t bin_exact(const BinModel& M, uint64_t xbits) {
+  if (M.clamp && ord_of(xbits, M.kt) < M.ord_lo) return 0u;  // below a sample range
   return bin_exact_v(M.kt, M.lo_bits, M.lo_d, M.s, M.beta, xbits);
 }
 
@@ -336,8 +351,31 @@ __device__ __noinline__ uint32_t bin_exact_call(uint32_t kt, uint64_t lo_bits, d
 }
 #endif
 
+// Keys outside a sample range (R14): below it bin 0; above it the exact
+// sequence (the fixed-point form covers [lo, hi] only).  Returns 1 and sets
+// *k when it decides, 2 when the exact sequence must, 0 otherwise.
+PCF_HD int bin_outside(const BinModel& M, uint64_t xbits, uint32_t* k) {
+  if (!M.clamp) return 0;
+  const uint64_t o = ord_of(xbits, M.kt);
+  if (o < M.ord_lo) {
+    *k = 0u;
+    return 1;
+  }
+  return o > M.ord_hi ? 2 : 0;
+}
+
 // Certified fast path, exact binary64 sequence when it cannot decide.
 PCF_HD uint32_t bin_of(const BinModel& M, uint64_t xbits) {
+  uint32_t ko = 0;
+  const int out = bin_outside(M, xbits, &ko);
+  if (out == 1) return ko;
+  if (out == 2) {
+#ifdef __CUDA_ARCH__
+    return bin_exact_call(M.kt, M.lo_bits, M.lo_d, M.s, M.beta, xbits);
+#else
+    return bin_exact(M, xbits);
+#endif
+  }
   const uint64_t V = mulhi64(bin_dn(M, xbits), M.sig);
   const uint32_t klo = shr_F(V > M.eu ? V - M.eu : 0ull, M.F), khi = shr_F(V + M.eu, M.F);
   if (klo >= M.beta) return M.beta;
@@ -352,6 +390,7 @@ PCF_HD uint32_t bin_of(const BinModel& M, uint64_t xbits) {
 // Fast path only: the bin when *amb stays false; callers that evaluate many
 // keys collect the undecided ones and run bin_exact afterwards, keeping the
 // out-of-line call out of their load/compute loops.
+// (a model over the array's range: every key lies in [lo, hi])
 PCF_HD uint32_t bin_fast(const BinModel& M, uint64_t xbits, bool& amb) {
   const uint64_t V = mulhi64(bin_dn(M, xbits), M.sig);
   const uint32_t klo = shr_F(V > M.eu ? V - M.eu : 0ull, M.F), khi = shr_F(V + M.eu, M.F);
@@ -359,7 +398,21 @@ PCF_HD uint32_t bin_fast(const BinModel& M, uint64_t xbits, bool& amb) {
   return klo >= M.beta ? M.beta : klo;
 }
 
+// The same for a model that may be over the samples' range (R14): keys
+// below it bin 0, keys above it undecided (the exact sequence decides).
+PCF_HD uint32_t bin_fast_clamped(const BinModel& M, uint64_t xbits, bool& amb) {
+  uint32_t ko = 0;
+  const int out = bin_outside(M, xbits, &ko);
+  if (out) {
+    amb = out == 2;
+    return ko;
+  }
+  return bin_fast(M, xbits, amb);
+}
+
 // Exact bin of a key (out of line on the device)
+// (callers reach it only for keys that bin_fast or bin_fast_clamped left
+// undecided, none of which lies below a sample range)
 PCF_HD uint32_t bin_exact_of(const BinModel& M, uint64_t xbits) {
 #ifdef __CUDA_ARCH__
   return bin_exact_call(M.kt, M.lo_bits, M.lo_d, M.s, M.beta, xbits);
@@ -370,6 +423,9 @@ PCF_HD uint32_t bin_exact_of(const BinModel& M, uint64_t xbits) {
 
 // Whether the fast path decides this key (for tests and counters).
 PCF_HD bool bin_fast_decides(const BinModel& M, uint64_t xbits) {
+  uint32_t ko = 0;
+  const int out = bin_outside(M, xbits, &ko);
+  if (out) return out == 1;
   const uint64_t V = mulhi64(bin_dn(M, xbits), M.sig);
   const uint32_t klo = shr_F(V > M.eu ? V - M.eu : 0ull, M.F), khi = shr_F(V + M.eu, M.F);
   return klo >= M.beta || klo == khi;
@@ -403,6 +459,10 @@ PCF_HD void spline_set(BinModel* M, uint32_t alpha, uint32_t gamma) {
 
 // bin of x and its position in it (the first two steps above)
 PCF_HD uint32_t spline_bin(const BinModel& M, uint64_t xbits, double* f) {
+  if (M.clamp && ord_of(xbits, M.kt) < M.ord_lo) {  // below a sample range
+    *f = 0.0;
+    return 0u;
+  }
   const double d = M.kt == KEY_F64 ? dsub(as_f64(xbits), M.lo_d) : u64_to_f64(xbits - M.lo_bits);
   const double p = dmul(d, M.s);
   if (!(p < (double)M.beta)) {

@@ -101,7 +101,7 @@ struct ParamCache {
 struct pcf_ctx {
   int device = 0;
   int num_sms = 0;
-  Policy policy{3, 3, 3, 3, 4, 0, 100};
+  Policy policy{3, 3, 3, 3, 4, MODEL_PCF, 100, RANGE_ARRAY, 0};
   pcf_tuning tuning{11, 14, 4096};
   std::string last_err;
   pcf_call_stats stats{};
@@ -225,6 +225,7 @@ bool policy_ok(const Policy& P) {
   if (P.d_num < 1 || P.d_num >= P.den) return false;
   if (P.tau < 16 || P.tau > 65535) return false;
   if (P.model != MODEL_PCF && P.model != MODEL_SPLINE) return false;
+  if (P.range_mode != RANGE_ARRAY && P.range_mode != RANGE_SAMPLE) return false;
   return true;
 }
 
@@ -618,6 +619,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   lc.pairs = pairs;
   lc.launches = &ctx->stats.kernel_launches;
   lc.model = ctx->policy.model;
+  lc.range_mode = ctx->policy.range_mode;
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
   CK(cudaMemsetAsync(lc.status, 0, 4, st));
@@ -766,27 +768,48 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     uint32_t* Xv = L.two_pass ? P2v : P1v;
     Seg* d_segs = L.dp.segs;
 
-    // range, model
-    CK(launch_range(lc, d_segs, S, L.dp.rb, L.n_range, src, first && kt == KEY_F64));
-    if (first && kt == KEY_F64) {
+    // range, model.  NaN keys (level 0, binary64) are flagged by the full
+    // range pass, or with a sample range by k_hist1 and the range pass of
+    // the segments that need one; either way before any output is written
+    const bool srange = lc.range_mode == RANGE_SAMPLE;
+    const bool check_nan = first && kt == KEY_F64;
+    auto nan_gate = [&]() -> pcf_status {
       CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
       CK(cudaStreamSynchronize(st));
       if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+      return launch_small();
+    };
+    if (srange) {
+      // the samples' range; the array's where it is equal or degenerate (R14)
+      CK(launch_sample_range(lc, d_segs, S, L.dp.k1, L.n_k1, src));
+      CK(launch_model(lc, d_segs, S, 1));
+      CK(launch_range(lc, d_segs, S, L.dp.rb, L.n_range, src, check_nan, SEG_NEEDRANGE));
+      CK(launch_model(lc, d_segs, S, 2));
+    } else {
+      CK(launch_range(lc, d_segs, S, L.dp.rb, L.n_range, src, check_nan));
+      if (first) {
+        const pcf_status r = check_nan ? nan_gate() : launch_small();
+        if (r != PCF_OK) return r;
+      }
+      CK(launch_model(lc, d_segs, S));
     }
-    if (first) {
-      pcf_status r = launch_small();
-      if (r != PCF_OK) return r;
-    }
-    CK(launch_model(lc, d_segs, S));
     tm.mark(0);
     // (sub)arrays with one value are final; degenerate ones join the
-    // fallback list, whose keys are taken from X
-    if (src != out_k)
-      CK(launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, src, out_k, src_v, out_v,
-                          1u << SEG_SINGLE));
-    if (src != X)
-      CK(launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, src, X, src_v, Xv,
-                          1u << SEG_DEGEN));
+    // fallback list, whose keys are taken from X (with a sample range on
+    // binary64 keys at level 0: after the NaN gate below, as they write
+    // the output)
+    auto copy_special = [&]() -> cudaError_t {
+      cudaError_t e = cudaSuccess;
+      if (src != out_k)
+        e = launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, src, out_k, src_v, out_v,
+                             1u << SEG_SINGLE);
+      if (!e && src != X)
+        e = launch_copy_segs(lc, d_segs, S, L.dp.rb, L.n_range, src, X, src_v, Xv,
+                             1u << SEG_DEGEN);
+      return e;
+    };
+    const bool late_gate = srange && first;
+    if (!late_gate) CK(copy_special());
     // lists
     const uint64_t max_items = std::max<uint64_t>(L.n_buckets, S) + 16;
     CK(ensure(ctx->leaf, max_items * sizeof(BRec)));
@@ -822,7 +845,13 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     CK(ensure(ctx->cmat1, L.cmat1 * 4));
     CK(cudaMemsetAsync(ctx->cmat1.p, 0, L.cmat1 * 4, st));
     CK(launch_hist1(lc, d_segs, S, L.dp.t1, L.n_t1, tile_keys, src, as<uint32_t>(ctx->tpool),
-                    as<uint32_t>(ctx->cmat1), L.dmax1, as<uint32_t>(ctx->jbuf)));
+                    as<uint32_t>(ctx->cmat1), L.dmax1, as<uint32_t>(ctx->jbuf),
+                    srange && check_nan));
+    if (late_gate) {
+      const pcf_status r = check_nan ? nan_gate() : launch_small();
+      if (r != PCF_OK) return r;
+      CK(copy_special());
+    }
     CK(launch_scan(lc, as<uint32_t>(ctx->cmat1), L.cmat1, nullptr, as<uint64_t>(ctx->sw),
                    tile_counter, scan_withhold, spin_limit, nullptr));
     tm.mark(2);
@@ -1008,7 +1037,7 @@ pcf_status pcf_ctx_destroy(pcf_ctx* ctx) {
 
 pcf_status pcf_ctx_set_policy(pcf_ctx* ctx, const pcf_policy* p) {
   if (!ctx || !p) return PCF_ERR_INVALID_ARG;
-  Policy P{p->a_num, p->b_num, p->c_num, p->d_num, p->den, p->model, p->tau};
+  Policy P{p->a_num, p->b_num, p->c_num, p->d_num, p->den, p->model, p->tau, p->range_mode, 0};
   if (!policy_ok(P)) return PCF_ERR_INVALID_ARG;
   ctx->policy = P;
   return PCF_OK;
@@ -1230,6 +1259,7 @@ pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_
   lc.pairs = false;
   lc.launches = &ctx->stats.kernel_launches;
   lc.model = ctx->policy.model;
+  lc.range_mode = ctx->policy.range_mode;
   ctx->stats = pcf_call_stats{};
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
@@ -1257,14 +1287,23 @@ pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_
   const DevPlan dp = dev_plan(ctx->segs.p, PL);
   const uint32_t tile_keys = 1u << ctx->tuning.tile_log2;
   const uint64_t spin_limit = kSpinLimit;
-  CK(launch_range(lc, dp.segs, S, dp.rb, pl.range_base[S], (const uint64_t*)d_keys,
-                  kt == PCF_KEY_F64));
-  if (kt == PCF_KEY_F64) {
-    CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
-    CK(cudaStreamSynchronize(st));
-    if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+  const bool srange = lc.range_mode == RANGE_SAMPLE;
+  if (srange) {
+    CK(launch_sample_range(lc, dp.segs, S, dp.k1, pl.k1_base[S], (const uint64_t*)d_keys));
+    CK(launch_model(lc, dp.segs, S, 1));
+    CK(launch_range(lc, dp.segs, S, dp.rb, pl.range_base[S], (const uint64_t*)d_keys,
+                    kt == PCF_KEY_F64, SEG_NEEDRANGE));
+    CK(launch_model(lc, dp.segs, S, 2));
+  } else {
+    CK(launch_range(lc, dp.segs, S, dp.rb, pl.range_base[S], (const uint64_t*)d_keys,
+                    kt == PCF_KEY_F64));
+    if (kt == PCF_KEY_F64) {
+      CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
+      CK(cudaStreamSynchronize(st));
+      if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+    }
+    CK(launch_model(lc, dp.segs, S));
   }
-  CK(launch_model(lc, dp.segs, S));
   CK(ensure(ctx->tpool, pl.tpool * 4));
   CK(cudaMemsetAsync(ctx->tpool.p, 0, pl.tpool * 4, st));
   const uint64_t scan_max = std::max(pl.cmat1, pl.tpool);
@@ -1279,7 +1318,7 @@ pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_
   CK(ensure(ctx->jbuf, n_total * 4));
   CK(launch_hist1(lc, dp.segs, S, dp.t1, pl.tile1_base[S], tile_keys, (const uint64_t*)d_keys,
                   as<uint32_t>(ctx->tpool), as<uint32_t>(ctx->cmat1), pl.dmax1,
-                  as<uint32_t>(ctx->jbuf)));
+                  as<uint32_t>(ctx->jbuf), srange && kt == PCF_KEY_F64));
   const size_t n_counts = (size_t)S * (gamma + 1);
   uint32_t* counts = d_counts;
   if (!counts) {

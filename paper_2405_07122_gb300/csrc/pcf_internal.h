@@ -15,7 +15,9 @@ enum : uint32_t {
   STATUS_INTERNAL = 4u,  // an internal capacity check failed
 };
 
-enum : uint32_t { SEG_BUCKET = 0, SEG_SINGLE = 1, SEG_DEGEN = 2 };
+// SEG_NEEDRANGE: the samples' range (R14) was equal or degenerate; the
+// array's own range decides
+enum : uint32_t { SEG_BUCKET = 0, SEG_SINGLE = 1, SEG_DEGEN = 2, SEG_NEEDRANGE = 3 };
 
 // One (sub)array bucketed by a global level (Algorithm 1, one call of
 // Learned-Sort with its own model).  Host-planned fields first.
@@ -133,6 +135,7 @@ struct LaunchCfg {
   cudaStream_t stream;
   uint32_t kt;
   uint32_t model = MODEL_PCF;  // the policy's CDF model
+  uint32_t range_mode = RANGE_ARRAY;  // ... and range
   bool pairs;
   uint32_t* status;  // device status word
   uint64_t* launches;  // host counter of kernel launches (may be null)
@@ -156,18 +159,28 @@ constexpr uint32_t kScanTile = 4096;    // entries per decoupled-lookback tile
 constexpr uint32_t kMergeTile = 2048;   // keys per block-sorted run
 constexpr uint32_t kMaxDigitBits = 12;
 
+// only_status: reduce only the segments in that status (~0u: all)
 cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* range_base,
-                         uint32_t n_tiles, const uint64_t* keys, bool check_nan);
-cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S);
+                         uint32_t n_tiles, const uint64_t* keys, bool check_nan,
+                         uint32_t only_status = ~0u);
+// pass 0: the range reduced by launch_range; 1: the samples' range (R14),
+// SEG_NEEDRANGE where it is equal or degenerate; 2: those segments again,
+// from their array range
+cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t pass = 0);
+// min and max of every segment's alpha samples into its range fields
+cudaError_t launch_sample_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
+                                uint32_t n_ctas, const uint64_t* keys);
 cudaError_t launch_sample(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
                           uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool);
 // cumulative counts b (inclusive scan of the whole pool) + per-segment bases
 cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tpool,
                          uint64_t pool_n, uint64_t* status_words, uint32_t* tile_counter,
                          uint64_t spin_limit);
+// check_nan: flag NaN keys (a sample range has no full range pass to do it)
 cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
                          uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
-                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout);
+                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout,
+                         bool check_nan = false);
 // Level-0 bucket sizes of every segment (ids from k_hist1's jbuf): counts
 // (zeroed by the caller) at bucket_base, and out_max[s] = max_j |c_j| (n
 // for a segment that was not bucketed).

@@ -46,9 +46,11 @@ __device__ __forceinline__ uint64_t ld_nc(const uint64_t* p) { return __ldg(p); 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_range(Seg* segs, uint32_t S, const uint32_t* range_base,
                                                const uint64_t* __restrict__ keys, uint32_t kt,
-                                               int check_nan, uint32_t* status) {
+                                               int check_nan, uint32_t* status,
+                                               uint32_t only_status) {
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(range_base, S + 1, t) - 1;
+  if (only_status != ~0u && segs[s].status != only_status) return;
   const uint64_t off = segs[s].off, n = segs[s].n;
   const uint64_t base = off + (uint64_t)(t - range_base[s]) * kRangeTile;
   const uint64_t end = min(off + n, base + kRangeTile);
@@ -100,17 +102,58 @@ __global__ void __launch_bounds__(256) k_range(Seg* segs, uint32_t S, const uint
 // ---------------------------------------------------------------------------
 // k_model: Alg. 1's early exits and the bin constants
 // ---------------------------------------------------------------------------
-__global__ void k_model(Seg* segs, uint32_t S, uint32_t kt, uint32_t model) {
+__global__ void k_model(Seg* segs, uint32_t S, uint32_t kt, uint32_t model, uint32_t pass) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   Seg& g = segs[s];
-  if (g.ord_lo == g.ord_hi) {  // one distinct value: already sorted
-    g.status = SEG_SINGLE;
-    return;
-  }
+  if (pass == 2 && g.status != SEG_NEEDRANGE) return;
   const uint64_t lo = bits_of_ord(g.ord_lo, kt), hi = bits_of_ord(g.ord_hi, kt);
-  g.status = make_bin_model(kt, lo, hi, g.beta, &g.bm) ? SEG_DEGEN : SEG_BUCKET;
+  if (pass == 1) {
+    // the samples' range (R14); equal or degenerate: the array's decides
+    if (g.ord_lo == g.ord_hi || make_bin_model(kt, lo, hi, g.beta, &g.bm)) {
+      g.status = SEG_NEEDRANGE;
+      g.ord_lo = ~0ull;
+      g.ord_hi = 0ull;
+      return;
+    }
+    g.bm.clamp = 1;
+    g.status = SEG_BUCKET;
+  } else {
+    if (g.ord_lo == g.ord_hi) {  // one distinct value: already sorted
+      g.status = SEG_SINGLE;
+      return;
+    }
+    g.status = make_bin_model(kt, lo, hi, g.beta, &g.bm) ? SEG_DEGEN : SEG_BUCKET;
+  }
   if (g.status == SEG_BUCKET && model == MODEL_SPLINE) spline_set(&g.bm, g.alpha, g.gamma);
+}
+
+// min / max of each segment's alpha samples (R2's positions), per CTA of
+// kSamplesPerCta samples, into the segment's range (the samples' range, R14)
+__global__ void __launch_bounds__(256) k_sample_range(Seg* segs, uint32_t S,
+                                                      const uint32_t* k1_base,
+                                                      const uint64_t* __restrict__ keys,
+                                                      uint32_t kt) {
+  const uint32_t c = blockIdx.x;
+  const uint32_t s = upper_bound_dev(k1_base, S + 1, c) - 1;
+  Seg& g = segs[s];
+  const uint32_t cta = c - k1_base[s];
+  const uint64_t st = sample_state(g.seed, g.depth, g.start, g.n);
+  const uint32_t j0 = cta * kSamplesPerCta, j1 = min(g.alpha, j0 + kSamplesPerCta);
+  uint64_t mn = ~0ull, mx = 0ull;
+  for (uint32_t j = j0 + threadIdx.x; j < j1; j += 256) {
+    const uint64_t o = ord_of(ld_nc(keys + g.off + sample_index(st, j, g.n)), kt);
+    mn = min(mn, o);
+    mx = max(mx, o);
+  }
+  for (int d = 16; d; d >>= 1) {
+    mn = min(mn, (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d));
+    mx = max(mx, (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d));
+  }
+  if ((threadIdx.x & 31) == 0 && mn <= mx) {
+    atomicMin((unsigned long long*)&g.ord_lo, (unsigned long long)mn);
+    atomicMax((unsigned long long*)&g.ord_hi, (unsigned long long)mx);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -208,15 +251,70 @@ __device__ __forceinline__ void hist_inc(uint32_t* hist, uint32_t d, bool valid,
   else if (valid) atomicAdd(&hist[d], 1u);
 }
 
+// k_hist1's PCF loop: the bucket id of every key of [base, end) into jout
+// and the histogram of its high digit; CLAMP: the model spans the samples'
+// range (R14).  Returns whether a NaN key was seen (check_nan).
+template <bool CLAMP>
+__device__ __forceinline__ bool hist1_pcf(const BinModel& bm, const Seg& g, uint64_t base,
+                                          uint64_t end, const uint64_t* __restrict__ keys,
+                                          const uint32_t* __restrict__ tpool, uint32_t* hist,
+                                          uint32_t* __restrict__ jout, uint32_t b2, bool agg,
+                                          int check_nan) {
+  bool nan = false;
+  {
+    const uint32_t* T = tpool + g.T_off;
+    const uint32_t tb = g.tbase, al = g.alpha, ga = g.gamma;
+    constexpr int U = 8;
+    for (uint64_t i0 = base; i0 < end; i0 += 256 * U) {
+      uint64_t x[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
+        x[u] = i < end ? ld_nc(keys + i) : 0ull;
+      }
+      if (check_nan) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) nan |= is_nan_bits(x[u]);
+      }
+      uint32_t bn[U], amb = 0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        bool a;
+        bn[u] = CLAMP ? bin_fast_clamped(bm, x[u], a) : bin_fast(bm, x[u], a);
+        amb |= (uint32_t)a << u;
+      }
+      if (amb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
+      }
+      uint32_t tv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) tv[u] = __ldg(T + bn[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
+        const bool v = i < end;
+        const uint32_t j = v ? bucket_of_count(tv[u] - tb, al, ga) : 0u;
+        if (v) jout[i] = j;
+        hist_inc(hist, j >> b2, v, agg);
+      }
+    }
+  }
+  return nan;
+}
+
 __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
                                                const uint32_t* tile_base, uint32_t tile_keys,
                                                const uint64_t* __restrict__ keys, uint32_t kt,
                                                const uint32_t* __restrict__ tpool,
-                                               uint32_t* cmat, uint32_t* __restrict__ jout) {
+                                               uint32_t* cmat, uint32_t* __restrict__ jout,
+                                               int check_nan, uint32_t* status) {
   extern __shared__ uint32_t hist[];
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
   __shared__ BinModel bm;
+  bool nan = false;
   const Seg& g = segs[s];
   const uint32_t tt = t - tile_base[s];
   const uint32_t D = 1u << g.b1, b2 = g.b2;
@@ -241,52 +339,25 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
       uint32_t j = 0;
       if (v) {
         double f;
-        const uint32_t k = spline_bin(bm, ld_nc(keys + i), &f);
+        const uint64_t x = ld_nc(keys + i);
+        if (check_nan) nan |= is_nan_bits(x);
+        const uint32_t k = spline_bin(bm, x, &f);
         const uint32_t bk = __ldg(T + k) - tb, bkm1 = k ? __ldg(T + k - 1) - tb : 0u;
         j = spline_bucket(bm, f, bkm1, bk);
         jout[i] = j;
       }
       hist_inc(hist, j >> b2, v, agg);
     }
+  } else if (bm.clamp) {
+    nan |= hist1_pcf<true>(bm, g, base, end, keys, tpool, hist, jout, b2, agg, check_nan);
   } else {
-    const uint32_t* T = tpool + g.T_off;
-    const uint32_t tb = g.tbase, al = g.alpha, ga = g.gamma;
-    constexpr int U = 8;
-    for (uint64_t i0 = base; i0 < end; i0 += 256 * U) {
-      uint64_t x[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
-        x[u] = i < end ? ld_nc(keys + i) : 0ull;
-      }
-      uint32_t bn[U], amb = 0;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        bool a;
-        bn[u] = bin_fast(bm, x[u], a);
-        amb |= (uint32_t)a << u;
-      }
-      if (amb) {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
-      }
-      uint32_t tv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) tv[u] = __ldg(T + bn[u]);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
-        const bool v = i < end;
-        const uint32_t j = v ? bucket_of_count(tv[u] - tb, al, ga) : 0u;
-        if (v) jout[i] = j;
-        hist_inc(hist, j >> b2, v, agg);
-      }
-    }
+    nan |= hist1_pcf<false>(bm, g, base, end, keys, tpool, hist, jout, b2, agg, check_nan);
   }
+  if (check_nan && __any_sync(~0u, nan) && (threadIdx.x & 31) == 0) atomicOr(status, STATUS_NAN);
   __syncthreads();
   for (uint32_t d = threadIdx.x; d < D; d += 256) cmat[g.cbase1 + (uint64_t)d * g.tiles1 + tt] = hist[d];
 }
+
 
 // ---------------------------------------------------------------------------
 // k_scan: exclusive prefix sum of u32 data[0..n) in place, single pass with
@@ -1032,17 +1103,26 @@ __global__ void __launch_bounds__(256) k_copy_segs(const Seg* segs, uint32_t S,
 static inline uint32_t cdiv(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
 cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* range_base,
-                         uint32_t n_tiles, const uint64_t* keys, bool check_nan) {
+                         uint32_t n_tiles, const uint64_t* keys, bool check_nan,
+                         uint32_t only_status) {
   if (!n_tiles) return cudaSuccess;
   k_range<<<n_tiles, 256, 0, c.stream>>>(segs, S, range_base, keys, c.kt, check_nan ? 1 : 0,
-                                         c.status);
+                                         c.status, only_status);
   count_launch(c);
   return cudaGetLastError();
 }
 
-cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S) {
+cudaError_t launch_sample_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
+                                uint32_t n_ctas, const uint64_t* keys) {
+  if (!n_ctas) return cudaSuccess;
+  k_sample_range<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t pass) {
   if (!S) return cudaSuccess;
-  k_model<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, c.kt, c.model);
+  k_model<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, c.kt, c.model, pass);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1068,10 +1148,11 @@ cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tp
 
 cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const uint32_t* tile_base,
                          uint32_t n_tiles, uint32_t tile_keys, const uint64_t* keys,
-                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout) {
+                         const uint32_t* tpool, uint32_t* cmat, uint32_t dmax, uint32_t* jout,
+                         bool check_nan) {
   if (!n_tiles) return cudaSuccess;
   k_hist1<<<n_tiles, 256, dmax * 4, c.stream>>>(segs, S, tile_base, tile_keys, keys, c.kt, tpool,
-                                                cmat, jout);
+                                                cmat, jout, check_nan ? 1 : 0, c.status);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -293,49 +293,87 @@ __device__ void std_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) 
 // are finished here (ranked) when small, else pushed.  Returns false when
 // the per-warp stack would overflow.
 // ---------------------------------------------------------------------------
-template <bool PAIRS, bool SPLINE>
+template <bool PAIRS, bool SPLINE, bool SRANGE>
 __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                            uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
                            uint32_t& top, uint32_t lane, bool root, uint64_t rmn, uint64_t rmx) {
   const uint32_t o = it.o, n = it.n;
-  // range (a root call's per-lane range was taken while its keys loaded)
-  uint64_t mn = rmn, mx = rmx;
-  if (!root) {
-    mn = ~0ull;
-    mx = 0ull;
-    for (uint32_t i = lane; i < n; i += 32) {
-      const uint64_t v = w.A[o + i];
-      mn = v < mn ? v : mn;
-      mx = v > mx ? v : mx;
+  constexpr bool spline = SPLINE;
+  // alpha..delta and the sample stream: with the array's range taken after
+  // the range pass (fewer registers live across it)
+  ushort4 q = make_ushort4(0, 0, 0, 0);
+  uint64_t state = 0;
+  if constexpr (SRANGE) {
+    q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
+    state = sample_state(seed, it.depth, it.start, n);
+  }
+  // the samples' range (R14) when the policy asks for it and it is usable
+  bool have_model = false;
+  if constexpr (SRANGE) {
+    const uint32_t alpha = q.x, beta = q.y, gamma = q.z;
+    uint64_t smn = ~0ull, smx = 0ull;
+    for (uint32_t s = lane; s < alpha; s += 32) {
+      const uint64_t v = w.A[o + (uint32_t)sample_index(state, s, n)];
+      smn = v < smn ? v : smn;
+      smx = v > smx ? v : smx;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+      const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)smn, d);
+      const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)smx, d);
+      smn = a < smn ? a : smn;
+      smx = b > smx ? b : smx;
+    }
+    int ok = 0;
+    if (lane == 0 && smn != smx &&
+        !make_bin_model(kt, bits_of_ord(smn, kt), bits_of_ord(smx, kt), beta, w.bm)) {
+      w.bm->clamp = 1;
+      if (spline) spline_set(w.bm, alpha, gamma);
+      ok = 1;
+    }
+    have_model = __shfl_sync(~0u, ok, 0) != 0;
+  }
+  if (!have_model) {
+    // range (a root call's per-lane range was taken while its keys loaded)
+    uint64_t mn = rmn, mx = rmx;
+    if (!root) {
+      mn = ~0ull;
+      mx = 0ull;
+      for (uint32_t i = lane; i < n; i += 32) {
+        const uint64_t v = w.A[o + i];
+        mn = v < mn ? v : mn;
+        mx = v > mx ? v : mx;
+      }
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+      const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+      const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+      mn = a < mn ? a : mn;
+      mx = b > mx ? b : mx;
+    }
+    if (mn == mx) return true;  // one value: sorted
+    if constexpr (!SRANGE) {
+      q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
+      state = sample_state(seed, it.depth, it.start, n);
+    }
+    int degen = 0;
+    if (lane == 0) {
+      degen = make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), q.y, w.bm);
+      if (!degen && spline) spline_set(w.bm, q.x, q.z);
+    }
+    degen = __shfl_sync(~0u, degen, 0);
+    if (degen) {  // R5: a degenerate range goes to Standard-Sort
+      std_sort<PAIRS>(w, o, n, lane);
+      return true;
     }
   }
-#pragma unroll
-  for (int d = 16; d; d >>= 1) {
-    const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
-    const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
-    mn = a < mn ? a : mn;
-    mx = b > mx ? b : mx;
-  }
-  if (mn == mx) return true;  // one value: sorted
-  const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
   const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
-  constexpr bool spline = SPLINE;
-  int degen = 0;
-  if (lane == 0) {
-    degen = make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
-    if (!degen && spline) spline_set(w.bm, alpha, gamma);
-  }
-  degen = __shfl_sync(~0u, degen, 0);
-  if (degen) {  // R5: a degenerate range goes to Standard-Sort
-    std_sort<PAIRS>(w, o, n, lane);
-    return true;
-  }
   for (uint32_t k = lane; k <= beta; k += 32) w.tab[k] = 0;
   for (uint32_t k = lane; k <= gamma; k += 32) w.cnt[k] = 0;
   __syncwarp();
   const BinModel bm = *w.bm;
   // training: alpha samples with replacement, counted per bin
-  const uint64_t state = sample_state(seed, it.depth, it.start, n);
   for (uint32_t s = lane; s < alpha; s += 32) {
     const uint32_t idx = (uint32_t)sample_index(state, s, n);
     const uint64_t x = bits_of_ord(w.A[o + idx], kt);
@@ -378,7 +416,7 @@ __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, 
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       bool a;
-      bn[u] = bin_fast(bm, x[u], a);
+      bn[u] = SRANGE ? bin_fast_clamped(bm, x[u], a) : bin_fast(bm, x[u], a);
       amb |= (uint32_t)a << u;
     }
     if (amb) {
@@ -510,7 +548,7 @@ __global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t 
   }
 }
 
-template <bool PAIRS, bool SPLINE>
+template <bool PAIRS, bool SPLINE, bool SRANGE>
 __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restrict__ br,
                                                            const uint32_t* __restrict__ list,
                                                            const uint32_t* __restrict__ count,
@@ -559,7 +597,9 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
         const Item it = w.stk[top];
         __syncwarp();
         if (it.std) std_sort<PAIRS>(w, it.o, it.n, lane);
-        else ok = learn_step<PAIRS, SPLINE>(w, geo, it, r.seed, kt, P, ptab, top, lane, root, rmn, rmx);
+        else
+          ok = learn_step<PAIRS, SPLINE, SRANGE>(w, geo, it, r.seed, kt, P, ptab, top, lane, root,
+                                                 rmn, rmx);
         root = false;
       }
     }
@@ -588,8 +628,9 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
 template <uint32_t NT>
 struct CtaShared {
   uint64_t mn[NT / 32], mx[NT / 32];
+  uint64_t smn[NT / 32], smx[NT / 32];  // the samples' range (R14)
   uint32_t wsum[NT / 32];
-  uint32_t top, flag, ovf;
+  uint32_t top, flag, ovf, sok;
 };
 
 // Scan of src[0..m) into dst by the CTA (each thread a contiguous run, one
@@ -629,56 +670,112 @@ __device__ __forceinline__ void cta_scan(const uint32_t* src, uint32_t* dst, uin
 constexpr uint32_t kSampRegs = 3;
 
 // root: the range was reduced into sh.mn / sh.mx while the keys were loaded
-template <uint32_t NT, bool SPLINE>
+template <uint32_t NT, bool SPLINE, bool SRANGE>
 __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                                uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
                                CtaShared<NT>& sh, bool root) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t o = it.o, n = it.n;
-  uint64_t mn = ~0ull, mx = 0ull;
-  if (!root) {
-    for (uint32_t i = tid; i < n; i += NT) {
-      const uint64_t v = w.A[o + i];
-      mn = v < mn ? v : mn;
-      mx = v > mx ? v : mx;
-    }
-#pragma unroll
-    for (int d = 16; d; d >>= 1) {
-      const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
-      const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
-      mn = a < mn ? a : mn;
-      mx = b > mx ? b : mx;
-    }
-    if (lane == 0) {
-      sh.mn[wid] = mn;
-      sh.mx[wid] = mx;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (uint32_t k = 0; k < NT / 32; ++k) {
-    mn = sh.mn[k] < mn ? sh.mn[k] : mn;
-    mx = sh.mx[k] > mx ? sh.mx[k] : mx;
-  }
-  if (mn == mx) return;  // one value: sorted
   const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
   const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
   constexpr bool spline = SPLINE;
-  if (tid == 0) {
-    sh.flag = (uint32_t)make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
-    if (!sh.flag && spline) spline_set(w.bm, alpha, gamma);
+  // the sample positions and keys do not depend on the model: with the
+  // array's range they are drawn while thread 0 builds it, with the
+  // samples' range first
+  const uint64_t state = sample_state(seed, it.depth, it.start, n);
+  uint64_t sx[kSampRegs];
+  bool drawn = false;
+  auto draw = [&]() {
+#pragma unroll
+    for (uint32_t u = 0; u < kSampRegs; ++u) {
+      const uint32_t s = tid + u * NT;
+      sx[u] = s < alpha ? bits_of_ord(w.A[o + (uint32_t)sample_index(state, s, n)], kt) : 0ull;
+    }
+    drawn = true;
+  };
+  // the samples' range (R14) when the policy asks for it and it is usable
+  bool have_model = false;
+  if constexpr (SRANGE) {
+    draw();
+    uint64_t smn = ~0ull, smx = 0ull;
+#pragma unroll
+    for (uint32_t u = 0; u < kSampRegs; ++u) {
+      if (tid + u * NT < alpha) {
+        const uint64_t v = ord_of(sx[u], kt);
+        smn = v < smn ? v : smn;
+        smx = v > smx ? v : smx;
+      }
+    }
+    for (uint32_t s = tid + kSampRegs * NT; s < alpha; s += NT) {
+      const uint64_t v = w.A[o + (uint32_t)sample_index(state, s, n)];
+      smn = v < smn ? v : smn;
+      smx = v > smx ? v : smx;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+      const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)smn, d);
+      const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)smx, d);
+      smn = a < smn ? a : smn;
+      smx = b > smx ? b : smx;
+    }
+    if (lane == 0) {
+      sh.smn[wid] = smn;
+      sh.smx[wid] = smx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (uint32_t k = 0; k < NT / 32; ++k) {
+        smn = sh.smn[k] < smn ? sh.smn[k] : smn;
+        smx = sh.smx[k] > smx ? sh.smx[k] : smx;
+      }
+      sh.sok = smn != smx &&
+               !make_bin_model(kt, bits_of_ord(smn, kt), bits_of_ord(smx, kt), beta, w.bm);
+      if (sh.sok) {
+        w.bm->clamp = 1;
+        if (spline) spline_set(w.bm, alpha, gamma);
+      }
+    }
+    __syncthreads();
+    have_model = sh.sok != 0;
+  }
+  if (!have_model) {
+    uint64_t mn = ~0ull, mx = 0ull;
+    if (!root) {
+      for (uint32_t i = tid; i < n; i += NT) {
+        const uint64_t v = w.A[o + i];
+        mn = v < mn ? v : mn;
+        mx = v > mx ? v : mx;
+      }
+#pragma unroll
+      for (int d = 16; d; d >>= 1) {
+        const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+        const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+      }
+      if (lane == 0) {
+        sh.mn[wid] = mn;
+        sh.mx[wid] = mx;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < NT / 32; ++k) {
+      mn = sh.mn[k] < mn ? sh.mn[k] : mn;
+      mx = sh.mx[k] > mx ? sh.mx[k] : mx;
+    }
+    if (mn == mx) return;  // one value: sorted
+    if (tid == 0) {
+      sh.flag = (uint32_t)make_bin_model(kt, bits_of_ord(mn, kt), bits_of_ord(mx, kt), beta, w.bm);
+      if (!sh.flag && spline) spline_set(w.bm, alpha, gamma);
+    }
+  } else if (tid == 0) {
+    sh.flag = 0;
   }
   for (uint32_t k = tid; k <= beta; k += NT) w.tab[k] = 0;
   for (uint32_t k = tid; k <= gamma; k += NT) w.cnt[k] = 0;
-  // the sample positions and keys do not depend on the model: draw them
-  // while thread 0 builds it
-  const uint64_t state = sample_state(seed, it.depth, it.start, n);
-  uint64_t sx[kSampRegs];
-#pragma unroll
-  for (uint32_t u = 0; u < kSampRegs; ++u) {
-    const uint32_t s = tid + u * NT;
-    sx[u] = s < alpha ? bits_of_ord(w.A[o + (uint32_t)sample_index(state, s, n)], kt) : 0ull;
-  }
+  if (!drawn) draw();
   __syncthreads();
   if (sh.flag) {  // R5: a degenerate range goes to Standard-Sort
     if (wid == 0) std_sort<false>(w, o, n, lane);
@@ -724,7 +821,7 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       bool a;
-      bn[u] = bin_fast(bm, x[u], a);
+      bn[u] = SRANGE ? bin_fast_clamped(bm, x[u], a) : bin_fast(bm, x[u], a);
       amb |= (uint32_t)a << u;
     }
     if (amb) {
@@ -779,7 +876,7 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
   }
 }
 
-template <uint32_t NT, bool SPLINE>
+template <uint32_t NT, bool SPLINE, bool SRANGE>
 __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(const BRec* __restrict__ br,
                                                         const uint32_t* __restrict__ list,
                                                         const uint32_t* __restrict__ count,
@@ -838,8 +935,8 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
         __syncthreads();
         if (wid == 0) std_sort<false>(w, it.o, it.n, lane);
       } else {
-        learn_step_cta<NT, SPLINE>(w, geo, it, r.seed, kt, P, ptab, sh,
-                                   top == 1 && it.o == 0 && it.n == n);
+        learn_step_cta<NT, SPLINE, SRANGE>(w, geo, it, r.seed, kt, P, ptab, sh,
+                                           top == 1 && it.o == 0 && it.n == n);
       }
       __syncthreads();
     }
@@ -887,16 +984,17 @@ uint32_t onchip_classes(uint32_t leaf_cap) {
 }
 
 // one CTA of NT threads per bucket of the class whose slices are g.bytes
-template <uint32_t NT, bool SPLINE>
+template <uint32_t NT, bool SPLINE, bool SRANGE>
 static cudaError_t launch_cta_model(const LaunchCfg& c, const BRec* br, const uint32_t* list,
                                     const uint32_t* count, const OnchipGeo& g, const uint64_t* X,
                                     uint64_t* out, const Policy& P, const uint16_t* ptab) {
   constexpr uint32_t kMaxPerSm = NT <= 64 ? 16u : 512u / NT;
   const uint32_t per = max(1u, min(kMaxPerSm, (uint32_t)((227u * 1024u) / (g.bytes + 1024u))));
-  cudaError_t e = allow_max_smem((const void*)k_onchip_cta<NT, SPLINE>);
+  cudaError_t e = allow_max_smem((const void*)k_onchip_cta<NT, SPLINE, SRANGE>);
   if (e) return e;
-  k_onchip_cta<NT, SPLINE><<<(uint32_t)num_sms_of_current_device() * per, NT, g.bytes,
-                             c.stream>>>(br, list, count, g, X, out, c.kt, P, ptab, c.status);
+  k_onchip_cta<NT, SPLINE, SRANGE><<<(uint32_t)num_sms_of_current_device() * per, NT, g.bytes,
+                                     c.stream>>>(br, list, count, g, X, out, c.kt, P, ptab,
+                                                 c.status);
   return cudaGetLastError();
 }
 
@@ -904,12 +1002,15 @@ template <uint32_t NT>
 static cudaError_t launch_cta_class(const LaunchCfg& c, const BRec* br, const uint32_t* list,
                                     const uint32_t* count, const OnchipGeo& g, const uint64_t* X,
                                     uint64_t* out, const Policy& P, const uint16_t* ptab) {
-  return P.model == MODEL_SPLINE
-             ? launch_cta_model<NT, true>(c, br, list, count, g, X, out, P, ptab)
-             : launch_cta_model<NT, false>(c, br, list, count, g, X, out, P, ptab);
+  const bool sr = P.range_mode == RANGE_SAMPLE;
+  if (P.model == MODEL_SPLINE)
+    return sr ? launch_cta_model<NT, true, true>(c, br, list, count, g, X, out, P, ptab)
+              : launch_cta_model<NT, true, false>(c, br, list, count, g, X, out, P, ptab);
+  return sr ? launch_cta_model<NT, false, true>(c, br, list, count, g, X, out, P, ptab)
+            : launch_cta_model<NT, false, false>(c, br, list, count, g, X, out, P, ptab);
 }
 
-template <bool PAIRS, bool SPLINE>
+template <bool PAIRS, bool SPLINE, bool SRANGE>
 static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const uint32_t* list,
                                      const uint32_t* count, const OnchipGeo& g, const uint64_t* X,
                                      const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
@@ -917,10 +1018,10 @@ static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const u
   const size_t sm = (size_t)kWarps * g.bytes;
   const uint32_t per_sm = max(1u, min(8u, (uint32_t)((227u * 1024u) / (sm + 1024u))));
   const uint32_t grid = (uint32_t)num_sms_of_current_device() * per_sm;
-  cudaError_t e = allow_max_smem((const void*)k_onchip<PAIRS, SPLINE>);
+  cudaError_t e = allow_max_smem((const void*)k_onchip<PAIRS, SPLINE, SRANGE>);
   if (e) return e;
-  k_onchip<PAIRS, SPLINE><<<grid, kWarps * 32, sm, c.stream>>>(br, list, count, g, X, Xv, out,
-                                                               out_v, c.kt, P, ptab, c.status);
+  k_onchip<PAIRS, SPLINE, SRANGE><<<grid, kWarps * 32, sm, c.stream>>>(
+      br, list, count, g, X, Xv, out, out_v, c.kt, P, ptab, c.status);
   return cudaGetLastError();
 }
 
@@ -961,17 +1062,19 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
       else e = launch_cta_class<512>(c, br, list, counts + cls, g, X, out, P, ptab);
       if (e) return e;
     } else {
-      const bool sp = P.model == MODEL_SPLINE;
-      if (c.pairs)
-        e = sp ? launch_warp_model<true, true>(c, br, list, counts + cls, g, X, Xv, out, out_v, P,
-                                               ptab)
-               : launch_warp_model<true, false>(c, br, list, counts + cls, g, X, Xv, out, out_v,
-                                                P, ptab);
-      else
-        e = sp ? launch_warp_model<false, true>(c, br, list, counts + cls, g, X, Xv, out, out_v,
-                                                P, ptab)
-               : launch_warp_model<false, false>(c, br, list, counts + cls, g, X, Xv, out, out_v,
-                                                 P, ptab);
+      const uint32_t v = (c.pairs ? 4u : 0u) | (P.model == MODEL_SPLINE ? 2u : 0u) |
+                         (P.range_mode == RANGE_SAMPLE ? 1u : 0u);
+      const uint32_t* cnt = counts + cls;
+      switch (v) {
+        case 0: e = launch_warp_model<false, false, false>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+        case 1: e = launch_warp_model<false, false, true>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+        case 2: e = launch_warp_model<false, true, false>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+        case 3: e = launch_warp_model<false, true, true>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+        case 4: e = launch_warp_model<true, false, false>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+        case 5: e = launch_warp_model<true, false, true>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+        case 6: e = launch_warp_model<true, true, false>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+        default: e = launch_warp_model<true, true, true>(c, br, list, cnt, g, X, Xv, out, out_v, P, ptab); break;
+      }
       if (e) return e;
     }
     count_launch(c);

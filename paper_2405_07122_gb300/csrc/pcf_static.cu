@@ -124,7 +124,7 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
   uint32_t* status = (uint32_t*)(base + kOffStatus);
   uint32_t* lists = (uint32_t*)(base + kOffLists);
   cudaStream_t st = (cudaStream_t)stream;
-  const Policy P{3, 3, 3, 3, 4, 0, 100};  // the default policy (Sec. 4)
+  const Policy P{3, 3, 3, 3, 4, MODEL_PCF, 100, RANGE_ARRAY, 0};  // the default policy (Sec. 4)
 
   // the status word is the only scratch that must start at zero here (the
   // class counts are cleared by the on-chip launch itself); the records,

@@ -30,13 +30,14 @@ class PcfError(RuntimeError):
 
 
 MODELS = {"pcf": 0, "spline": 1}
+RANGES = {"array": 0, "sample": 1}
 
 
 class Policy(ctypes.Structure):
     _fields_ = [("a_num", ctypes.c_uint32), ("b_num", ctypes.c_uint32),
                 ("c_num", ctypes.c_uint32), ("d_num", ctypes.c_uint32),
                 ("den", ctypes.c_uint32), ("model", ctypes.c_uint32),
-                ("tau", ctypes.c_uint64)]
+                ("tau", ctypes.c_uint64), ("range_mode", ctypes.c_uint32)]
 
 
 class Tuning(ctypes.Structure):
@@ -153,13 +154,16 @@ class Context:
         if rc:
             raise PcfError(rc, lib().pcf_last_cuda_error(self._h).decode())
 
-    def set_policy(self, a_num=3, b_num=3, c_num=3, d_num=3, den=4, tau=100, model="pcf"):
-        """alpha..delta = floor(n^(x_num/den)), tau, and the CDF model: "pcf"
-        (Sec. 3.3) or "spline" (Spline Learned Sort, App. A.5)."""
+    def set_policy(self, a_num=3, b_num=3, c_num=3, d_num=3, den=4, tau=100, model="pcf",
+                   range_mode="array"):
+        """alpha..delta = floor(n^(x_num/den)), tau, the CDF model ("pcf",
+        Sec. 3.3, or "spline", App. A.5) and the range the bins span
+        ("array": the (sub)array's, "sample": the alpha samples')."""
         m = MODELS[model] if isinstance(model, str) else int(model)
+        r = RANGES[range_mode] if isinstance(range_mode, str) else int(range_mode)
         self._check(lib().pcf_ctx_set_policy(self._h, ctypes.byref(
             Policy(a_num=a_num, b_num=b_num, c_num=c_num, d_num=d_num, den=den, model=m,
-                   tau=tau))))
+                   tau=tau, range_mode=r))))
 
     def set_tuning(self, max_digit_bits=0, tile_log2=0, leaf_cap=0):
         self._check(lib().pcf_ctx_set_tuning(self._h, ctypes.byref(
