@@ -246,6 +246,40 @@ def test_invalid_arguments(ctx, P):
     assert L.pcf_sort_keys(ctx._h, t.data_ptr() + 4, t.data_ptr(), 2, 0, 0, None) == 1
     with pytest.raises(P.PcfError):
         ctx.set_policy(3, 3, 3, 4, 4, 100)  # delta exponent must be < 1
+    with pytest.raises(P.PcfError):
+        ctx.set_policy(model=2)             # no such CDF model
+    with pytest.raises(P.PcfError):
+        ctx.set_policy(range_mode=5)        # no such range mode
+    # the bucketing-only entry: arrays of fewer than 2 keys, bad parameters
+    k = torch.from_numpy(W.f64_keys("normal", 1000, 1)).cuda()
+    for offs, abc in [([0, 1, 1000], (10, 10, 10)), ([0, 500, 400, 1000], (10, 10, 10)),
+                      ([0, 1000], (0, 10, 10)), ([0, 1000], (10, 10, 1 << 24))]:
+        with pytest.raises(P.PcfError) as ei:
+            ctx.bucket_sizes(k, offs, *abc)
+        assert ei.value.code == 1
+    x = W.f64_keys("normal", 1000, 2)
+    x[500] = np.nan
+    with pytest.raises(P.PcfError) as ei:
+        ctx.bucket_sizes(to_dev(x), [0, 1000], 30, 30, 30)
+    assert ei.value.code == 2
+    ctx.set_policy()  # back to the default for the tests that follow
+
+
+def test_host_batch_error_leaves_no_copy_in_flight(ctx, P):
+    # a NaN in the second of three arrays: the call fails, returns with its
+    # copies drained, and the context sorts normally afterwards
+    xs = [W.f64_keys("uniform", 200000, 60 + i) for i in range(3)]
+    xs[1][1234] = np.nan
+    hs = [torch.from_numpy(x.copy()).pin_memory() for x in xs]
+    with pytest.raises(P.PcfError) as ei:
+        ctx.sort_keys_host_batch(hs, key_type="f64")
+    assert ei.value.code == 2
+    ref, _ = oracle.sort(xs[0])
+    assert same_bits(hs[0].numpy(), ref)       # the array before the failure is done
+    h = torch.from_numpy(xs[2].copy()).pin_memory()
+    ctx.sort_keys_host_batch([h], key_type="f64")
+    ref, _ = oracle.sort(xs[2])
+    assert same_bits(h.numpy(), ref)
 
 
 def test_host_end_to_end(ctx):
