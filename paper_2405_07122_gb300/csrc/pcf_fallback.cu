@@ -2,7 +2,10 @@
 // on-chip kernels: |c| >= delta (Algorithm 1's failure guard, Sato & Matsui,
 // TMLR 2025) or a degenerate range.  A stable merge sort: block-local sorted
 // runs of kMergeTile keys, then merge passes split by merge-path
-// partitioning, one CTA per kMergeTile outputs.
+// partitioning, one CTA per kMergeTile outputs.  Before it, a bucket that
+// one value dominates is split stably into below / equal / above that value
+// (k_fb_mode, k_fb_part_count, k_fb_part_scatter; the host driver runs the
+// rounds).
 #include "pcf_internal.h"
 
 namespace pcf {

@@ -3,6 +3,7 @@
 // Sec. 3.3), for a batch of (sub)arrays ("segments"):
 //
 //   k_range     x_min, x_max of every segment (+ NaN check)          Sec. 3.3
+//   k_sample_range  the same over the alpha samples (sample-range policy)
 //   k_model     degenerate-range test and the bin function's constants
 //   k_sample    draw alpha keys, count them per bin, and (last CTA of the
 //               segment) accumulate b_k and the bucket table
@@ -13,6 +14,9 @@
 //   k_groups / k_hist2 / k_scatter2   the same for the low digit, per group
 //   k_buckets   the per-bucket decision of Alg. 1 (|c| >= delta -> standard
 //               sort; small -> shared-memory kernel; else next level)
+//   k_next_segs / k_cols_*   the next level's plan, built on the device
+//   k_bucket_sizes / k_bucket_max   level-0 bucket sizes only (Sec. 4.2)
+//   k_xfer      small host <-> device copies through pinned host memory
 //
 // The gamma + 1 buckets are produced by two stable scatters on the high and
 // the low bits of the bucket id; two stable passes compose to the single

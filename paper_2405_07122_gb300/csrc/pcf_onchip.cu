@@ -1,11 +1,14 @@
-// pcf_onchip.cu -- buckets finished on chip, one warp per bucket.
+// pcf_onchip.cu -- buckets finished on chip: a warp, or a CTA, per bucket.
 //
 // Every bucket of a global level that fits on chip is one call of
 // Learned-Sort (Algorithm 1 of Sato & Matsui, TMLR 2025, with the PCF model
-// of Sec. 3.3).  A warp takes a bucket, stages its keys in the warp's slice
-// of shared memory (as order-preserving integers), and runs the recursion
-// there with warp-synchronous code -- no block barriers, so the 30-40 warps
-// of an SM overlap each other's latencies:
+// of Sec. 3.3, or the spline model of App. A.5).  Buckets of at most 256
+// keys (and every bucket of a key-value sort) go to a warp, which stages its
+// keys in the warp's slice of shared memory (as order-preserving integers)
+// and runs the recursion there with warp-synchronous code -- no block
+// barriers, so the 30-40 warps of an SM overlap each other's latencies.
+// Larger buckets of keys-only sorts go to a CTA of 64-512 threads (one slice
+// per CTA, up to 8192 keys; k_onchip_cta).  The steps:
 //   - Learned-Sort step: range (warp reduction), the model (lane 0; the
 //     binary64 division runs in one lane), alpha samples with replacement
 //     counted per bin (Sec. 3.3), b_k by a warp scan and the bucket table
@@ -18,9 +21,10 @@
 //     keys among the bucket's; a whole call by ranking (at most 32 keys), a
 //     bitonic network across the warp's registers (keys only, at most 64) or
 //     a merge sort (larger, or key-value: stable).
-// The leaf records are first listed by size class; the warps of a launch
-// take the buckets of one class in turn (the class's slice size bounds the
-// keys of a bucket; three classes up to 1024 keys).
+// The leaf records are first listed by size class; the warps (or CTAs) of a
+// launch take the buckets of one class in turn (the class's slice size
+// bounds the keys of a bucket; classes (0, 256], (256, 512], ... up to
+// leaf_cap).  The CDF model and the range policy are template parameters.
 #include "pcf_internal.h"
 
 namespace pcf {
