@@ -361,8 +361,25 @@ struct LevelPlan {
            tiles2_bound = 0;
   uint32_t dmax1 = 1, dmax2 = 1;
   bool two_pass = false;
+  uint32_t tile_log2 = 14;  // the level's pass-1 count tiles
   DevPlan dp{};
 };
+
+// Tiles of a level's passes: the tuning's pass-1 size (halved, down to 2^12,
+// while the level would have fewer than 4 tiles per SM, so that small
+// arrays still spread over the GPU) and pass-2 tiles up to 4x that, while
+// they still give 4 per SM.  Level 0 only: later levels are planned on the
+// device with the tuning's size.
+uint32_t level0_tile_log2(const pcf_tuning& tu, uint64_t n_level, int num_sms) {
+  uint32_t t = tu.tile_log2;
+  while (t > 12 && (n_level >> t) < 4ull * (uint64_t)num_sms) --t;
+  return t;
+}
+uint32_t pass2_shift(uint32_t tile_log2, uint64_t n_level, int num_sms) {
+  uint32_t sh = 2;
+  while (sh > 0 && (n_level >> (tile_log2 + sh)) < 4ull * (uint64_t)num_sms) --sh;
+  return sh;
+}
 
 // alpha, beta, gamma, delta of every on-chip size n <= cap, so the leaf
 // kernel looks them up instead of evaluating floor(n^{p/q}) per bucket.
@@ -724,7 +741,12 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   LevelPlan L;
   if (!big.empty()) {
     Plan pl;
-    plan_level(ctx->policy, ctx->tuning, ctx->pcache, big, pl);
+    uint64_t n_big = 0;
+    for (auto& sg : big) n_big += sg.n;
+    pcf_tuning tu0 = ctx->tuning;
+    tu0.tile_log2 = level0_tile_log2(ctx->tuning, n_big, ctx->num_sms);
+    L.tile_log2 = tu0.tile_log2;
+    plan_level(ctx->policy, tu0, ctx->pcache, big, pl);
     const uint32_t S = (uint32_t)big.size();
     const PlanLayout PL = plan_layout(S);
     CK(ensure_host(ctx->h_stage, PL.bytes));
@@ -844,7 +866,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     kb.out_v = P2v;
     CK(ensure(ctx->cmat1, L.cmat1 * 4));
     CK(cudaMemsetAsync(ctx->cmat1.p, 0, L.cmat1 * 4, st));
-    CK(launch_hist1(lc, d_segs, S, L.dp.t1, L.n_t1, tile_keys, src, as<uint32_t>(ctx->tpool),
+    const uint32_t tk = 1u << L.tile_log2;
+    CK(launch_hist1(lc, d_segs, S, L.dp.t1, L.n_t1, tk, src, as<uint32_t>(ctx->tpool),
                     as<uint32_t>(ctx->cmat1), L.dmax1, as<uint32_t>(ctx->jbuf),
                     srange && check_nan));
     if (late_gate) {
@@ -855,18 +878,18 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     CK(launch_scan(lc, as<uint32_t>(ctx->cmat1), L.cmat1, nullptr, as<uint64_t>(ctx->sw),
                    tile_counter, scan_withhold, spin_limit, nullptr));
     tm.mark(2);
-    CK(launch_scatter1(lc, d_segs, S, L.dp.t1, L.n_t1, tile_keys, kb, as<uint32_t>(ctx->tpool),
+    CK(launch_scatter1(lc, d_segs, S, L.dp.t1, L.n_t1, tk, kb, as<uint32_t>(ctx->tpool),
                        as<uint32_t>(ctx->cmat1), L.dmax1));
     tm.mark(3);
     ctx->stats.global_passes += 1;
     ctx->stats.bytes_moved += n_level * (8 /*range*/ + 8 + 4 /*hist1*/ + 12 + 10 /*scatter1*/) +
                               (pairs ? n_level * 8 : 0);
-    // pass 2: count tiles 4x larger than pass 1's.  Its digit is the wider
-    // one, and larger tiles keep its count matrix (written and read with a
-    // stride of one row per digit) small; the plan's bounds, taken with
-    // pass 1's tile size, still hold (there are fewer tiles)
+    // pass 2: count tiles up to 4x larger than pass 1's.  Its digit is the
+    // wider one, and larger tiles keep its count matrix (written and read
+    // with a stride of one row per digit) small; the plan's bounds, taken
+    // with pass 1's tile size, still hold (there are fewer tiles)
     if (L.two_pass) {
-      const uint32_t tile_keys2 = tile_keys << 2;
+      const uint32_t tile_keys2 = tk << pass2_shift(L.tile_log2, n_level, ctx->num_sms);
       CK(ensure(ctx->groups, L.n_groups * sizeof(Group)));
       CK(ensure(ctx->gtiles, L.n_groups * 4));
       CK(ensure(ctx->gcent, L.n_groups * 4));
@@ -970,6 +993,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       N.dmax1 = std::max(1u, pt.dmax1);
       N.dmax2 = std::max(1u, pt.dmax2);
       N.two_pass = pt.two_pass != 0;
+      N.tile_log2 = ctx->tuning.tile_log2;  // as the device planner used
       N.dp = ndp;
     }
     L = N;
