@@ -325,6 +325,9 @@ def main():
     assert all(bool((p[1:] >= p[:-1]).all()) for p in pinned), "e2e output not sorted"
 
     peak, peak_kind = peaks()
+    # the library's own 16-byte copy over two 800 MB arrays: the passes'
+    # access pattern at full speed, a reference beside the measured peak
+    copy_gbs = ctx.copy_bandwidth(ins[0], outs[0], reps=10, stream=stream)
     per_launch = {}
     for k, b in KERNEL_BYTES.items():
         ms_k = stages[k] / (t_steps * 4)
@@ -353,7 +356,8 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": stage_traffic(dom, n), "bytes_per_key": dom_b},
+                     "traffic": stage_traffic(dom, n), "bytes_per_key": dom_b,
+                     "copy_kernel_gbs": copy_gbs},
         # the whole sort against the copy peak: the bytes the passes it ran
         # must move (the library's pass model), and the 48 B/key minimum of
         # one bucketing level (range 8, predict 8, move 16, finish 16)

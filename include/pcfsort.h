@@ -218,6 +218,15 @@ pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_
                             uint64_t beta, uint64_t gamma, uint32_t* d_counts, uint64_t* h_max,
                             void* stream);
 
+/* Device copy bandwidth with the passes' access pattern (16-byte loads and
+ * stores, grid-stride, each byte read and written once): one untimed copy,
+ * then `reps` copies of `bytes` from d_src to d_dst (device buffers, 16-byte
+ * aligned, not overlapping; bytes a non-zero multiple of 16), timed with CUDA
+ * events on `stream`.  *gb_per_s = 2 * bytes * reps / time.  A reference for
+ * the passes' roofline measured in the same run. */
+pcf_status pcf_copy_bandwidth(pcf_ctx* ctx, const void* d_src, void* d_dst, uint64_t bytes,
+                              uint32_t reps, void* stream, double* gb_per_s);
+
 /* Stage timing of the last sort (milliseconds between CUDA events recorded
  * on the sort's stream) when enabled with pcf_ctx_enable_timing(ctx, 1):
  * [0] range (k_range + k_model), [1] sample + PCF table (k_sample),

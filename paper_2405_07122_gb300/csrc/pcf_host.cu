@@ -1364,6 +1364,40 @@ pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_
   return PCF_OK;
 }
 
+// Device copy bandwidth with the passes' access pattern: reps copies of
+// `bytes` from d_src to d_dst (16-byte aligned, bytes a multiple of 16),
+// timed with CUDA events on `stream` after one untimed copy; *gb_per_s =
+// 2 bytes (read + written) per copy / mean time.
+pcf_status pcf_copy_bandwidth(pcf_ctx* ctx, const void* d_src, void* d_dst, uint64_t bytes,
+                              uint32_t reps, void* stream, double* gb_per_s) {
+  if (!ctx || !d_src || !d_dst || !gb_per_s || reps == 0 || bytes == 0 || (bytes & 15) ||
+      (((uintptr_t)d_src | (uintptr_t)d_dst) & 15))
+    return PCF_ERR_INVALID_ARG;
+  if (overlap(d_src, d_dst, bytes)) return PCF_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t grid = (uint32_t)ctx->num_sms * 8;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ctx, e);
+  }
+  e = launch_copy128(st, d_src, d_dst, bytes / 16, grid);
+  if (!e) e = cudaEventRecord(e0, st);
+  for (uint32_t r = 0; r < reps && !e; ++r) e = launch_copy128(st, d_src, d_dst, bytes / 16, grid);
+  if (!e) e = cudaEventRecord(e1, st);
+  if (!e) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(e);
+  *gb_per_s = ms > 0.f ? 2.0 * (double)bytes * reps / (ms * 1e-3) / 1e9 : 0.0;
+  return PCF_OK;
+}
+
 // ---- self-test hooks (used by the test suite) ----
 
 // Host copy of the kernels' bin function, for CPU checks of the fast path.

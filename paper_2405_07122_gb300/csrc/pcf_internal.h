@@ -187,6 +187,9 @@ cudaError_t launch_hist1(const LaunchCfg& c, const Seg* segs, uint32_t S, const 
 cudaError_t launch_bucket_sizes(const LaunchCfg& c, const Seg* segs, uint32_t S,
                                 const uint32_t* tile_base, uint32_t n_tiles, uint32_t tile_keys,
                                 const uint32_t* jbuf, uint32_t* counts, uint64_t* out_max);
+// 16-byte device-to-device copy of n16 words (the copy bandwidth probe)
+cudaError_t launch_copy128(cudaStream_t st, const void* src, void* dst, uint64_t n16,
+                           uint32_t grid);
 // Small host <-> device transfers of a sort, copied by the SMs through the
 // device view of pinned host memory.  A copy-engine transfer would queue
 // behind any large copy in the same direction already issued on another

@@ -1230,6 +1230,34 @@ cudaError_t launch_bucket_sizes(const LaunchCfg& c, const Seg* segs, uint32_t S,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Copy bandwidth probe: the same 16-byte, grid-stride, read-once write-once
+// access pattern as the passes, over device buffers (a roofline reference
+// measured beside the sort; the reported peak stays the pool's measurement).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_copy128(const uint4* __restrict__ src,
+                                                 uint4* __restrict__ dst, uint64_t n16) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = t;
+  for (; i + 3 * nt < n16; i += 4 * nt) {
+    const uint4 a = __ldg(src + i), b = __ldg(src + i + nt), c = __ldg(src + i + 2 * nt),
+                d = __ldg(src + i + 3 * nt);
+    dst[i] = a;
+    dst[i + nt] = b;
+    dst[i + 2 * nt] = c;
+    dst[i + 3 * nt] = d;
+  }
+  for (; i < n16; i += nt) dst[i] = __ldg(src + i);
+}
+
+cudaError_t launch_copy128(cudaStream_t st, const void* src, void* dst, uint64_t n16,
+                           uint32_t grid) {
+  if (!n16) return cudaSuccess;
+  k_copy128<<<grid, 256, 0, st>>>((const uint4*)src, (uint4*)dst, n16);
+  return cudaGetLastError();
+}
+
 // Byte copy by the SMs (one side pinned host memory, seen through its
 // device pointer): 16-byte words when both ends allow it.
 __global__ void k_xfer(uint8_t* __restrict__ dst, const uint8_t* __restrict__ src, size_t n,

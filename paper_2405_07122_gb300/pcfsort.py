@@ -83,6 +83,7 @@ def lib():
                                    ctypes.c_int, _u64, _vp],
             "pcf_sort_keys_host": [_vp, _vp, _u64, ctypes.c_int, _u64, _vp],
             "pcf_sort_keys_host_batch": [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _vp],
+            "pcf_copy_bandwidth": [_vp, _vp, _vp, _u64, _u32, _vp, ctypes.POINTER(ctypes.c_double)],
             "pcf_bucket_sizes": [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _u64, _u64, _u64, _vp,
                                  _vp, _vp],
             "pcf_sort_segmented_static": [_vp, _vp, _vp, _u32, _u64, ctypes.c_int, _u64, _vp],
@@ -273,6 +274,16 @@ class Context:
             alpha, beta, gamma, None if counts_out is None else counts_out.data_ptr(),
             out.ctypes.data_as(ctypes.POINTER(_u64)), _stream_ptr(stream)))
         return out
+
+    def copy_bandwidth(self, src, dst, reps=10, stream=None):
+        """GB/s (read + written) of the library's 16-byte copy over two CUDA
+        tensors of equal byte size."""
+        nbytes = src.numel() * src.element_size()
+        out = ctypes.c_double(0.0)
+        self._check(lib().pcf_copy_bandwidth(self._h, src.data_ptr(), dst.data_ptr(),
+                                             nbytes - nbytes % 16, reps, _stream_ptr(stream),
+                                             ctypes.byref(out)))
+        return out.value
 
     # -- self-test hooks ----------------------------------------------------
     def debug_scan(self, data_u32, withhold_tile=0xFFFFFFFF, spin_limit=0, stream=None):

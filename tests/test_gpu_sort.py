@@ -282,6 +282,16 @@ def test_host_batch_error_leaves_no_copy_in_flight(ctx, P):
     assert same_bits(h.numpy(), ref)
 
 
+def test_copy_bandwidth_probe(ctx, P):
+    src = torch.randint(-2**62, 2**62, (1 << 24,), dtype=torch.int64, device="cuda")
+    dst = torch.zeros_like(src)
+    gbs = ctx.copy_bandwidth(src, dst, reps=3)
+    torch.cuda.synchronize()
+    assert torch.equal(src, dst) and gbs > 0
+    with pytest.raises(P.PcfError):
+        ctx.copy_bandwidth(src[:-2], src[2:], reps=1)  # overlapping buffers
+
+
 def test_host_end_to_end(ctx):
     x = W.f64_keys("normal", 1 << 20, 21)
     h = torch.from_numpy(x.copy()).pin_memory()
