@@ -37,14 +37,20 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=None, checked: bool = False) -> str:
+    """Compiles and links the library; checked=True builds the index-checked
+    variant (-DPCF_CHECKED) into _build/checked/libpcfsort_checked.so."""
+    out_dir = os.path.join(OUT_DIR, "checked") if checked else OUT_DIR
+    lib = os.path.join(out_dir, "libpcfsort_checked.so") if checked else LIB
+    if checked:
+        extra = list(extra or []) + ["-DPCF_CHECKED"]
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "pcfsort.h"))
     objs, jobs = [], []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OUT_DIR, s.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc()] + ARCH + NVCC_FLAGS + (extra or []) + ["-c", src, "-o", obj]
@@ -56,15 +62,15 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
                 sys.stderr.write(res.stdout + res.stderr)
             if res.returncode:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp.%d" % os.getpid()
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode:
             sys.stderr.write(res.stdout + res.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -162,9 +162,19 @@ pcf_status cuda_fail(pcf_ctx* c, cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
   } while (0)
 
+// Test hook: the allocation that many device allocations from now fails
+// (host side, as cudaMalloc would report exhausted memory); -1: never.
+thread_local int64_t g_fail_alloc_after = -1;
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return cudaSuccess;
+  if (g_fail_alloc_after >= 0 && g_fail_alloc_after-- == 0) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    return cudaErrorMemoryAllocation;
+  }
   if (b.p) {
     cudaFree(b.p);
     b.p = nullptr;
@@ -639,8 +649,13 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   lc.range_mode = ctx->policy.range_mode;
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
-  CK(cudaMemsetAsync(lc.status, 0, 4, st));
+  CK(cudaMemsetAsync(lc.status, 0, 16, st));
   CK(ensure_host(ctx->h_status, 64));
+#ifdef PCF_CHECKED
+  // the key buffers' length, for the checked build's index checks
+  *(uint64_t*)((char*)ctx->h_status.p + 8) = n_total;
+  CK(launch_xfer(st, (char*)lc.status + 8, (char*)ctx->h_status.dp + 8, 8));
+#endif
   CK(ensure_host(ctx->h_lout, sizeof(LevelOut)));
   CK(ensure(ctx->lout, sizeof(LevelOut) + 64));
   CK(ensure(ctx->misc, 256));
@@ -949,7 +964,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     const LevelOut lo = *(LevelOut*)ctx->h_lout.p;
     const uint32_t stw = *(uint32_t*)ctx->h_status.p;
     if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
-    if (stw & STATUS_INTERNAL) return PCF_ERR_INTERNAL;
+    if (stw & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
     ctx->stats.leaf_buckets += lo.n_leaf;
     uint64_t level_fb_keys = 0;
     // standard sort of the large failure-guard / degenerate buckets
@@ -1007,7 +1022,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   const uint32_t stw = *(uint32_t*)ctx->h_status.p;
   if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
   if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
-  if (stw & STATUS_INTERNAL) return PCF_ERR_INTERNAL;
+  if (stw & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
   return PCF_OK;
 }
 
@@ -1287,7 +1302,7 @@ pcf_status pcf_bucket_sizes(pcf_ctx* ctx, const void* d_keys, const uint64_t* h_
   ctx->stats = pcf_call_stats{};
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
-  CK(cudaMemsetAsync(lc.status, 0, 4, st));
+  CK(cudaMemsetAsync(lc.status, 0, 16, st));
   CK(ensure_host(ctx->h_status, 64));
   CK(ensure(ctx->misc, 256));
   Params fixed;
@@ -1400,6 +1415,10 @@ pcf_status pcf_copy_bandwidth(pcf_ctx* ctx, const void* d_src, void* d_dst, uint
 
 // ---- self-test hooks (used by the test suite) ----
 
+// The k-th device workspace allocation from now (0: the next) on this host
+// thread fails as an out-of-memory error; k < 0 clears the injection.
+void pcf_debug_fail_alloc_after(int64_t k) { g_fail_alloc_after = k < 0 ? -1 : k; }
+
 // Host copy of the kernels' bin function, for CPU checks of the fast path.
 // Returns 1 (and writes nothing) if the range [lo, hi] is degenerate.
 int pcf_debug_bins_host(uint32_t kt, uint64_t lo_bits, uint64_t hi_bits, uint32_t beta,
@@ -1437,7 +1456,7 @@ pcf_status pcf_debug_scan(pcf_ctx* ctx, uint32_t* d_data, uint64_t n, uint32_t w
   lc.pairs = false;
   lc.launches = nullptr;
   lc.status = as<uint32_t>(ctx->status);
-  CK(cudaMemsetAsync(lc.status, 0, 4, st));
+  CK(cudaMemsetAsync(lc.status, 0, 16, st));
   CK(launch_scan(lc, d_data, n, nullptr, as<uint64_t>(ctx->sw), as<uint32_t>(ctx->misc),
                  withhold_tile, spin_limit ? spin_limit : kSpinLimit, nullptr));
   CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));

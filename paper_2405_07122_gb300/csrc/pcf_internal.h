@@ -13,6 +13,7 @@ enum : uint32_t {
   STATUS_NAN = 1u,       // a NaN key was seen (binary64 keys)
   STATUS_TIMEOUT = 2u,   // a bounded wait gave up
   STATUS_INTERNAL = 4u,  // an internal capacity check failed
+  STATUS_BOUNDS = 8u,    // a checked build caught an index out of bounds
 };
 
 // SEG_NEEDRANGE: the samples' range (R14) was equal or degenerate; the
@@ -129,6 +130,29 @@ struct KeyBufs {
   uint16_t* tmp_aux;    // low bucket-id digit carried from pass 1 to pass 2
   const uint32_t* jbuf; // bucket id of every key of the level (written by k_hist1)
 };
+
+// ---- checked builds (-DPCF_CHECKED) ----
+// Index checks in place of a memory checker: a computed index is tested
+// against its buffer before the access; one out of bounds sets STATUS_BOUNDS
+// and the access is skipped (no trap, no fault).  The key buffers' length
+// is read from the status buffer (u64 at byte 8, written at each call's
+// start).  In normal builds every check is `true`.
+#ifdef PCF_CHECKED
+__device__ __forceinline__ bool pcf_in_bounds(uint64_t i, uint64_t n, uint32_t* status) {
+  if (i < n) return true;
+  if (status) atomicOr(status, (uint32_t)STATUS_BOUNDS);
+  return false;
+}
+__device__ __forceinline__ uint64_t pcf_key_limit(const uint32_t* status) {
+  const uint64_t lim = status ? *reinterpret_cast<const volatile uint64_t*>(status + 2) : 0ull;
+  return lim ? lim : ~0ull;  // 0: not set by this entry point
+}
+#define PCF_IN(i, n, st) pcf_in_bounds((uint64_t)(i), (uint64_t)(n), (st))
+#define PCF_IN_KEYS(i, st) pcf_in_bounds((uint64_t)(i), pcf_key_limit(st), (st))
+#else
+#define PCF_IN(i, n, st) true
+#define PCF_IN_KEYS(i, st) true
+#endif
 
 // ---- kernel launchers ----
 struct LaunchCfg {

@@ -501,7 +501,9 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
                              const uint32_t* __restrict__ src_j, uint32_t b2,
                              const uint64_t* __restrict__ src, const uint32_t* __restrict__ src_v,
                              const uint16_t* __restrict__ src_aux, uint64_t* __restrict__ dst,
-                             uint32_t* __restrict__ dst_v, uint16_t* __restrict__ dst_aux) {
+                             uint32_t* __restrict__ dst_v, uint16_t* __restrict__ dst_aux,
+                             uint32_t* status = nullptr) {
+  (void)status;
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const uint32_t lmask = lanemask_lt();
   const uint32_t low_mask = (1u << b2) - 1u;
@@ -599,6 +601,7 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
       const uint32_t li = (uint32_t)w * (32 * kItems) + (uint32_t)k * 32 + (uint32_t)l;
       if (li < nsub) {
         const uint32_t pos = sm.dbase[dig[k]] + my[dig[k]] + rank[k];
+        if (!PCF_IN(pos, nsub, status)) continue;
         sm.skey[pos] = key[k];
         sm.sdig[pos] = (uint16_t)dig[k];
         if (PASS == 1) sm.saux[pos] = (uint16_t)aux[k];
@@ -614,6 +617,7 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
       if (pos < nsub) {
         const uint32_t d = sm.sdig[pos];
         const uint64_t o = (uint64_t)sm.gofs[d] + (pos - sm.dbase[d]);
+        if (!PCF_IN_KEYS(o, status)) continue;
         dst[o] = sm.skey[pos];
         if (PASS == 1) dst_aux[o] = sm.saux[pos];
         if (PAIRS) dst_v[o] = sm.sval[pos];
@@ -632,7 +636,8 @@ template <bool PAIRS>
 __global__ void __launch_bounds__(256, 2) k_scatter1(const Seg* segs, uint32_t S,
                                                   const uint32_t* tile_base, uint32_t tile_keys,
                                                   KeyBufs kb, const uint32_t* __restrict__ tpool,
-                                                  const uint32_t* __restrict__ cmat) {
+                                                  const uint32_t* __restrict__ cmat,
+                                                  uint32_t* status) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
@@ -648,7 +653,7 @@ __global__ void __launch_bounds__(256, 2) k_scatter1(const Seg* segs, uint32_t S
   const uint64_t tile_off = g.off + (uint64_t)tt * tile_keys;
   const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, g.off + g.n - tile_off);
   scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, kb.jbuf, g.b2, kb.src, kb.src_v, nullptr, kb.tmp,
-                         kb.tmp_v, kb.tmp_aux);
+                         kb.tmp_v, kb.tmp_aux, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -739,7 +744,8 @@ template <bool PAIRS>
 __global__ void __launch_bounds__(256, 2) k_scatter2(const Group* groups, uint32_t n_groups,
                                                   const Seg* segs, const uint32_t* g_tile_scan,
                                                   const uint64_t* total_tiles, uint32_t tile_keys,
-                                                  KeyBufs kb, const uint32_t* __restrict__ cmat2) {
+                                                  KeyBufs kb, const uint32_t* __restrict__ cmat2,
+                                                  uint32_t* status) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t t = blockIdx.x;
   if (t >= *total_tiles) return;
@@ -756,7 +762,7 @@ __global__ void __launch_bounds__(256, 2) k_scatter2(const Group* groups, uint32
   const uint64_t tile_off = gr.off + (uint64_t)tt * tile_keys;
   const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, gr.off + gr.n - tile_off);
   scatter_tile<2, PAIRS>(sm, D, tile_off, tile_n, nullptr, 0, kb.tmp, kb.tmp_v, kb.tmp_aux, kb.out,
-                         kb.out_v, nullptr);
+                         kb.out_v, nullptr, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -857,6 +863,7 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
       if (PAIRS) tv[q][t] = val;
     }
     for (uint32_t i = 0; i < size; ++i) {
+      if (!PCF_IN_KEYS(off + i, status)) break;
       out_k[off + i] = tk[i][t];
       if (PAIRS) out_v[off + i] = tv[i][t];
     }
@@ -1314,12 +1321,13 @@ cudaError_t launch_scatter1(const LaunchCfg& c, const Seg* segs, uint32_t S,
   cudaError_t e;
   if (c.pairs) {
     if ((e = set_smem(k_scatter1<true>, sm))) return e;
-    k_scatter1<true><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb, tpool, cmat);
+    k_scatter1<true><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb, tpool, cmat,
+                                                      c.status);
     count_launch(c);
   } else {
     if ((e = set_smem(k_scatter1<false>, sm))) return e;
     k_scatter1<false><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb, tpool,
-                                                       cmat);
+                                                       cmat, c.status);
     count_launch(c);
   }
   return cudaGetLastError();
@@ -1366,12 +1374,14 @@ cudaError_t launch_scatter2(const LaunchCfg& c, const Group* groups, uint32_t n_
   if (c.pairs) {
     if ((e = set_smem(k_scatter2<true>, sm))) return e;
     k_scatter2<true><<<n_tiles_bound, 256, sm, c.stream>>>(groups, n_groups, segs, g_tile_scan,
-                                                           total_tiles, tile_keys, kb, cmat2);
+                                                           total_tiles, tile_keys, kb, cmat2,
+                                                           c.status);
     count_launch(c);
   } else {
     if ((e = set_smem(k_scatter2<false>, sm))) return e;
     k_scatter2<false><<<n_tiles_bound, 256, sm, c.stream>>>(groups, n_groups, segs, g_tile_scan,
-                                                            total_tiles, tile_keys, kb, cmat2);
+                                                            total_tiles, tile_keys, kb, cmat2,
+                                                            c.status);
     count_launch(c);
   }
   return cudaGetLastError();

@@ -612,6 +612,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
       return;
     }
     for (uint32_t i = lane; i < n; i += 32) {
+      if (!PCF_IN_KEYS(off + i, status)) break;
       out[off + i] = bits_of_ord(w.A[i], kt);
       if (PAIRS) out_v[off + i] = w.Av[i];
     }
@@ -948,7 +949,10 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
       if (tid == 0) atomicOr(status, STATUS_INTERNAL);
       return;
     }
-    for (uint32_t i = tid; i < n; i += NT) out[off + i] = bits_of_ord(w.A[i], kt);
+    for (uint32_t i = tid; i < n; i += NT) {
+      if (!PCF_IN_KEYS(off + i, status)) break;
+      out[off + i] = bits_of_ord(w.A[i], kt);
+    }
     __syncthreads();
   }
 }

@@ -126,10 +126,11 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
   cudaStream_t st = (cudaStream_t)stream;
   const Policy P{3, 3, 3, 3, 4, MODEL_PCF, 100, RANGE_ARRAY, 0};  // the default policy (Sec. 4)
 
-  // the status word is the only scratch that must start at zero here (the
+  // the status word (and, for checked builds, the key limit after it: zero,
+  // no limit) is the only scratch that must start at zero here (the
   // class counts are cleared by the on-chip launch itself); the records,
   // lists and table are fully written before they are read
-  if (cudaMemsetAsync(status, 0, 4, st) != cudaSuccess) return PCF_ERR_CUDA;
+  if (cudaMemsetAsync(status, 0, 16, st) != cudaSuccess) return PCF_ERR_CUDA;
   const uint64_t work = std::max<uint64_t>(std::max<uint64_t>(S, kStCap + 1), n_total / 8);
   const uint32_t grid = (uint32_t)std::min<uint64_t>((work + 255) / 256, 1024);
   k_static_prepare<<<grid, 256, 0, st>>>(d_offsets, S, n_total, seed, P,
@@ -159,6 +160,6 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
       cudaStreamSynchronize(st) != cudaSuccess)
     return PCF_ERR_CUDA;
   if (h_status & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
-  if (h_status & STATUS_INTERNAL) return PCF_ERR_INTERNAL;
+  if (h_status & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
   return PCF_OK;
 }

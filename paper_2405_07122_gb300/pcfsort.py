@@ -107,6 +107,8 @@ def lib():
         L.pcf_debug_root_floor.argtypes = [_u64, _u32, _u32]
         L.pcf_debug_sample_index.restype = _u64
         L.pcf_debug_sample_index.argtypes = [_u64, _u64, _u64, _u64, _u64]
+        L.pcf_debug_fail_alloc_after.restype = None
+        L.pcf_debug_fail_alloc_after.argtypes = [ctypes.c_int64]
         _lib = L
     return _lib
 

@@ -282,6 +282,34 @@ def test_host_batch_error_leaves_no_copy_in_flight(ctx, P):
     assert same_bits(h.numpy(), ref)
 
 
+def test_injected_allocation_failure(P):
+    # a device allocation fails (injected on the host, as an exhausted
+    # device would report it) at every point of a fresh context's first
+    # sort: the call returns PCF_ERR_OOM with nothing in flight, and the
+    # same context then sorts correctly
+    x = W.f64_keys("lognormal", 300000, 77)
+    ref, _ = oracle.sort(x)
+    L = P.lib()
+    failures = 0
+    for k in range(64):
+        c = P.Context(0)
+        L.pcf_debug_fail_alloc_after(k)
+        try:
+            got = gpu_sort(c, x)
+            L.pcf_debug_fail_alloc_after(-1)
+            assert same_bits(got, ref)
+            c.close()
+            break  # k is past the last allocation of the call
+        except P.PcfError as e:
+            assert e.code == 3, (k, e.code)
+            failures += 1
+        finally:
+            L.pcf_debug_fail_alloc_after(-1)
+        assert same_bits(gpu_sort(c, x), ref), k
+        c.close()
+    assert failures >= 5
+
+
 def test_copy_bandwidth_probe(ctx, P):
     src = torch.randint(-2**62, 2**62, (1 << 24,), dtype=torch.int64, device="cuda")
     dst = torch.zeros_like(src)
