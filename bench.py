@@ -354,6 +354,12 @@ def main():
         "e2e": {"value": e2e, "unit": "Gkeys/s", "h2d_bytes_per_step": 8 * 4 * n,
                 "d2h_bytes_per_step": 8 * 4 * n},
         "gpu_launches": int(launches),
+        # every stage against the same peak: its algorithmic bytes per key x
+        # n over its time per array (all levels of the array included)
+        "stage_rooflines": {k: {"bytes_per_key": b_k, "ms_per_array": ms_k,
+                                "achieved_gbs": b_k * n / (ms_k / 1e3) / 1e9,
+                                "frac": b_k * n / (ms_k / 1e3) / 1e9 / peak}
+                            for k, (ms_k, b_k) in per_launch.items()},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": stage_traffic(dom, n), "bytes_per_key": dom_b,

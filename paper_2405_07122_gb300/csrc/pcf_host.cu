@@ -15,6 +15,8 @@
 #include <map>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pcfsort.h"
 #include "pcf_internal.h"
 
@@ -161,6 +163,15 @@ pcf_status cuda_fail(pcf_ctx* c, cudaError_t e) {
     cudaError_t e_ = (expr);                        \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
   } while (0)
+
+// NVTX range over a scope (a profiler's timeline shows the sort's levels
+// and stages; without a tool attached it costs a few nanoseconds)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Test hook: the allocation that many device allocations from now fails
 // (host side, as cudaMalloc would report exhausted memory); -1: never.
@@ -464,6 +475,7 @@ uint32_t tiles_of(uint64_t n, uint32_t tile) { return (uint32_t)((n + tile - 1) 
 pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> work, uint64_t* C,
                         uint32_t* Cv, uint64_t* D, uint32_t* Dv, uint64_t* out_k, uint32_t* out_v,
                         uint32_t* tile_counter, uint64_t spin_limit) {
+  NvtxRange nvtx_fb("pcf fallback");
   const cudaStream_t st = lc.stream;
   const uint64_t kv = lc.pairs ? 12 : 8;  // bytes per key (+ value)
   for (uint32_t round = 0; !work.empty(); ++round) {
@@ -634,6 +646,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                     uint32_t* out_v, const std::vector<InSeg>& user, uint32_t kt, bool pairs,
                     cudaStream_t st, uint32_t scan_withhold = 0xFFFFFFFFu,
                     uint64_t spin_limit = kSpinLimit) {
+  NvtxRange nvtx_sort("pcf sort");
   ctx->stats = pcf_call_stats{};
   for (int i = 0; i < 8; ++i) ctx->stage_ms[i] = 0;
   uint64_t n_total = 0;
@@ -794,6 +807,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   }
   bool first = true;
   while (L.S) {
+    NvtxRange nvtx_level(first ? "pcf level 0" : "pcf level");
     const uint32_t S = L.S;
     const uint64_t n_level = L.n_level;
     ctx->stats.levels += 1;
