@@ -182,6 +182,48 @@ pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_keys_out,
                                      const uint64_t* d_offsets, uint32_t S, uint64_t n_total,
                                      pcf_key_type kt, uint64_t seed, void* stream);
 
+/* A batched sort captured in a CUDA graph (the batched form: one graph
+ * launch runs the whole sort of pcf_sort_segmented -- every level's kernels,
+ * copies and memsets -- with no host round trip inside).
+ *
+ * pcf_graph_create sorts the buffers once as pcf_sort_segmented would
+ * (d_keys_in -> d_keys_out, segments h_offsets, seed + s for segment s,
+ * the policy and tuning of `like`, copied), keeping the host's decision at
+ * the end of each global level: the next level's plan and the buckets sent
+ * to the standard sort.  It then captures the same sort into a graph.  The
+ * graph keeps the buffer addresses and the segments; its own context owns
+ * the scratch (about what pcf_sort_segmented would use; `like` is not
+ * used after the call).  Out of place only: the key (and value) buffers in
+ * and out must not overlap, and the graph never writes the input.
+ *
+ * pcf_graph_launch sorts the CURRENT contents of d_keys_in into d_keys_out
+ * and returns when they are sorted.  It replays the graph; a guard kernel
+ * at each level's end compares the device's own plan with the recorded one,
+ * and on a difference every later kernel of the graph returns at once and
+ * the call sorts the input again without the graph, keeping the new plan
+ * and capturing again (*replayed = 0).  The output is the same either way
+ * (the unique sorted order).  A sort whose recording sent buckets to the
+ * standard sort (duplicate-heavy input; its rounds are planned on the host)
+ * is not captured: its launches sort without the graph.
+ *
+ * Errors as pcf_sort_segmented (a NaN key: PCF_ERR_INVALID_KEY, output not
+ * written).  One graph must not be launched from two threads at once. */
+typedef struct pcf_graph pcf_graph;
+pcf_status pcf_graph_create(pcf_graph** out, const pcf_ctx* like, const void* d_keys_in,
+                            const uint32_t* d_vals_in, void* d_keys_out, uint32_t* d_vals_out,
+                            const uint64_t* h_offsets, uint32_t S, pcf_key_type kt,
+                            uint64_t seed, void* stream);
+/* replayed (may be NULL): 1 when the graph did the sort, 0 when it ran
+ * without the graph */
+pcf_status pcf_graph_launch(pcf_graph* g, void* stream, int* replayed);
+/* captured: whether the graph holds a capture; replays / eager_runs: the
+ * launches it replayed, the sorts it ran without the graph (creation
+ * included).  Any output pointer may be NULL. */
+pcf_status pcf_graph_info(const pcf_graph* g, int* captured, uint64_t* replays,
+                          uint64_t* eager_runs);
+/* Frees the graph and its context.  NULL is accepted. */
+pcf_status pcf_graph_destroy(pcf_graph* g);
+
 /* End-to-end form on HOST buffers: copies h_keys (n keys, ideally pinned)
  * to the device, sorts, and copies the result back into h_keys. */
 pcf_status pcf_sort_keys_host(pcf_ctx* ctx, void* h_keys, uint64_t n, pcf_key_type kt,

@@ -66,7 +66,9 @@ __device__ __forceinline__ uint32_t merge_path(const uint64_t* L, uint32_t nL, c
 __global__ void __launch_bounds__(256) k_fb_range(const FbItem* items, uint32_t n_items,
                                                   const uint32_t* tile_base,
                                                   const uint64_t* __restrict__ keys, uint32_t kt,
-                                                  uint64_t* ord_lohi) {
+                                                  uint64_t* ord_lohi,
+                                                  const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t t = blockIdx.x;
   const uint32_t i = ub_dev(tile_base, n_items + 1, t) - 1;
   const FbItem it = items[i];
@@ -93,7 +95,9 @@ template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_fb_block_sort(const FbItem* items, uint32_t n_items,
                                                        const uint32_t* tile_base,
                                                        const uint64_t* ord_lohi, uint64_t* keys,
-                                                       uint32_t* vals, uint32_t kt) {
+                                                       uint32_t* vals, uint32_t kt,
+                                                       const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   __shared__ uint64_t sk[2][kMergeTile];
   __shared__ uint32_t sv[PAIRS ? 2 : 1][PAIRS ? kMergeTile : 1];
   const uint32_t t = blockIdx.x;
@@ -167,7 +171,9 @@ __global__ void __launch_bounds__(256) k_fb_merge(const FbItem* items, uint32_t 
                                                   const uint64_t* ord_lohi, uint64_t w,
                                                   const uint64_t* __restrict__ src, uint64_t* dst,
                                                   const uint32_t* __restrict__ src_v,
-                                                  uint32_t* dst_v, uint32_t kt) {
+                                                  uint32_t* dst_v, uint32_t kt,
+                                                  const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   __shared__ uint64_t sk[kMergeTile];
   __shared__ uint32_t sv[PAIRS ? kMergeTile : 1];
   __shared__ uint32_t s_split[2];
@@ -228,7 +234,9 @@ __global__ void __launch_bounds__(256) k_fb_copy(const FbItem* items, uint32_t n
                                                  const uint64_t* ord_lohi, const uint64_t* src,
                                                  uint64_t* dst, const uint32_t* src_v,
                                                  uint32_t* dst_v, const uint64_t* orig,
-                                                 const uint32_t* orig_v) {
+                                                 const uint32_t* orig_v,
+                                                 const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t t = blockIdx.x;
   const uint32_t i = ub_dev(tile_base, n_items + 1, t) - 1;
   if (ord_lohi && ord_lohi[2 * i] == ord_lohi[2 * i + 1]) {  // never moved: copy from there
@@ -256,7 +264,9 @@ __global__ void __launch_bounds__(kModeSample) k_fb_mode(const FbItem* items, ui
                                                          const uint64_t* __restrict__ keys,
                                                          uint32_t kt,
                                                          const uint64_t* ord_lohi,
-                                                         uint64_t* pivot, uint32_t* dom) {
+                                                         uint64_t* pivot, uint32_t* dom,
+                                                         const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   __shared__ uint64_t s[kModeSample];
   __shared__ uint32_t best_c[kModeSample / 32];
   __shared__ uint64_t best_v[kModeSample / 32];
@@ -264,7 +274,10 @@ __global__ void __launch_bounds__(kModeSample) k_fb_mode(const FbItem* items, ui
   if (i >= n_items) return;
   const FbItem it = items[i];
   if (it.n < 2 || ord_lohi[2 * i] == ord_lohi[2 * i + 1]) {  // one value: nothing to split
-    if (t == 0) dom[i] = 0;
+    if (t == 0) {
+      dom[i] = 0;
+      pivot[i] = 0;  // defined, so that a replayed sort graph can compare it
+    }
     return;
   }
   s[t] = ord_of(__ldg(keys + it.off + (uint64_t)t * it.n / kModeSample), kt);
@@ -311,7 +324,9 @@ __global__ void __launch_bounds__(256) k_fb_part_count(const FbItem* items, uint
                                                        const uint64_t* __restrict__ keys,
                                                        uint32_t kt, const uint64_t* pivot,
                                                        uint32_t* cnt,
-                                                       unsigned long long* item_cnt) {
+                                                       unsigned long long* item_cnt,
+                                                       const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   __shared__ uint32_t s3[3];
   const uint32_t t = blockIdx.x;
   const uint32_t i = fb_item_of(mtile_base, n_items, t);
@@ -355,7 +370,9 @@ __global__ void __launch_bounds__(256) k_fb_part_scatter(const FbItem* items, ui
                                                          const uint32_t* __restrict__ vals,
                                                          uint32_t kt, const uint64_t* pivot,
                                                          const uint32_t* cnt_ex, uint64_t* dst,
-                                                         uint32_t* dst_v) {
+                                                         uint32_t* dst_v,
+                                                         const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   static_assert(kMergeTile == 256 * 8, "one tile is 256 threads x 8 keys");
   __shared__ uint64_t sh8[8];
   const uint32_t t = blockIdx.x;
@@ -412,7 +429,8 @@ cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_
                             const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
                             uint64_t* ord_lohi) {
   if (!n_tiles) return cudaSuccess;
-  k_fb_range<<<n_tiles, 256, 0, c.stream>>>(items, n_items, tile_base, keys, c.kt, ord_lohi);
+  k_fb_range<<<n_tiles, 256, 0, c.stream>>>(items, n_items, tile_base, keys, c.kt, ord_lohi,
+                                            c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -425,10 +443,10 @@ cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_i
   if (!n_mtiles) return cudaSuccess;
   if (c.pairs) {
     k_fb_block_sort<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi,
-                                                          keys, vals, c.kt);
+                                                          keys, vals, c.kt, c.status);
   } else {
     k_fb_block_sort<false><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi,
-                                                           keys, vals, c.kt);
+                                                           keys, vals, c.kt, c.status);
   }
   count_launch(c);
   cudaError_t e = cudaGetLastError();
@@ -440,10 +458,10 @@ cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_i
   for (uint64_t w = kMergeTile; w < max_n; w *= 2) {
     if (c.pairs) {
       k_fb_merge<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi, w, A,
-                                                       B, Av, Bv, c.kt);
+                                                       B, Av, Bv, c.kt, c.status);
     } else {
       k_fb_merge<false><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi, w, A,
-                                                        B, Av, Bv, c.kt);
+                                                        B, Av, Bv, c.kt, c.status);
     }
     count_launch(c);
     if ((e = cudaGetLastError())) return e;
@@ -458,10 +476,11 @@ cudaError_t launch_fb_sort(const LaunchCfg& c, const FbItem* items, uint32_t n_i
   if (A != final_k || keys != final_k) {
     if (c.pairs) {
       k_fb_copy<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi, A,
-                                                      final_k, Av, final_v, keys, vals);
+                                                      final_k, Av, final_v, keys, vals, c.status);
     } else {
       k_fb_copy<false><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, ord_lohi, A,
-                                                       final_k, nullptr, nullptr, keys, nullptr);
+                                                       final_k, nullptr, nullptr, keys, nullptr,
+                                                       c.status);
     }
     count_launch(c);
     if ((e = cudaGetLastError())) return e;
@@ -475,10 +494,11 @@ cudaError_t launch_fb_move(const LaunchCfg& c, const FbItem* items, uint32_t n_i
   if (!n_mtiles || src == dst) return cudaSuccess;
   if (c.pairs)
     k_fb_copy<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, nullptr, src, dst,
-                                                    src_v, dst_v, nullptr, nullptr);
+                                                    src_v, dst_v, nullptr, nullptr, c.status);
   else
     k_fb_copy<false><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, nullptr, src,
-                                                     dst, nullptr, nullptr, nullptr, nullptr);
+                                                     dst, nullptr, nullptr, nullptr, nullptr,
+                                                     c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -488,7 +508,7 @@ cudaError_t launch_fb_mode(const LaunchCfg& c, const FbItem* items, uint32_t n_i
                            uint32_t* dom) {
   if (!n_items) return cudaSuccess;
   k_fb_mode<<<n_items, kModeSample, 0, c.stream>>>(items, n_items, keys, c.kt, ord_lohi, pivot,
-                                                   dom);
+                                                   dom, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -500,7 +520,7 @@ cudaError_t launch_fb_part_count(const LaunchCfg& c, const FbItem* items, uint32
   if (!n_mtiles) return cudaSuccess;
   k_fb_part_count<<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, n_mtiles, keys,
                                                   c.kt, pivot, cnt,
-                                                  (unsigned long long*)item_cnt);
+                                                  (unsigned long long*)item_cnt, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -514,11 +534,11 @@ cudaError_t launch_fb_part_scatter(const LaunchCfg& c, const FbItem* items, uint
   if (c.pairs)
     k_fb_part_scatter<true><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base, n_mtiles,
                                                             keys, vals, c.kt, pivot, cnt_ex, dst,
-                                                            dst_v);
+                                                            dst_v, c.status);
   else
     k_fb_part_scatter<false><<<n_mtiles, 256, 0, c.stream>>>(items, n_items, mtile_base,
                                                              n_mtiles, keys, vals, c.kt, pivot,
-                                                             cnt_ex, dst, dst_v);
+                                                             cnt_ex, dst, dst_v, c.status);
   count_launch(c);
   return cudaGetLastError();
 }

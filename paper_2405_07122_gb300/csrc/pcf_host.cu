@@ -177,9 +177,15 @@ struct NvtxRange {
 // (host side, as cudaMalloc would report exhausted memory); -1: never.
 thread_local int64_t g_fail_alloc_after = -1;
 
+// Set while this thread captures a sort graph: the capture reuses the
+// buffers of the run it replays, and a buffer that would have to grow
+// fails the capture instead (an allocation is not a stream operation).
+thread_local bool g_capturing = false;
+
 cudaError_t ensure(DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return cudaSuccess;
+  if (g_capturing) return cudaErrorStreamCaptureUnsupported;
   if (g_fail_alloc_after >= 0 && g_fail_alloc_after-- == 0) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
@@ -209,6 +215,7 @@ cudaError_t ensure(DevBuf& b, size_t bytes) {
 cudaError_t ensure_host(HostBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return cudaSuccess;
+  if (g_capturing) return cudaErrorStreamCaptureUnsupported;
   if (b.p) cudaFreeHost(b.p);
   b.p = nullptr;
   b.cap = 0;
@@ -464,6 +471,40 @@ constexpr uint32_t kSplitRounds = 8;
 
 uint32_t tiles_of(uint64_t n, uint32_t tile) { return (uint32_t)((n + tile - 1) / tile); }
 
+// A sort's host decisions, for a CUDA graph of the same sort.  Everything
+// the host launches follows from the segment sizes and from what it reads
+// back: at each global level's end the next level's plan (device built) and
+// the buckets sent to the standard sort; in each round of that sort the
+// items' ranges, pivots and split decisions and the sizes of the split
+// parts.  RUN_RECORD keeps those read-backs; RUN_CAPTURE launches the same
+// work from them without reading back (for stream capture), with a guard
+// kernel in place of each read-back that compares the device's value with
+// the kept one and sets STATUS_REPLAN on a difference.
+enum RunMode { RUN_EAGER = 0, RUN_RECORD = 1, RUN_CAPTURE = 2 };
+enum { FB_LOHI = 0, FB_PIVOT = 1, FB_DOM = 2, FB_PART = 3 };
+struct FbRound {
+  std::vector<uint8_t> got[4];  // the round's read-backs (FB_*), as read
+};
+struct SortRecord {
+  std::vector<LevelOut> levels;
+  std::vector<std::vector<FbItem>> fb_lists;  // each standard-sort list, by offset
+  std::vector<FbRound> rounds;                // every round of those sorts, in order
+  size_t arena_bytes = 0;                     // the rounds' host-to-device staging
+};
+// A capture's view of a recording: the read-backs, their device copy (one
+// blob: the level records, the lists, the rounds' buffers) and a pinned
+// arena for the rounds' uploads, never reused within the capture (the
+// graph's copies read it at every replay).
+struct Replay {
+  const SortRecord* rec = nullptr;
+  const uint8_t* d_blob = nullptr;
+  size_t levels_at = 0;
+  std::vector<size_t> list_at;
+  std::vector<std::vector<size_t>> round_at;  // [round][FB_*]
+  HostBuf* arena = nullptr;
+  size_t arena_off = 0, next_list = 0, next_round = 0;
+};
+
 // The standard sort of one level's fallback items (failure-guard buckets,
 // |c| >= delta, and degenerate ones), keys in C, scratch D (both free at
 // the items' offsets), result in out.  Per round: the range of every item
@@ -474,13 +515,24 @@ uint32_t tiles_of(uint64_t n, uint32_t tile) { return (uint32_t)((n + tile - 1) 
 // throughout, so the pair sorts stay stable.
 pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> work, uint64_t* C,
                         uint32_t* Cv, uint64_t* D, uint32_t* Dv, uint64_t* out_k, uint32_t* out_v,
-                        uint32_t* tile_counter, uint64_t spin_limit) {
+                        uint32_t* tile_counter, uint64_t spin_limit, RunMode mode = RUN_EAGER,
+                        SortRecord* rec = nullptr, Replay* rp = nullptr) {
   NvtxRange nvtx_fb("pcf fallback");
   const cudaStream_t st = lc.stream;
+  const bool capture = mode == RUN_CAPTURE;
   const uint64_t kv = lc.pairs ? 12 : 8;  // bytes per key (+ value)
   for (uint32_t round = 0; !work.empty(); ++round) {
     const uint32_t nf = (uint32_t)work.size();
     const bool try_split = round < kSplitRounds;
+    FbRound* rr = nullptr;  // this round's record (RUN_RECORD)
+    size_t rno = 0;         // ... or its recording (RUN_CAPTURE)
+    if (mode == RUN_RECORD) {
+      rec->rounds.emplace_back();
+      rr = &rec->rounds.back();
+    } else if (capture) {
+      rno = rp->next_round++;
+      if (rno >= rp->rec->rounds.size()) return PCF_ERR_INTERNAL;
+    }
     // device layout of the round: items | sort items | split items | done
     // items (at most three parts per split item)
     CK(ensure(ctx->fb_items, (size_t)6 * nf * sizeof(FbItem)));
@@ -505,22 +557,47 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
     CK(ensure_host(ctx->h_fb, (size_t)256 * nf + 1024));
     size_t aoff = 0;
     auto put = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+      const size_t step = (bytes + 15) & ~(size_t)15;
+      if (mode == RUN_RECORD) rec->arena_bytes += step;
+      if (capture) {  // the capture's own arena, one slice per upload
+        if (rp->arena_off + step > rp->arena->cap) return cudaErrorInvalidValue;
+        char* h = (char*)rp->arena->p + rp->arena_off;
+        rp->arena_off += step;
+        memcpy(h, src, bytes);
+        return launch_xfer(st, dst, dview(*rp->arena, h), bytes);
+      }
       char* h = (char*)ctx->h_fb.p + aoff;
       memcpy(h, src, bytes);
-      aoff += (bytes + 15) & ~(size_t)15;
+      aoff += step;
       return launch_xfer(st, dst, dview(ctx->h_fb, h), bytes);
     };
     std::vector<std::pair<void*, std::pair<const char*, size_t>>> gets;
-    auto get = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    std::vector<std::pair<int, std::pair<const void*, size_t>>> kept;  // (FB_*, host copy)
+    // a read-back: copied to the host (kind >= 0: kept when recording), or,
+    // in a capture, the recorded value with a guard against the device's
+    auto get = [&](void* dst, const void* src, size_t bytes, int kind) -> cudaError_t {
+      if (capture) {
+        const std::vector<uint8_t>& v = rp->rec->rounds[rno].got[kind];
+        if (v.size() != bytes) return cudaErrorInvalidValue;
+        memcpy(dst, v.data(), bytes);
+        return launch_guard_words(lc, src, rp->d_blob + rp->round_at[rno][kind], bytes / 4);
+      }
       char* h = (char*)ctx->h_fb.p + aoff;
       aoff += (bytes + 15) & ~(size_t)15;
       gets.push_back({dst, {h, bytes}});
+      if (mode == RUN_RECORD && kind >= 0) kept.push_back({kind, {dst, bytes}});
       return launch_xfer(st, dview(ctx->h_fb, h), src, bytes);
     };
+    auto sync = [&]() -> cudaError_t { return capture ? cudaSuccess : cudaStreamSynchronize(st); };
     // after a synchronisation: the gets land in their host vectors
     auto land = [&]() {
       for (auto& g : gets) memcpy(g.first, g.second.first, g.second.second);
       gets.clear();
+      for (auto& k : kept) {
+        const uint8_t* b = (const uint8_t*)k.second.first;
+        rr->got[k.first].assign(b, b + k.second.second);
+      }
+      kept.clear();
     };
 
     std::vector<uint32_t> rb(nf + 1, 0);
@@ -537,12 +614,12 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
     std::vector<uint64_t> pivot(nf, 0);
     std::vector<uint32_t> dom(nf, 0);
     if (try_split) CK(launch_fb_mode(lc, d_items, nf, C, d_lohi, d_pivot, d_dom));
-    CK(get(lohi.data(), d_lohi, nf * 16));
+    CK(get(lohi.data(), d_lohi, nf * 16, FB_LOHI));
     if (try_split) {
-      CK(get(pivot.data(), d_pivot, nf * 8));
-      CK(get(dom.data(), d_dom, nf * 4));
+      CK(get(pivot.data(), d_pivot, nf * 8, FB_PIVOT));
+      CK(get(dom.data(), d_dom, nf * 4, FB_DOM));
     }
-    CK(cudaStreamSynchronize(st));
+    CK(sync());
     land();
 
     std::vector<FbItem> sw_items, sp_items;
@@ -595,9 +672,9 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
       CK(launch_fb_part_scatter(lc, d_items_p, np, d_mb_p, mp, C, Cv, d_piv_p, cnt, D, Dv));
       std::vector<uint64_t> part(3 * (size_t)np);
       uint32_t stw = 0;
-      CK(get(part.data(), d_item_cnt, (size_t)np * 24));
-      CK(get(&stw, lc.status, 4));
-      CK(cudaStreamSynchronize(st));
+      CK(get(part.data(), d_item_cnt, (size_t)np * 24, FB_PART));
+      if (!capture) CK(get(&stw, lc.status, 4, -1));
+      CK(sync());
       land();
       if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
       // the parts: below and above go round again (unless they are too short
@@ -630,7 +707,7 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
         CK(launch_fb_move(lc, d_items_d, nd, d_mb_d, mb_d[nd], D, out_k, Dv, out_v));
       }
     }
-    CK(cudaStreamSynchronize(st));
+    CK(sync());
     work.swap(next);
     std::swap(C, D);
     std::swap(Cv, Dv);
@@ -642,10 +719,12 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
 // The whole sort of a batch of arrays.  Level-0 segments are the caller's
 // arrays; keys flow src -> tmp (pass 1) -> out (pass 2); leaf buckets are
 // finished in place in out; fallback buckets are merge-sorted in out.
+// mode / rec / rp: see SortRecord and Replay.
 pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, uint64_t* out_k,
                     uint32_t* out_v, const std::vector<InSeg>& user, uint32_t kt, bool pairs,
                     cudaStream_t st, uint32_t scan_withhold = 0xFFFFFFFFu,
-                    uint64_t spin_limit = kSpinLimit) {
+                    uint64_t spin_limit = kSpinLimit, RunMode mode = RUN_EAGER,
+                    SortRecord* rec = nullptr, Replay* rp = nullptr) {
   NvtxRange nvtx_sort("pcf sort");
   ctx->stats = pcf_call_stats{};
   for (int i = 0; i < 8; ++i) ctx->stage_ms[i] = 0;
@@ -682,8 +761,9 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   Timer tm(ctx, st);
   tm.mark(-1);
 
-  // NaN check of everything first; every writer below is skipped on NaN by
-  // the host before launch.
+  // NaN check of every key by the range passes (the small arrays' here,
+  // the others' at level 0); every later kernel is gated on the status word
+  // (pcf_aborted), so none writes once a NaN is seen.
   std::vector<InSeg> small, big;
   for (auto& s : user) {
     if (s.n == 0) continue;
@@ -712,7 +792,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   }
 
   // ---- level 0 of the small arrays: straight to the shared-memory kernel,
-  // launched once the NaN check of every key has passed
+  // launched after the range passes that check every key for NaN (and gated
+  // on their flag)
   auto launch_small = [&]() -> pcf_status {
     if (small.empty()) return PCF_OK;
     const uint32_t S = (uint32_t)small.size();
@@ -738,11 +819,6 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     return PCF_OK;
   };
   if (big.empty()) {
-    if (kt == KEY_F64) {
-      CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
-      CK(cudaStreamSynchronize(st));
-      if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
-    }
     pcf_status r = launch_small();
     if (r != PCF_OK) return r;
     tm.mark(6);
@@ -806,6 +882,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     L.dp = dev_plan(pbuf[cur]->p, PL);
   }
   bool first = true;
+  size_t level_no = 0;
   while (L.S) {
     NvtxRange nvtx_level(first ? "pcf level 0" : "pcf level");
     const uint32_t S = L.S;
@@ -821,15 +898,10 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
 
     // range, model.  NaN keys (level 0, binary64) are flagged by the full
     // range pass, or with a sample range by k_hist1 and the range pass of
-    // the segments that need one; either way before any output is written
+    // the segments that need one; either way before any kernel that writes
+    // the output runs (those are gated on the flag)
     const bool srange = lc.range_mode == RANGE_SAMPLE;
     const bool check_nan = first && kt == KEY_F64;
-    auto nan_gate = [&]() -> pcf_status {
-      CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
-      CK(cudaStreamSynchronize(st));
-      if (*(uint32_t*)ctx->h_status.p & STATUS_NAN) return PCF_ERR_INVALID_KEY;
-      return launch_small();
-    };
     if (srange) {
       // the samples' range; the array's where it is equal or degenerate (R14)
       CK(launch_sample_range(lc, d_segs, S, L.dp.k1, L.n_k1, src));
@@ -839,7 +911,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     } else {
       CK(launch_range(lc, d_segs, S, L.dp.rb, L.n_range, src, check_nan));
       if (first) {
-        const pcf_status r = check_nan ? nan_gate() : launch_small();
+        const pcf_status r = launch_small();
         if (r != PCF_OK) return r;
       }
       CK(launch_model(lc, d_segs, S));
@@ -900,7 +972,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                     as<uint32_t>(ctx->cmat1), L.dmax1, as<uint32_t>(ctx->jbuf),
                     srange && check_nan));
     if (late_gate) {
-      const pcf_status r = check_nan ? nan_gate() : launch_small();
+      const pcf_status r = launch_small();
       if (r != PCF_OK) return r;
       CK(copy_special());
     }
@@ -972,22 +1044,47 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                         ctx->policy, dbits, tile_keys, ndp, as<uint32_t>(ctx->pcols),
                         as<uint32_t>(ctx->pbsums), d_lo, as<uint64_t>(ctx->sw), tile_counter,
                         spin_limit, &totals[2]));
-    CK(launch_xfer(st, ctx->h_lout.dp, d_lo, sizeof(LevelOut)));
-    CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
-    CK(cudaStreamSynchronize(st));
-    const LevelOut lo = *(LevelOut*)ctx->h_lout.p;
-    const uint32_t stw = *(uint32_t*)ctx->h_status.p;
-    if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
-    if (stw & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
+    LevelOut lo;
+    if (mode == RUN_CAPTURE) {
+      if (level_no >= rp->rec->levels.size()) return PCF_ERR_INTERNAL;
+      const LevelOut* d_levels = (const LevelOut*)(rp->d_blob + rp->levels_at);
+      CK(launch_guard(lc, d_lo, d_levels + level_no));
+      lo = rp->rec->levels[level_no];
+    } else {
+      CK(launch_xfer(st, ctx->h_lout.dp, d_lo, sizeof(LevelOut)));
+      CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
+      CK(cudaStreamSynchronize(st));
+      lo = *(LevelOut*)ctx->h_lout.p;
+      const uint32_t stw = *(uint32_t*)ctx->h_status.p;
+      if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+      if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
+      if (stw & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
+      if (mode == RUN_RECORD) rec->levels.push_back(lo);
+    }
+    ++level_no;
     ctx->stats.leaf_buckets += lo.n_leaf;
     uint64_t level_fb_keys = 0;
-    // standard sort of the large failure-guard / degenerate buckets
+    // standard sort of the large failure-guard / degenerate buckets, in
+    // offset order (the device lists them in any order)
     if (lo.n_fb) {
-      std::vector<FbItem> items(lo.n_fb);
-      CK(ensure_host(ctx->h_fb, (size_t)lo.n_fb * sizeof(FbItem)));
-      CK(launch_xfer(st, ctx->h_fb.dp, ctx->fb.p, lo.n_fb * sizeof(FbItem)));
-      CK(cudaStreamSynchronize(st));
-      memcpy(items.data(), ctx->h_fb.p, lo.n_fb * sizeof(FbItem));
+      std::vector<FbItem> items;
+      if (mode == RUN_CAPTURE) {
+        const size_t li = rp->next_list++;
+        if (li >= rp->rec->fb_lists.size() || rp->rec->fb_lists[li].size() != lo.n_fb)
+          return PCF_ERR_INTERNAL;
+        items = rp->rec->fb_lists[li];
+        CK(launch_guard_list(lc, as<FbItem>(ctx->fb), (const FbItem*)(rp->d_blob + rp->list_at[li]),
+                             lo.n_fb));
+      } else {
+        items.resize(lo.n_fb);
+        CK(ensure_host(ctx->h_fb, (size_t)lo.n_fb * sizeof(FbItem)));
+        CK(launch_xfer(st, ctx->h_fb.dp, ctx->fb.p, lo.n_fb * sizeof(FbItem)));
+        CK(cudaStreamSynchronize(st));
+        memcpy(items.data(), ctx->h_fb.p, lo.n_fb * sizeof(FbItem));
+        std::sort(items.begin(), items.end(),
+                  [](const FbItem& a, const FbItem& b) { return a.off < b.off; });
+        if (mode == RUN_RECORD) rec->fb_lists.push_back(items);
+      }
       for (const FbItem& it : items) level_fb_keys += it.n;
       ctx->stats.fallback_keys += level_fb_keys;
       ctx->stats.fallback_buckets += lo.n_fb;
@@ -995,7 +1092,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       uint64_t* Y = (X == tmp_k) ? out_k : tmp_k;
       uint32_t* Yv = (X == tmp_k) ? out_v : tmp_v;
       const pcf_status fs = run_fallback(ctx, lc, std::move(items), X, Xv, Y, Yv, out_k, out_v,
-                                         tile_counter, spin_limit);
+                                         tile_counter, spin_limit, mode, rec, rp);
       if (fs != PCF_OK) return fs;
       tm.mark(7);
     }
@@ -1031,12 +1128,96 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     src_v = Xv;
     first = false;
   }
+  if (mode == RUN_CAPTURE) return PCF_OK;  // the replay reads the status word
   CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
   CK(cudaStreamSynchronize(st));
   const uint32_t stw = *(uint32_t*)ctx->h_status.p;
   if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
   if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
   if (stw & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
+  return PCF_OK;
+}
+
+}  // namespace
+
+// A sort captured in a CUDA graph: one graph launch replays every kernel,
+// copy and memset of the sort of fixed buffers and segments.  Its private
+// context owns the scratch the graph's nodes point at, so no other call
+// can move it.
+struct pcf_graph {
+  pcf_ctx* ctx = nullptr;
+  const uint64_t* in_k = nullptr;
+  const uint32_t* in_v = nullptr;
+  uint64_t* out_k = nullptr;
+  uint32_t* out_v = nullptr;
+  std::vector<InSeg> segs;
+  uint32_t kt = 0;
+  bool pairs = false;
+  SortRecord rec;
+  DevBuf d_blob;               // the recording's read-backs on the device, for the guards
+  HostBuf arena;               // the captured standard-sort rounds' uploads
+  cudaStream_t cs = nullptr;   // the stream captures run on
+  cudaGraphExec_t exec = nullptr;
+  uint64_t replays = 0, eager_runs = 0;
+  ~pcf_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+namespace {
+
+// Sorts the graph's input once without a graph, keeping its host decisions,
+// then captures the same sort from them.  If the capture fails the graph's
+// launches sort without it.
+pcf_status graph_build(pcf_graph* g, cudaStream_t st) {
+  pcf_ctx* ctx = g->ctx;
+  if (g->exec) {
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  g->rec = SortRecord{};
+  pcf_status r = run_sort(ctx, g->in_k, g->in_v, g->out_k, g->out_v, g->segs, g->kt, g->pairs, st,
+                          0xFFFFFFFFu, kSpinLimit, RUN_RECORD, &g->rec);
+  if (r != PCF_OK) {
+    cudaStreamSynchronize(st);
+    return r;
+  }
+  ++g->eager_runs;
+  // the read-backs the guards compare with, in one device blob
+  const SortRecord& rec = g->rec;
+  Replay rp;
+  rp.rec = &rec;
+  std::vector<uint8_t> blob;
+  auto add = [&](const void* p, size_t bytes) {
+    const size_t at = (blob.size() + 15) & ~(size_t)15;
+    blob.resize(at + bytes);
+    if (bytes) memcpy(blob.data() + at, p, bytes);
+    return at;
+  };
+  rp.levels_at = add(rec.levels.data(), rec.levels.size() * sizeof(LevelOut));
+  for (const auto& l : rec.fb_lists) rp.list_at.push_back(add(l.data(), l.size() * sizeof(FbItem)));
+  for (const FbRound& rd : rec.rounds) {
+    rp.round_at.emplace_back();
+    for (int k = 0; k < 4; ++k) rp.round_at.back().push_back(add(rd.got[k].data(), rd.got[k].size()));
+  }
+  CK(ensure(g->d_blob, blob.size() + 16));
+  CK(cudaMemcpy(g->d_blob.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  CK(ensure_host(g->arena, rec.arena_bytes + 64));
+  rp.d_blob = (const uint8_t*)g->d_blob.p;
+  rp.arena = &g->arena;
+  CK(cudaStreamBeginCapture(g->cs, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
+  r = run_sort(ctx, g->in_k, g->in_v, g->out_k, g->out_v, g->segs, g->kt, g->pairs, g->cs,
+               0xFFFFFFFFu, kSpinLimit, RUN_CAPTURE, nullptr, &rp);
+  g_capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(g->cs, &graph);
+  if (r == PCF_OK && e == cudaSuccess && graph &&
+      cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess)
+    g->exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();  // a failed capture leaves the graph eager, not the context broken
   return PCF_OK;
 }
 
@@ -1201,6 +1382,113 @@ pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_
   const bool pairs = d_vals_in != nullptr || d_vals_out != nullptr;
   return sort_common(ctx, d_keys_in, d_vals_in, d_keys_out, d_vals_out, segs, h_offsets[S], kt,
                      pairs, stream);
+}
+
+pcf_status pcf_graph_create(pcf_graph** out, const pcf_ctx* like, const void* d_keys_in,
+                            const uint32_t* d_vals_in, void* d_keys_out, uint32_t* d_vals_out,
+                            const uint64_t* h_offsets, uint32_t S, pcf_key_type kt, uint64_t seed,
+                            void* stream) {
+  if (!out) return PCF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!like || (!h_offsets && S)) return PCF_ERR_INVALID_ARG;
+  if (kt != PCF_KEY_F64 && kt != PCF_KEY_U64) return PCF_ERR_INVALID_ARG;
+  if (S && h_offsets[0] != 0) return PCF_ERR_INVALID_ARG;
+  std::vector<InSeg> segs;
+  segs.reserve(S);
+  for (uint32_t s = 0; s < S; ++s) {
+    if (h_offsets[s + 1] < h_offsets[s]) return PCF_ERR_INVALID_ARG;
+    segs.push_back(InSeg{h_offsets[s], h_offsets[s + 1] - h_offsets[s], 0, seed + s, 0});
+  }
+  const uint64_t n = S ? h_offsets[S] : 0;
+  const bool pairs = d_vals_in != nullptr || d_vals_out != nullptr;
+  if (n > 0xFFFFFFFFull) return PCF_ERR_INVALID_ARG;
+  if (n) {
+    if (!d_keys_in || !d_keys_out || (pairs && (!d_vals_in || !d_vals_out)))
+      return PCF_ERR_INVALID_ARG;
+    if (((uintptr_t)d_keys_in & 7) || ((uintptr_t)d_keys_out & 7)) return PCF_ERR_INVALID_ARG;
+    if (pairs && (((uintptr_t)d_vals_in & 3) || ((uintptr_t)d_vals_out & 3)))
+      return PCF_ERR_INVALID_ARG;
+    // out of place only: a replay whose plan no longer holds sorts the
+    // input again, so the graph must never write it
+    if (d_keys_in == d_keys_out || overlap(d_keys_in, d_keys_out, n * 8))
+      return PCF_ERR_INVALID_ARG;
+    if (pairs && (d_vals_in == d_vals_out || overlap(d_vals_in, d_vals_out, n * 4)))
+      return PCF_ERR_INVALID_ARG;
+  }
+  if (!policy_ok(like->policy)) return PCF_ERR_INVALID_ARG;
+  pcf_graph* g = new (std::nothrow) pcf_graph();
+  if (!g) return PCF_ERR_OOM;
+  pcf_status r = pcf_ctx_create(&g->ctx, like->device);
+  if (r != PCF_OK) {
+    delete g;
+    return r;
+  }
+  pcf_ctx* ctx = g->ctx;
+  ctx->policy = like->policy;
+  ctx->tuning = like->tuning;
+  g->in_k = (const uint64_t*)d_keys_in;
+  g->in_v = d_vals_in;
+  g->out_k = (uint64_t*)d_keys_out;
+  g->out_v = d_vals_out;
+  g->segs = std::move(segs);
+  g->kt = (uint32_t)kt;
+  g->pairs = pairs;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (!e) e = cudaStreamCreateWithFlags(&g->cs, cudaStreamNonBlocking);
+  if (e) {
+    r = cuda_fail(ctx, e);
+  } else {
+    r = graph_build(g, (cudaStream_t)stream);
+  }
+  if (r != PCF_OK) {
+    pcf_graph_destroy(g);
+    return r;
+  }
+  *out = g;
+  return PCF_OK;
+}
+
+pcf_status pcf_graph_launch(pcf_graph* g, void* stream, int* replayed) {
+  if (replayed) *replayed = 0;
+  if (!g) return PCF_ERR_INVALID_ARG;
+  pcf_ctx* ctx = g->ctx;
+  const cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device));
+  if (g->exec) {
+    CK(cudaGraphLaunch(g->exec, st));
+    CK(launch_xfer(st, ctx->h_status.dp, ctx->status.p, 4));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t stw = *(uint32_t*)ctx->h_status.p;
+    if (!(stw & STATUS_ABORT)) {
+      ++g->replays;
+      if (replayed) *replayed = 1;
+      return PCF_OK;
+    }
+    if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
+    if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
+    if (stw & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
+    // STATUS_REPLAN: this input takes another plan than the recorded one;
+    // the graph stopped at that level's end and left the input as it was
+  }
+  return graph_build(g, st);
+}
+
+pcf_status pcf_graph_info(const pcf_graph* g, int* captured, uint64_t* replays,
+                          uint64_t* eager_runs) {
+  if (!g) return PCF_ERR_INVALID_ARG;
+  if (captured) *captured = g->exec != nullptr;
+  if (replays) *replays = g->replays;
+  if (eager_runs) *eager_runs = g->eager_runs;
+  return PCF_OK;
+}
+
+pcf_status pcf_graph_destroy(pcf_graph* g) {
+  if (!g) return PCF_OK;
+  pcf_ctx* ctx = g->ctx;
+  if (ctx) cudaSetDevice(ctx->device);
+  delete g;  // the graph and its stream before the context's buffers
+  pcf_ctx_destroy(ctx);
+  return PCF_OK;
 }
 
 pcf_status pcf_sort_keys_host(pcf_ctx* ctx, void* h_keys, uint64_t n, pcf_key_type kt,

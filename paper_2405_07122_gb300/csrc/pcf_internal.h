@@ -14,7 +14,20 @@ enum : uint32_t {
   STATUS_TIMEOUT = 2u,   // a bounded wait gave up
   STATUS_INTERNAL = 4u,  // an internal capacity check failed
   STATUS_BOUNDS = 8u,    // a checked build caught an index out of bounds
+  STATUS_REPLAN = 16u,   // a replayed sort graph met a plan other than its recording
+  STATUS_ABORT = STATUS_NAN | STATUS_TIMEOUT | STATUS_INTERNAL | STATUS_BOUNDS | STATUS_REPLAN,
 };
+
+// The device-side gate of a sort: each kernel of a level returns before any
+// other access once the status word holds an abort bit (a NaN key, a failed
+// wait or check, a replayed graph whose plan no longer holds).  Nothing is
+// written after the sort has failed, with no host round trip between the
+// range pass that finds a NaN and the kernels that write the output.  The
+// word changes only between launches (or, for NaN and timeouts, inside the
+// launch that finds them), and kernel boundaries order it.
+__device__ __forceinline__ bool pcf_aborted(const uint32_t* status) {
+  return status && (*reinterpret_cast<const volatile uint32_t*>(status) & STATUS_ABORT) != 0;
+}
 
 // SEG_NEEDRANGE: the samples' range (R14) was equal or degenerate; the
 // array's own range decides
@@ -183,6 +196,12 @@ constexpr uint32_t kScanTile = 4096;    // entries per decoupled-lookback tile
 constexpr uint32_t kMergeTile = 2048;   // keys per block-sorted run
 constexpr uint32_t kMaxDigitBits = 12;
 
+// a replayed graph's end-of-level check against its recording (STATUS_REPLAN)
+cudaError_t launch_guard(const LaunchCfg& c, const LevelOut* dev, const LevelOut* rec);
+cudaError_t launch_guard_list(const LaunchCfg& c, const FbItem* dev, const FbItem* rec,
+                              uint32_t n);
+cudaError_t launch_guard_words(const LaunchCfg& c, const void* dev, const void* rec,
+                               uint64_t n_words);
 // only_status: reduce only the segments in that status (~0u: all)
 cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* range_base,
                          uint32_t n_tiles, const uint64_t* keys, bool check_nan,

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(256) k_range(Seg* segs, uint32_t S, const uint
                                                const uint64_t* __restrict__ keys, uint32_t kt,
                                                int check_nan, uint32_t* status,
                                                uint32_t only_status) {
+  if (pcf_aborted(status)) return;
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(range_base, S + 1, t) - 1;
   if (only_status != ~0u && segs[s].status != only_status) return;
@@ -106,7 +107,9 @@ __global__ void __launch_bounds__(256) k_range(Seg* segs, uint32_t S, const uint
 // ---------------------------------------------------------------------------
 // k_model: Alg. 1's early exits and the bin constants
 // ---------------------------------------------------------------------------
-__global__ void k_model(Seg* segs, uint32_t S, uint32_t kt, uint32_t model, uint32_t pass) {
+__global__ void k_model(Seg* segs, uint32_t S, uint32_t kt, uint32_t model, uint32_t pass,
+                        const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   Seg& g = segs[s];
@@ -137,7 +140,8 @@ __global__ void k_model(Seg* segs, uint32_t S, uint32_t kt, uint32_t model, uint
 __global__ void __launch_bounds__(256) k_sample_range(Seg* segs, uint32_t S,
                                                       const uint32_t* k1_base,
                                                       const uint64_t* __restrict__ keys,
-                                                      uint32_t kt) {
+                                                      uint32_t kt, const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t c = blockIdx.x;
   const uint32_t s = upper_bound_dev(k1_base, S + 1, c) - 1;
   Seg& g = segs[s];
@@ -202,7 +206,8 @@ __device__ __forceinline__ T block_excl_scan256(T v, T* sh8, T* total) {
 __global__ void __launch_bounds__(256) k_sample(const Seg* segs, uint32_t S,
                                                 const uint32_t* k1_base,
                                                 const uint64_t* __restrict__ keys, uint32_t kt,
-                                                uint32_t* tpool) {
+                                                uint32_t* tpool, const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t c = blockIdx.x;
   const uint32_t s = upper_bound_dev(k1_base, S + 1, c) - 1;
   const Seg& g = segs[s];
@@ -222,7 +227,8 @@ __global__ void __launch_bounds__(256) k_sample(const Seg* segs, uint32_t S,
 }
 
 // tbase of each segment: the inclusive pool scan just before its table
-__global__ void k_seg_base(Seg* segs, uint32_t S, const uint32_t* tpool) {
+__global__ void k_seg_base(Seg* segs, uint32_t S, const uint32_t* tpool, const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const uint64_t o = segs[s].T_off;
@@ -314,6 +320,7 @@ __global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
                                                const uint32_t* __restrict__ tpool,
                                                uint32_t* cmat, uint32_t* __restrict__ jout,
                                                int check_nan, uint32_t* status) {
+  if (pcf_aborted(status)) return;
   extern __shared__ uint32_t hist[];
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
@@ -384,6 +391,9 @@ __global__ void __launch_bounds__(256) k_scan(uint32_t* data, uint64_t n, const 
   __shared__ uint32_t s_tile, s_prefix;
   __shared__ uint32_t sh8[8];
   __shared__ uint32_t buf[kScanTile];
+  // gated before taking a tile: the tiles no CTA takes are the last ones,
+  // which no taken tile waits on
+  if (pcf_aborted(status)) return;
   if (n_dev) n = *n_dev;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
   __syncthreads();
@@ -638,6 +648,7 @@ __global__ void __launch_bounds__(256, 2) k_scatter1(const Seg* segs, uint32_t S
                                                   KeyBufs kb, const uint32_t* __restrict__ tpool,
                                                   const uint32_t* __restrict__ cmat,
                                                   uint32_t* status) {
+  if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
@@ -662,7 +673,9 @@ __global__ void __launch_bounds__(256, 2) k_scatter1(const Seg* segs, uint32_t S
 // ---------------------------------------------------------------------------
 __global__ void k_groups(const Seg* segs, uint32_t S, const uint64_t* group_base_dev,
                          uint64_t n_groups, const uint32_t* cmat1, uint32_t tile_keys,
-                         Group* groups, uint32_t* g_tiles, uint32_t* g_centries) {
+                         Group* groups, uint32_t* g_tiles, uint32_t* g_centries,
+                         const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint64_t G = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (G >= n_groups) return;
   const uint32_t s = upper_bound_dev(group_base_dev, S + 1, G) - 1;
@@ -694,7 +707,9 @@ __global__ void k_groups(const Seg* segs, uint32_t S, const uint64_t* group_base
 }
 
 // cbase of every group from the scanned entry counts
-__global__ void k_group_bases(Group* groups, uint64_t n_groups, const uint32_t* g_centries_scan) {
+__global__ void k_group_bases(Group* groups, uint64_t n_groups, const uint32_t* g_centries_scan,
+                              const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint64_t G = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (G >= n_groups) return;
   groups[G].cbase = g_centries_scan[G];
@@ -707,7 +722,8 @@ __global__ void __launch_bounds__(256) k_hist2(const Group* groups, uint32_t n_g
                                                const Seg* segs, const uint32_t* g_tile_scan,
                                                const uint64_t* total_tiles, uint32_t tile_keys,
                                                const uint16_t* __restrict__ aux,
-                                               uint32_t* cmat2) {
+                                               uint32_t* cmat2, const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   extern __shared__ uint32_t hist[];
   const uint32_t t = blockIdx.x;
   if (t >= *total_tiles) return;
@@ -746,6 +762,7 @@ __global__ void __launch_bounds__(256, 2) k_scatter2(const Group* groups, uint32
                                                   const uint64_t* total_tiles, uint32_t tile_keys,
                                                   KeyBufs kb, const uint32_t* __restrict__ cmat2,
                                                   uint32_t* status) {
+  if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t t = blockIdx.x;
   if (t >= *total_tiles) return;
@@ -794,6 +811,7 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
                                                  uint32_t* out_v, BRec* brec, uint32_t* next_flag,
                                                  FbItem* fb, LevelOut* lo, uint32_t max_items,
                                                  uint32_t* status) {
+  if (pcf_aborted(status)) return;
   // [kTiny][256] (transposed: thread t owns column t, so accesses are
   // conflict-free)
   __shared__ uint64_t tk[kTiny][256];
@@ -915,6 +933,7 @@ __global__ void k_next_segs(const BRec* __restrict__ brec, const uint32_t* __res
                             const uint64_t* __restrict__ n_flagged, uint64_t n_buckets, Policy P,
                             uint32_t dbits, uint32_t tile_keys, Seg* nsegs, uint32_t* cols,
                             uint32_t s_max, LevelOut* lo, uint32_t* status) {
+  if (pcf_aborted(status)) return;
   const uint64_t B = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (B >= n_buckets) return;
   const uint32_t s = pos[B];
@@ -974,7 +993,9 @@ constexpr uint32_t kColRows = 2048;
 
 __global__ void __launch_bounds__(256) k_cols_reduce(const uint32_t* __restrict__ cols,
                                                      uint32_t s_max, const uint64_t* n_rows,
-                                                     uint32_t* block_sums, uint32_t n_blocks) {
+                                                     uint32_t* block_sums, uint32_t n_blocks,
+                                                     const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t S = (uint32_t)(*n_rows < s_max ? *n_rows : (uint64_t)s_max);
   const uint32_t r0 = blockIdx.x * kColRows, r1 = min(S, r0 + kColRows);
   __shared__ uint32_t sh8[8];
@@ -993,7 +1014,9 @@ __global__ void __launch_bounds__(32 * PC_NCOL) k_cols_scan(uint32_t* block_sums
                                                             uint32_t n_blocks,
                                                             const uint64_t* n_rows,
                                                             uint32_t s_max, const Seg* nsegs,
-                                                            DevPlan dp, LevelOut* lo) {
+                                                            DevPlan dp, LevelOut* lo,
+                                                            const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t S = (uint32_t)(*n_rows < s_max ? *n_rows : (uint64_t)s_max);
   uint64_t carry = 0;
@@ -1026,7 +1049,9 @@ __global__ void __launch_bounds__(32 * PC_NCOL) k_cols_scan(uint32_t* block_sums
 __global__ void __launch_bounds__(256) k_cols_apply(const uint32_t* __restrict__ cols,
                                                     uint32_t s_max, const uint64_t* n_rows,
                                                     const uint32_t* __restrict__ block_sums,
-                                                    uint32_t n_blocks, DevPlan dp) {
+                                                    uint32_t n_blocks, DevPlan dp,
+                                                    const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t S = (uint32_t)(*n_rows < s_max ? *n_rows : (uint64_t)s_max);
   const uint32_t r0 = blockIdx.x * kColRows, r1 = min(S, r0 + kColRows);
   __shared__ uint32_t sh8[8];
@@ -1066,6 +1091,7 @@ __global__ void __launch_bounds__(256) k_cols_apply(const uint32_t* __restrict__
 // Segments whose range is degenerate go to the standard sort as a whole.
 __global__ void k_seg_status_lists(const Seg* segs, uint32_t S, FbItem* fb, LevelOut* lo,
                                    uint32_t max_items, uint32_t* status) {
+  if (pcf_aborted(status)) return;
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   if (segs[s].status != SEG_DEGEN) return;
@@ -1085,7 +1111,9 @@ __global__ void __launch_bounds__(256) k_copy_segs(const Seg* segs, uint32_t S,
                                                    const uint32_t* range_base,
                                                    const uint64_t* __restrict__ src, uint64_t* dst,
                                                    const uint32_t* __restrict__ src_v,
-                                                   uint32_t* dst_v, uint32_t status_mask) {
+                                                   uint32_t* dst_v, uint32_t status_mask,
+                                                   const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t t = blockIdx.x;
   const uint32_t s = upper_bound_dev(range_base, S + 1, t) - 1;
   const Seg& g = segs[s];
@@ -1108,9 +1136,81 @@ __global__ void __launch_bounds__(256) k_copy_segs(const Seg* segs, uint32_t S,
     for (uint64_t q = base + threadIdx.x; q < end; q += 256) dst_v[q] = src_v[q];
 }
 
+// A replayed sort graph's check at the end of a level: the host decisions the
+// graph was captured with (the next level's plan, and that no bucket went to
+// the standard sort) against what this run's device computed.  Any
+// difference sets STATUS_REPLAN, which gates every later kernel; the host
+// then sorts the input again without the graph.
+__global__ void k_guard(const LevelOut* dev, const LevelOut* rec, uint32_t* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const PlanTotals& a = dev->plan;
+  const PlanTotals& b = rec->plan;
+  bool same = dev->n_fb == rec->n_fb && dev->max_fb_n == rec->max_fb_n && a.n_keys == b.n_keys &&
+              a.lo == b.lo && a.hi == b.hi && a.S == b.S && a.dmax1 == b.dmax1 &&
+              a.dmax2 == b.dmax2 && a.two_pass == b.two_pass;
+  for (int k = 0; k < PC_NCOL; ++k) same = same && a.col[k] == b.col[k];
+  if (!same) atomicOr(status, STATUS_REPLAN);
+}
+
+// ... and of a level's standard-sort list, which the device builds in any
+// order: every one of its n items must be one of the recorded items (kept
+// sorted by offset; the items are disjoint, so equal counts and every item
+// found make the same set).
+__global__ void k_guard_list(const FbItem* dev, const FbItem* rec, uint32_t n, uint32_t* status) {
+  if (pcf_aborted(status)) return;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const FbItem d = dev[i];
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t m = (lo + hi) >> 1;
+    if (rec[m].off < d.off) lo = m + 1;
+    else hi = m;
+  }
+  if (lo >= n || rec[lo].off != d.off || rec[lo].n != d.n) atomicOr(status, STATUS_REPLAN);
+}
+
+// ... and of a buffer the host read back during the standard sort's rounds
+// (ranges, pivots, split decisions, part sizes): word for word.
+__global__ void k_guard_words(const uint32_t* dev, const uint32_t* rec, uint64_t n,
+                              uint32_t* status) {
+  if (pcf_aborted(status)) return;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    if (dev[i] != rec[i]) {
+      atomicOr(status, STATUS_REPLAN);
+      return;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_guard_list(const LaunchCfg& c, const FbItem* dev, const FbItem* rec,
+                              uint32_t n) {
+  if (!n) return cudaSuccess;
+  k_guard_list<<<(n + 255) / 256, 256, 0, c.stream>>>(dev, rec, n, c.status);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guard_words(const LaunchCfg& c, const void* dev, const void* rec,
+                               uint64_t n_words) {
+  if (!n_words) return cudaSuccess;
+  const uint64_t blocks = (n_words + 255) / 256;
+  const uint32_t grid = (uint32_t)(blocks < 256 ? blocks : 256);
+  k_guard_words<<<grid, 256, 0, c.stream>>>((const uint32_t*)dev, (const uint32_t*)rec, n_words,
+                                            c.status);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guard(const LaunchCfg& c, const LevelOut* dev, const LevelOut* rec) {
+  k_guard<<<1, 32, 0, c.stream>>>(dev, rec, c.status);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
 static inline uint32_t cdiv(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
 cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* range_base,
@@ -1126,14 +1226,14 @@ cudaError_t launch_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32
 cudaError_t launch_sample_range(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
                                 uint32_t n_ctas, const uint64_t* keys) {
   if (!n_ctas) return cudaSuccess;
-  k_sample_range<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt);
+  k_sample_range<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t pass) {
   if (!S) return cudaSuccess;
-  k_model<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, c.kt, c.model, pass);
+  k_model<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, c.kt, c.model, pass, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1141,7 +1241,7 @@ cudaError_t launch_model(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t pas
 cudaError_t launch_sample(const LaunchCfg& c, Seg* segs, uint32_t S, const uint32_t* k1_base,
                           uint32_t n_ctas, const uint64_t* keys, uint32_t* tpool) {
   if (!n_ctas) return cudaSuccess;
-  k_sample<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt, tpool);
+  k_sample<<<n_ctas, 256, 0, c.stream>>>(segs, S, k1_base, keys, c.kt, tpool, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1152,7 +1252,7 @@ cudaError_t launch_table(const LaunchCfg& c, Seg* segs, uint32_t S, uint32_t* tp
   cudaError_t e = launch_scan(c, tpool, pool_n, nullptr, status_words, tile_counter, 0xFFFFFFFFu,
                               spin_limit, nullptr, true);
   if (e) return e;
-  k_seg_base<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, tpool);
+  k_seg_base<<<cdiv(S, 128), 128, 0, c.stream>>>(segs, S, tpool, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1339,7 +1439,8 @@ cudaError_t launch_groups(const LaunchCfg& c, const Seg* segs, uint32_t S,
                           uint32_t* g_centries) {
   if (!n_groups) return cudaSuccess;
   k_groups<<<cdiv(n_groups, 256), 256, 0, c.stream>>>(segs, S, group_base_dev, n_groups, cmat1,
-                                                      tile_keys, groups, g_tiles, g_centries);
+                                                      tile_keys, groups, g_tiles, g_centries,
+                                                      c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1347,7 +1448,8 @@ cudaError_t launch_groups(const LaunchCfg& c, const Seg* segs, uint32_t S,
 cudaError_t launch_group_bases(const LaunchCfg& c, Group* groups, uint64_t n_groups,
                                const uint32_t* g_centries_scan) {
   if (!n_groups) return cudaSuccess;
-  k_group_bases<<<cdiv(n_groups, 256), 256, 0, c.stream>>>(groups, n_groups, g_centries_scan);
+  k_group_bases<<<cdiv(n_groups, 256), 256, 0, c.stream>>>(groups, n_groups, g_centries_scan,
+                                                           c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1358,7 +1460,8 @@ cudaError_t launch_hist2(const LaunchCfg& c, const Group* groups, uint32_t n_gro
                          uint32_t* cmat2, uint32_t dmax) {
   if (!n_tiles_bound) return cudaSuccess;
   k_hist2<<<n_tiles_bound, 256, dmax * 4, c.stream>>>(groups, n_groups, segs, g_tile_scan,
-                                                      total_tiles, tile_keys, aux, cmat2);
+                                                      total_tiles, tile_keys, aux, cmat2,
+                                                      c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1420,7 +1523,7 @@ cudaError_t launch_copy_segs(const LaunchCfg& c, const Seg* segs, uint32_t S,
                              uint32_t status_mask) {
   if (!n_tiles) return cudaSuccess;
   k_copy_segs<<<n_tiles, 256, 0, c.stream>>>(segs, S, range_base, src, dst, src_v, dst_v,
-                                             status_mask);
+                                             status_mask, c.status);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -1439,11 +1542,12 @@ cudaError_t launch_plan_next(const LaunchCfg& c, const BRec* brec, uint32_t* nex
                                                           s_max, lo, c.status);
   count_launch(c);
   const uint32_t nb = cdiv(s_max, kColRows);
-  k_cols_reduce<<<nb, 256, 0, c.stream>>>(cols, s_max, n_flagged, block_sums, nb);
+  k_cols_reduce<<<nb, 256, 0, c.stream>>>(cols, s_max, n_flagged, block_sums, nb, c.status);
   count_launch(c);
-  k_cols_scan<<<1, 32 * PC_NCOL, 0, c.stream>>>(block_sums, nb, n_flagged, s_max, out.segs, out, lo);
+  k_cols_scan<<<1, 32 * PC_NCOL, 0, c.stream>>>(block_sums, nb, n_flagged, s_max, out.segs, out, lo,
+                                                c.status);
   count_launch(c);
-  k_cols_apply<<<nb, 256, 0, c.stream>>>(cols, s_max, n_flagged, block_sums, nb, out);
+  k_cols_apply<<<nb, 256, 0, c.stream>>>(cols, s_max, n_flagged, block_sums, nb, out, c.status);
   count_launch(c);
   return cudaGetLastError();
 }

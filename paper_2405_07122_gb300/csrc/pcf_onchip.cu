@@ -532,7 +532,8 @@ __device__ __forceinline__ uint32_t size_class(uint32_t n) {
 }
 
 __global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t ncls,
-                             uint32_t* lists, uint32_t* counts) {
+                             uint32_t* lists, uint32_t* counts, const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31;
   uint32_t cls = kMaxClasses;
@@ -563,6 +564,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
                                                            uint32_t kt, Policy P,
                                                            const uint16_t* __restrict__ ptab,
                                                            uint32_t* status) {
+  if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const Slice w = carve(smem_raw + (size_t)wib * slice_bytes(geo, PAIRS), geo, PAIRS);
@@ -890,6 +892,7 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
                                                         uint64_t* out, uint32_t kt, Policy P,
                                                         const uint16_t* __restrict__ ptab,
                                                         uint32_t* status) {
+  if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ CtaShared<NT> sh;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1054,7 +1057,7 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
   const uint32_t ncls = onchip_classes(leaf_cap);
   cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kMaxClasses, c.stream);
   if (e) return e;
-  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts);
+  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts, c.status);
   count_launch(c);
   if ((e = cudaGetLastError())) return e;
   uint32_t cls = 0;

@@ -87,6 +87,12 @@ def lib():
             "pcf_bucket_sizes": [_vp, _vp, _vp, _u32, ctypes.c_int, _u64, _u64, _u64, _u64, _vp,
                                  _vp, _vp],
             "pcf_sort_segmented_static": [_vp, _vp, _vp, _u32, _u64, ctypes.c_int, _u64, _vp],
+            "pcf_graph_create": [ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _vp,
+                                 ctypes.POINTER(_u64), _u32, ctypes.c_int, _u64, _vp],
+            "pcf_graph_launch": [_vp, _vp, ctypes.POINTER(ctypes.c_int)],
+            "pcf_graph_info": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
+                               ctypes.POINTER(_u64)],
+            "pcf_graph_destroy": [_vp],
             "pcf_debug_scan": [_vp, _vp, _u64, _u32, _u64, _vp],
             "pcf_debug_level0": [_vp, _vp, _u64, ctypes.c_int, _u64, ctypes.POINTER(_u64),
                                  ctypes.POINTER(_u32), _u64],
@@ -307,6 +313,56 @@ class Context:
 
 
 # -- host copies of device functions (CPU self-checks) -------------------------
+class SortGraph:
+    """A pcf_graph: the segmented sort of fixed buffers captured in a CUDA
+    graph.  Creating it sorts keys_in into keys_out once (as
+    Context.sort_segmented would, out of place); launch() sorts their
+    current contents again, by a graph replay when the data takes the
+    recorded plan, else without the graph.  The tensors must outlive it."""
+
+    def __init__(self, ctx, keys_in, offsets, keys_out, vals_in=None, vals_out=None,
+                 key_type=None, seed=0, stream=None):
+        kt = _kt(key_type or ("f64" if str(keys_in.dtype) == "torch.float64" else "u64"))
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+        self._h = _vp()
+        self._keep = (keys_in, keys_out, vals_in, vals_out)
+        rc = lib().pcf_graph_create(
+            ctypes.byref(self._h), ctx._h, keys_in.data_ptr(),
+            None if vals_in is None else vals_in.data_ptr(), keys_out.data_ptr(),
+            None if vals_out is None else vals_out.data_ptr(),
+            offs.ctypes.data_as(ctypes.POINTER(_u64)), offs.size - 1, kt, seed,
+            _stream_ptr(stream))
+        if rc:
+            raise PcfError(rc)
+
+    def launch(self, stream=None):
+        """Sorts again; returns True when the graph replay did the sort."""
+        rep = ctypes.c_int(0)
+        rc = lib().pcf_graph_launch(self._h, _stream_ptr(stream), ctypes.byref(rep))
+        if rc:
+            raise PcfError(rc)
+        return bool(rep.value)
+
+    def info(self):
+        cap, rep, eag = ctypes.c_int(0), _u64(0), _u64(0)
+        rc = lib().pcf_graph_info(self._h, ctypes.byref(cap), ctypes.byref(rep), ctypes.byref(eag))
+        if rc:
+            raise PcfError(rc)
+        return {"captured": bool(cap.value), "replays": rep.value, "eager_runs": eag.value}
+
+    def close(self):
+        if self._h:
+            lib().pcf_graph_destroy(self._h)
+            self._h = _vp()
+        self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def bins_host(kt, lo_bits, hi_bits, beta, xs_bits):
     xs = np.ascontiguousarray(xs_bits, dtype=np.uint64)
     out = np.empty(xs.size, dtype=np.uint32)
