@@ -3,8 +3,9 @@ available): every computed store position of the scatters, the bucket
 decision's small sorts and the on-chip finish is tested against its buffer
 before the access, and one out of bounds would fail the call with
 PCF_ERR_INTERNAL instead of writing.  The checked library sorts a spread of
-inputs, policies and entry points in a subprocess (one library per process)
-and must match the oracle everywhere with no check firing."""
+inputs, policies and entry points (the CUDA-graph form included) in a
+subprocess (one library per process) and must match the oracle everywhere
+with no check firing."""
 import os
 import subprocess
 import sys
@@ -64,6 +65,28 @@ SCRIPT = textwrap.dedent('''
         a, b = int(offs[s]), int(offs[s + 1])
         ref, _ = oracle.sort(keys[a:b], seed=1 + s)
         assert np.array_equal(got[a:b], bits(ref)), s
+    # the same batch, and a duplicate-heavy array (standard-sort rounds),
+    # captured in a CUDA graph and replayed
+    o2 = torch.empty_like(t)
+    g = pcfsort.SortGraph(ctx, t, offs, o2, key_type="f64", seed=1)
+    assert g.info()["captured"]
+    for _ in range(2):
+        o2.zero_()
+        assert g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(o2.view(torch.int64), o.view(torch.int64))
+    g.close()
+    xd = W.inject_duplicates(W.f64_keys("normal", 300000, 6), seed=6)
+    td = dev(xd)
+    od = torch.empty_like(td)
+    g = pcfsort.SortGraph(ctx, td, [0, xd.size], od, key_type="f64")
+    assert g.info()["captured"]
+    od.zero_()
+    assert g.launch()
+    torch.cuda.synchronize()
+    ref, _ = oracle.sort(xd)
+    assert np.array_equal(od.cpu().numpy().view(np.uint64), bits(ref))
+    g.close()
     for model, rng in (("spline", "array"), ("pcf", "sample")):
         c = pcfsort.Context(0, tuning=dict(leaf_cap=1024))
         c.set_policy(model=model, range_mode=rng)

@@ -267,11 +267,14 @@ def test_rejects_in_place_and_overlap(P, ctx):
     assert e.value.code == 1  # PCF_ERR_INVALID_ARG
 
 
-def test_policy_and_tuning_follow_the_context(P):
+@pytest.mark.parametrize("model,rng", [("spline", "array"), ("pcf", "sample")])
+def test_policy_and_tuning_follow_the_context(P, model, rng):
     c = P.Context(0, tuning=dict(leaf_cap=1024))
-    c.set_policy(model="spline")
-    x = W.f64_keys("exponential", 2**20, 12)
-    offs = _offsets([x.size])
+    c.set_policy(model=model, range_mode=rng)
+    lens = [2**20, 3000, 50000]
+    offs = _offsets(lens)
+    x = np.concatenate([W.f64_keys(d, n, 12 + i) for i, (d, n) in
+                        enumerate(zip(("exponential", "normal", "mixture"), lens))])
     t = _dev(x)
     o = torch.empty_like(t)
     g = P.SortGraph(c, t, offs, o, key_type="f64")
@@ -280,5 +283,15 @@ def test_policy_and_tuning_follow_the_context(P):
     assert g.launch() is True
     torch.cuda.synchronize()
     _check(o, x, offs, 0)
+    # a NaN (with the samples' range it is found by the bucketing pass)
+    y = x.copy()
+    y[777] = np.nan
+    t.copy_(_dev(y))
+    o.fill_(7)
+    with pytest.raises(P.PcfError) as e:
+        g.launch()
+    assert e.value.code == 2  # PCF_ERR_INVALID_KEY
+    torch.cuda.synchronize()
+    assert bool((o == 7).all())
     g.close()
     c.close()
