@@ -1073,8 +1073,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
         if (li >= rp->rec->fb_lists.size() || rp->rec->fb_lists[li].size() != lo.n_fb)
           return PCF_ERR_INTERNAL;
         items = rp->rec->fb_lists[li];
-        CK(launch_guard_list(lc, as<FbItem>(ctx->fb), (const FbItem*)(rp->d_blob + rp->list_at[li]),
-                             lo.n_fb));
+        CK(launch_guard_list(lc, as<FbItem>(ctx->fb),
+                             (const FbItem*)(rp->d_blob + rp->list_at[li]), lo.n_fb));
       } else {
         items.resize(lo.n_fb);
         CK(ensure_host(ctx->h_fb, (size_t)lo.n_fb * sizeof(FbItem)));
@@ -1196,10 +1196,12 @@ pcf_status graph_build(pcf_graph* g, cudaStream_t st) {
     return at;
   };
   rp.levels_at = add(rec.levels.data(), rec.levels.size() * sizeof(LevelOut));
-  for (const auto& l : rec.fb_lists) rp.list_at.push_back(add(l.data(), l.size() * sizeof(FbItem)));
+  for (const auto& l : rec.fb_lists)
+    rp.list_at.push_back(add(l.data(), l.size() * sizeof(FbItem)));
   for (const FbRound& rd : rec.rounds) {
     rp.round_at.emplace_back();
-    for (int k = 0; k < 4; ++k) rp.round_at.back().push_back(add(rd.got[k].data(), rd.got[k].size()));
+    for (int k = 0; k < 4; ++k)
+      rp.round_at.back().push_back(add(rd.got[k].data(), rd.got[k].size()));
   }
   CK(ensure(g->d_blob, blob.size() + 16));
   CK(cudaMemcpy(g->d_blob.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
