@@ -492,9 +492,21 @@ def run_secondary(args):
         total = int(offs[-1])
         t = torch.from_numpy(keys).cuda()
         o = torch.empty_like(t)
+        # the knobs (digit width, count-tile size, on-chip capacity) chosen by
+        # the autotuner on a sample of the batch: its first 512 arrays (not timed)
+        from paper_2405_07122_gb300 import autotune
+        s_offs = offs[:513]
+        s_in, s_out = t[:int(s_offs[-1])], torch.empty(int(s_offs[-1]), dtype=t.dtype,
+                                                        device=t.device)
+        tctx = autotune.tuned_context(
+            autotune.workload_key("segmented", total),
+            sample_runner=lambda c: c.sort_segmented(s_in, s_offs, keys_out=s_out,
+                                                     key_type="f64"))
+        tuning = tctx.tuning()
+        del s_out
         # the batched form: one CUDA graph replay of the whole segmented sort
         # (creating the graph sorts once and captures; not timed)
-        graph = pcfsort.SortGraph(ctx, t, offs, o, key_type="f64")
+        graph = pcfsort.SortGraph(tctx, t, offs, o, key_type="f64")
         batched_out = o.clone()
         replayed = []
         ms_g = timed(lambda: replayed.append(graph.launch()), max(1, args.steps))
@@ -511,6 +523,7 @@ def run_secondary(args):
         ms_p = timed(plain, 1)
         assert bool((o == batched_out).all()), "batched and plain outputs differ"
         graph.close()
+        tctx.close()
         line.update(metric=METRIC, value=total / ms_g / 1e6, ms_per_batch=ms_g,
                     graph={"captured": ginfo["captured"], "every_launch_replayed": all(replayed),
                            "launches": len(replayed)},
@@ -518,7 +531,8 @@ def run_secondary(args):
                     plain_value=total / ms_p / 1e6, plain_ms=ms_p, dtype="f64",
                     config={"workload": "batched segmented sort: 2048 float64 arrays, lengths "
                                         "floor(2^U(10,22)), distributions drawn from 5",
-                            "total_keys": total,
+                            "total_keys": total, "tuning": tuning,
+                            "tuned_by": "autotune.tuned_context on the first 512 arrays",
                             "form": "one CUDA graph replay of the segmented sort "
                                     "(pcf_graph_launch) vs one pcf_sort_segmented call vs "
                                     "2048 pcf_sort_keys calls"})
