@@ -883,6 +883,9 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   }
   bool first = true;
   size_t level_no = 0;
+  // the status word was read after the last launch (the final read below
+  // would repeat it)
+  bool status_current = false;
   while (L.S) {
     NvtxRange nvtx_level(first ? "pcf level 0" : "pcf level");
     const uint32_t S = L.S;
@@ -1127,8 +1130,12 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     src = X;
     src_v = Xv;
     first = false;
+    // read at this level's end, and nothing launched since unless the
+    // standard sort ran
+    status_current = mode != RUN_CAPTURE && lo.n_fb == 0;
   }
   if (mode == RUN_CAPTURE) return PCF_OK;  // the replay reads the status word
+  if (status_current) return PCF_OK;
   CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
   CK(cudaStreamSynchronize(st));
   const uint32_t stw = *(uint32_t*)ctx->h_status.p;
