@@ -1158,6 +1158,7 @@ struct pcf_graph {
   uint64_t* out_k = nullptr;
   uint32_t* out_v = nullptr;
   std::vector<InSeg> segs;
+  uint64_t n = 0;  // keys in all segments (0: every launch has nothing to do)
   uint32_t kt = 0;
   bool pairs = false;
   SortRecord rec;
@@ -1191,6 +1192,7 @@ pcf_status graph_build(pcf_graph* g, cudaStream_t st) {
     return r;
   }
   ++g->eager_runs;
+  if (g->n == 0) return PCF_OK;  // nothing to capture (no status buffers either)
   // the read-backs the guards compare with, in one device blob
   const SortRecord& rec = g->rec;
   Replay rp;
@@ -1440,6 +1442,7 @@ pcf_status pcf_graph_create(pcf_graph** out, const pcf_ctx* like, const void* d_
   g->out_k = (uint64_t*)d_keys_out;
   g->out_v = d_vals_out;
   g->segs = std::move(segs);
+  g->n = n;
   g->kt = (uint32_t)kt;
   g->pairs = pairs;
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -1460,6 +1463,7 @@ pcf_status pcf_graph_create(pcf_graph** out, const pcf_ctx* like, const void* d_
 pcf_status pcf_graph_launch(pcf_graph* g, void* stream, int* replayed) {
   if (replayed) *replayed = 0;
   if (!g) return PCF_ERR_INVALID_ARG;
+  if (g->n == 0) return PCF_OK;
   pcf_ctx* ctx = g->ctx;
   const cudaStream_t st = (cudaStream_t)stream;
   CK(cudaSetDevice(ctx->device));

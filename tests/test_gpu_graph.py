@@ -255,6 +255,17 @@ def test_small_arrays_only(P, ctx):
         g.close()
 
 
+def test_no_keys(P, ctx):
+    # no segments, or only empty ones: nothing to sort, every launch returns
+    t = torch.empty(0, dtype=torch.float64, device="cuda")
+    o = torch.empty(0, dtype=torch.float64, device="cuda")
+    for offs in ([0], [0, 0, 0]):
+        g = P.SortGraph(ctx, t, offs, o, key_type="f64")
+        assert not g.info()["captured"]
+        assert g.launch() is False
+        g.close()
+
+
 def test_rejects_in_place_and_overlap(P, ctx):
     x = W.f64_keys("normal", 10000, 1)
     t = _dev(x)
