@@ -51,8 +51,8 @@
  *      bucket = min(floor(RN(y * g)), gamma) with g = RN(gamma / alpha)
  *      (floor(F gamma) of Alg. 1 with one division per model, not per key).
  *
- * Sample range (policy range_mode 1; SURVEY reading D9, a cheaper variant
- * of Sec. 3.3's whole-array range):
+ * Sample range (policy range_mode 1: a cheaper variant of Sec. 3.3's
+ * whole-array range, not one the paper uses):
  *   R14 lo, hi = the minimum and maximum of the alpha sampled keys (R2's
  *      indices).  If they are equal, or R5 finds that range degenerate, the
  *      (sub)array's own range is used instead, with R4 and R5 as usual.  A

@@ -4,6 +4,25 @@
 // Everything here is compiled both for sm_103a and for the host (the host
 // copies back the C ABI's self-test entry points); none of it is shared
 // with the CPU oracle.
+//
+// Readings of the paper the kernels follow, cited by label in comments:
+//   R1  floor(n^{p/q}) is the largest m with m^q <= n^p, in exact integers.
+//   R2  the alpha samples are drawn uniformly with replacement, sample j
+//       being floor(r_j n / 2^64) for output j of a SplitMix64 stream keyed
+//       by (seed, depth, start, n).
+//   R3  bin(x) = clamp(floor(RN(RN(x - lo) s)), 0, beta), s = RN(beta / RN(hi
+//       - lo)), binary64 round-to-nearest without contraction.
+//   R4  a (sub)array whose min and max are the same bits is already sorted.
+//   R5  a range that is zero, not finite, or gives a non-normal s goes to
+//       Standard-Sort.
+//   R6  the bucket id floor(b gamma / alpha) is exact integer arithmetic.
+//   R7  Standard-Sort may be any sort: the sorted output is unique.
+//   R8  the fallback test is |c| >= delta, with the parent's delta.
+//   R9  NaN keys are rejected.
+//   R13 spline model (App. A.5): the position inside the bin and the linear
+//       interpolation between b_{k-1} and b_k in binary64, in a fixed order.
+//   R14 sample range: lo, hi are the min and max of the alpha samples; the
+//       (sub)array's own range is used when they are equal or degenerate.
 #pragma once
 #include <stdint.h>
 
