@@ -237,6 +237,24 @@ def test_many_split_rounds_pairs(P, ctx):
     g.close()
 
 
+def test_zipf_pairs_three_levels(P, ctx):
+    # duplicate-heavy u64 pairs: several global levels and many split rounds,
+    # all captured; the replay is stable and matches the oracle
+    k = W.zipf_u64(1 << 22, seed=5, n_values=200000)
+    v = np.arange(k.size, dtype=np.uint32)
+    offs = _offsets([k.size])
+    t, tv = _dev(k), torch.from_numpy(v.view(np.int32)).cuda()
+    o, ov = torch.empty_like(t), torch.empty_like(tv)
+    g = P.SortGraph(ctx, t, offs, o, vals_in=tv, vals_out=ov, key_type="u64", seed=1)
+    assert g.info()["captured"]
+    o.zero_()
+    ov.zero_()
+    assert g.launch() is True
+    torch.cuda.synchronize()
+    _check(o, k, offs, 1, v, ov)
+    g.close()
+
+
 def test_small_arrays_only(P, ctx):
     g0 = np.random.Generator(np.random.PCG64(9))
     lens = g0.integers(0, 4097, size=300)
