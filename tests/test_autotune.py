@@ -27,3 +27,44 @@ def test_default_grid_is_speed_only():
     assert set(autotune.DEFAULT_GRID) == {"max_digit_bits", "tile_log2", "leaf_cap"}
     for v in autotune.DEFAULT_GRID["leaf_cap"]:
         assert 64 <= v <= 8192 and v & (v - 1) == 0
+
+
+class _FakeContext:
+    made = []
+
+    def __init__(self, device=0, tuning=None, **kw):
+        self.tuning_ = dict(tuning or {})
+        _FakeContext.made.append(self.tuning_)
+
+    def close(self):
+        pass
+
+
+def test_tune_and_cache_logic_without_a_gpu(monkeypatch, tmp_path):
+    # every grid point is tried once; the fastest is kept and cached; a
+    # cached class is served without tuning again
+    cost = {(10, 1024): 3.0, (10, 4096): 1.5, (11, 1024): 2.0, (11, 4096): 2.5}
+    monkeypatch.setattr(autotune.pcfsort, "Context", _FakeContext)
+    monkeypatch.setattr(autotune, "_time",
+                        lambda run, reps: (run(), cost[_FakeContext.cur])[1])
+
+    def runner(ctx):
+        _FakeContext.cur = (ctx.tuning_["max_digit_bits"], ctx.tuning_["leaf_cap"])
+
+    _FakeContext.made = []
+    grid = {"max_digit_bits": (10, 11), "leaf_cap": (1024, 4096)}
+    best, res = autotune.tune(runner, grid=grid)
+    assert best == {"max_digit_bits": 10, "leaf_cap": 4096}
+    assert res == cost and len(_FakeContext.made) == 4
+    path = str(tmp_path / "t.json")
+    c = autotune.tuned_context("k", runner, grid=grid, cache_path=path)
+    assert c.tuning_ == best and autotune.load_cache(path) == {"k": best}
+
+    def no_tuning(ctx):
+        raise AssertionError("a cached class is not tuned again")
+
+    c = autotune.tuned_context("k", no_tuning, grid=grid, cache_path=path)
+    assert c.tuning_ == best
+    # an unknown class without a runner gets the library's defaults
+    c = autotune.tuned_context("other", None, grid=grid, cache_path=path)
+    assert c.tuning_ == {}
