@@ -373,3 +373,32 @@ def test_seed_independent_output():
     a, _ = oracle.sort(x, seed=1)
     b, _ = oracle.sort(x, seed=2)
     assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def _total_order_u64(x):
+    # IEEE-754 total order of binary64 bit patterns as unsigned integers
+    b = np.ascontiguousarray(x).view(np.uint64)
+    neg = (b >> np.uint64(63)) == 1
+    return np.where(neg, ~b, b | np.uint64(1 << 63))
+
+
+@pytest.mark.parametrize("n", [2, 17, 1000, 4097, 100003])
+def test_std_sort_is_a_stable_sort(n):
+    # Standard-Sort (R7) against numpy's stable argsort of the total-order
+    # keys: heavy duplicates, signed zeros and infinities, values carried
+    g = np.random.Generator(np.random.PCG64(n))
+    x = np.round(g.normal(size=n) * 3.0)
+    x[g.random(n) < 0.1] = -0.0
+    x[g.random(n) < 0.1] = 0.0
+    x[g.random(n) < 0.02] = np.inf
+    x[g.random(n) < 0.02] = -np.inf
+    v = np.arange(n, dtype=np.uint32)
+    k, vv = oracle.std_sort(x, v)
+    order = np.argsort(_total_order_u64(x), kind="stable")
+    assert np.array_equal(k.view(np.uint64), x[order].view(np.uint64))
+    assert np.array_equal(vv, v[order])
+    # unsigned keys: plain unsigned order
+    u = g.integers(0, 50, size=n, dtype=np.uint64) * np.uint64(2**58)
+    ku, vu = oracle.std_sort(u, v)
+    order = np.argsort(u, kind="stable")
+    assert np.array_equal(ku, u[order]) and np.array_equal(vu, v[order])
