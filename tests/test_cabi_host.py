@@ -118,3 +118,50 @@ def test_bin_fast_path_rarely_falls_back(P):
     lo, hi = int(bits[np.argmin(x)]), int(bits[np.argmax(x)])
     _, fast = P.bins_host(0, lo, hi, 10**6, bits)
     assert int((fast == 0).sum()) <= 2
+
+
+def _boundary_keys_f64(lo, hi, beta, g, m=3000, spread=4):
+    # keys at (an estimate of) the bin boundaries lo + k (hi - lo) / beta and
+    # up to `spread` ulps either side, clipped to [lo, hi]
+    k = g.integers(0, beta + 1, m)
+    x0 = lo + k.astype(np.float64) * ((hi - lo) / beta)
+    xs = [x0]
+    up, dn = x0.copy(), x0.copy()
+    for _ in range(spread):
+        up = np.nextafter(up, np.inf)
+        dn = np.nextafter(dn, -np.inf)
+        xs += [up, dn]
+    x = np.clip(np.concatenate(xs), lo, hi)
+    return np.concatenate([[lo, hi], x])
+
+
+@pytest.mark.parametrize("lo,hi,beta", [
+    (-5.6, 5.7, 10**6), (0.0, 1.0, 31622), (1e-3, 7.5e3, 2**21), (-1e10, -1e10 + 1e-2, 181),
+    (1.0, 1.0 + 2.0 ** -30, 1000), (-3.0, 3.0, 7), (2.0 ** -1000, 2.0 ** -990, 92681)])
+def test_bin_fast_path_at_bin_boundaries(P, lo, hi, beta):
+    """Keys within a few ulps of the boundaries, where the fixed-point fast
+    path must notice the ambiguity and take the exact binary64 sequence:
+    every bin equals the oracle's."""
+    g = np.random.Generator(np.random.PCG64(beta))
+    x = _boundary_keys_f64(lo, hi, beta, g)
+    bits = x.view(np.uint64)
+    lob, hib = int(np.float64(lo).view(np.uint64)), int(np.float64(hi).view(np.uint64))
+    ref = oracle.bins(oracle.KEY_F64, lob, hib, beta, bits)
+    got = P.bins_host(oracle.KEY_F64, lob, hib, beta, bits)
+    assert ref is not None and got is not None
+    assert np.array_equal(ref.astype(np.uint32), got[0])
+    assert int((got[1] == 0).sum()) > 0  # the exact sequence was exercised
+
+
+@pytest.mark.parametrize("lo,hi,beta", [(0, 2**40, 10**6), (10**18, 10**18 + 12345, 181),
+                                        (0, 2**64 - 1, 2**21), (5, 2**33 + 7, 31622)])
+def test_bin_fast_path_at_bin_boundaries_u64(P, lo, hi, beta):
+    g = np.random.Generator(np.random.PCG64(beta + 1))
+    k = g.integers(0, beta + 1, 3000).astype(object)
+    centre = [lo + (int(kk) * (hi - lo)) // beta for kk in k]
+    xs = [min(hi, max(lo, c + d)) for c in centre for d in range(-3, 4)] + [lo, hi]
+    x = np.array(xs, dtype=np.uint64)
+    ref = oracle.bins(oracle.KEY_U64, lo, hi, beta, x)
+    got = P.bins_host(oracle.KEY_U64, lo, hi, beta, x)
+    assert ref is not None and got is not None
+    assert np.array_equal(ref.astype(np.uint32), got[0])
