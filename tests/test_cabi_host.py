@@ -165,3 +165,14 @@ def test_bin_fast_path_at_bin_boundaries_u64(P, lo, hi, beta):
     got = P.bins_host(oracle.KEY_U64, lo, hi, beta, x)
     assert ref is not None and got is not None
     assert np.array_equal(ref.astype(np.uint32), got[0])
+
+
+def test_binding_declares_every_function(P):
+    # every function of include/pcfsort.h has a ctypes signature in the
+    # binding (argument marshalling only, so a missing one would pass
+    # arguments untyped)
+    h = open(os.path.join(ROOT, "include", "pcfsort.h")).read()
+    names = sorted(set(re.findall(r"\b(pcf_[a-z0-9_]+)\s*\(", h)))
+    L = P.lib()
+    assert names and all(getattr(L, n).argtypes is not None for n in names), \
+        [n for n in names if getattr(L, n).argtypes is None]
