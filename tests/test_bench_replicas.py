@@ -3,8 +3,6 @@ with gloo, world size 2."""
 import os
 import sys
 
-import pytest
-import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 

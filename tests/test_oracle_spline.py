@@ -5,7 +5,6 @@ brute force.  (TEST INFRASTRUCTURE: CPU only.)"""
 import numpy as np
 
 import oracle
-from paper_2405_07122_gb300 import workloads as W
 
 from test_oracle_pins import KINDS, gen, is_total_order_sorted
 
