@@ -218,6 +218,9 @@ def main():
                     help="plain: the default 4 x 10^8 f64 line; the others are the "
                          "secondary configurations")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--leaf-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="on-chip finish of keys-only sorts: 1 block-local sort, 2 Learned-Sort "
+                         "steps in shared memory, 0 the library default (1)")
     args = ap.parse_args()
     n = args.n
     if args.workload != "plain" and args.impl == "ours":
@@ -248,6 +251,8 @@ def main():
     ctx = pcfsort.Context(local)
     if args.model != "pcf" or args.range != "array":
         ctx.set_policy(model=args.model, range_mode=args.range)
+    if args.leaf_mode:
+        ctx.set_tuning(leaf_mode=args.leaf_mode)
     ctx.reserve(n)
     # the sorts' own stream (created non-blocking by torch): on the legacy
     # default stream every launch would also order against other streams

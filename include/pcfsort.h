@@ -92,12 +92,17 @@ typedef struct {
  * uses tiles 4x larger);
  * leaf_cap = the largest bucket finished on chip (64..8192, power of two; key-
  * value sorts use at most 1024, and a smaller one where the policy's tables
- * would not fit shared memory).
- * Zero fields keep the current value.  Default: {11, 14, 4096}. */
+ * would not fit shared memory);
+ * leaf_mode = how keys-only sorts finish a bucket on chip: 1 = a block-local
+ * Standard-Sort of the whole bucket (one equal-width MSD split of its range,
+ * then ranks within the parts), 2 = the remaining Learned-Sort steps of
+ * Algorithm 1 run in shared memory.  Key-value sorts always take 2.
+ * Zero fields keep the current value.  Default: {11, 14, 4096, 1}. */
 typedef struct {
   uint32_t max_digit_bits;
   uint32_t tile_log2;
   uint32_t leaf_cap;
+  uint32_t leaf_mode;
 } pcf_tuning;
 
 typedef struct pcf_ctx pcf_ctx;

@@ -104,7 +104,7 @@ struct pcf_ctx {
   int device = 0;
   int num_sms = 0;
   Policy policy{3, 3, 3, 3, 4, MODEL_PCF, 100, RANGE_ARRAY, 0};
-  pcf_tuning tuning{11, 14, 4096};
+  pcf_tuning tuning{11, 14, 4096, 1};
   std::string last_err;
   pcf_call_stats stats{};
   bool timing = false;
@@ -739,6 +739,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   lc.launches = &ctx->stats.kernel_launches;
   lc.model = ctx->policy.model;
   lc.range_mode = ctx->policy.range_mode;
+  lc.leaf_sort = !pairs && ctx->tuning.leaf_mode == 1;
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
   CK(cudaMemsetAsync(lc.status, 0, 16, st));
@@ -1294,9 +1295,11 @@ pcf_status pcf_ctx_set_tuning(pcf_ctx* ctx, const pcf_tuning* t) {
   if (t->max_digit_bits) n.max_digit_bits = t->max_digit_bits;
   if (t->tile_log2) n.tile_log2 = t->tile_log2;
   if (t->leaf_cap) n.leaf_cap = t->leaf_cap;
+  if (t->leaf_mode) n.leaf_mode = t->leaf_mode;
   if (n.max_digit_bits < 4 || n.max_digit_bits > kMaxDigitBits) return PCF_ERR_INVALID_ARG;
   if (n.tile_log2 < 12 || n.tile_log2 > 18) return PCF_ERR_INVALID_ARG;
   if (n.leaf_cap < 64 || n.leaf_cap > 8192 || (n.leaf_cap & (n.leaf_cap - 1))) return PCF_ERR_INVALID_ARG;
+  if (n.leaf_mode != 1 && n.leaf_mode != 2) return PCF_ERR_INVALID_ARG;
   ctx->tuning = n;
   return PCF_OK;
 }

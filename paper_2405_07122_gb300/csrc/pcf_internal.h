@@ -174,6 +174,9 @@ struct LaunchCfg {
   uint32_t model = MODEL_PCF;  // the policy's CDF model
   uint32_t range_mode = RANGE_ARRAY;  // ... and range
   bool pairs;
+  // keys-only leaf buckets: finished by the block-local Standard-Sort
+  // (k_leaf_sort) rather than by further Learned-Sort steps on chip
+  bool leaf_sort = false;
   uint32_t* status;  // device status word
   uint64_t* launches;  // host counter of kernel launches (may be null)
 };

@@ -960,6 +960,185 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Block-local Standard-Sort of a whole leaf bucket (keys only).  Alg. 1
+// leaves the choice of Standard-Sort open (Sec. 3.1: any sort), and a bucket
+// that fits in shared memory is small: it is sorted here in one piece
+// instead of by further Learned-Sort steps.  The output is the unique
+// ascending order either way.
+//
+// One CTA of NT threads per bucket of at most NT * KPT keys:
+//   1. each thread loads KPT keys (order-preserving integers) into
+//      registers; the CTA reduces min and max;
+//   2. one equal-width split of [min, max] into M = 2^ceil(log2 n) parts:
+//      part(v) = (v - min) >> shift, shift chosen so that parts < M (an MSD
+//      radix digit of the key's offset from the minimum; it needs no model,
+//      no samples and no division); counts by shared atomics, an exclusive
+//      scan, and each key written to its part's range of B;
+//   3. every key's final position: its part's start plus its rank among the
+//      part's keys (smaller, or equal and earlier in B), written straight to
+//      the output (consecutive threads write nearly consecutive positions).
+//      Parts of more than kLeafRank keys (skewed or duplicate-heavy buckets)
+//      are listed and sorted afterwards by one warp each (rank, bitonic or
+//      merge sort in shared memory).
+// The count array is stored transposed (part d of thread chunk d / r at
+// column d % r), so that the scan's per-thread chunks are read without bank
+// conflicts.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kLeafRank = 16;
+
+template <uint32_t NT>
+struct LeafShared {
+  uint64_t mn[NT / 32], mx[NT / 32];
+  uint32_t wsum[NT / 32];
+  uint32_t n_big;
+};
+
+// B [cap] u64 | A2 [cap] u64 (merge scratch) | H [cap] u32 | big [cap / kLeafRank + 1] u32
+__host__ __device__ inline size_t leaf_sort_smem(uint32_t cap) {
+  return (size_t)cap * 16 + (size_t)cap * 4 + ((size_t)cap / kLeafRank + 1) * 4 + 16;
+}
+
+template <uint32_t NT, uint32_t KPT>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
+    k_leaf_sort(const BRec* __restrict__ br, const uint32_t* __restrict__ list,
+                const uint32_t* __restrict__ count, const uint64_t* __restrict__ X, uint64_t* out,
+                uint32_t kt, uint32_t* status) {
+  constexpr uint32_t CAP = NT * KPT, NW = NT / 32;
+  constexpr uint32_t LNT = NT == 32 ? 5 : NT == 64 ? 6 : NT == 128 ? 7 : NT == 256 ? 8
+                         : NT == 512 ? 9 : 10;
+  static_assert((1u << LNT) == NT, "NT must be a power of two, 32..1024");
+  if (pcf_aborted(status)) return;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ LeafShared<NT> sh;
+  uint64_t* B = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* A2 = B + CAP;
+  uint32_t* H = reinterpret_cast<uint32_t*>(A2 + CAP);
+  uint32_t* big = H + CAP;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t nitems = *count;
+  for (uint32_t li = blockIdx.x; li < nitems; li += gridDim.x) {
+    const BRec r = br[list[li]];
+    const uint32_t off = r.off, n = r.n;
+    const uint32_t m = n > 1 ? 32u - __clz(n - 1) : 0u;  // M = 2^m >= n parts
+    const uint32_t M = 1u << m;
+    const uint32_t lr = m > LNT ? m - LNT : 0u;          // r = 2^lr parts per thread chunk
+    const uint32_t rmask = (1u << lr) - 1u;
+    auto hix = [&](uint32_t d) -> uint32_t { return ((d & rmask) << LNT) | (d >> lr); };
+    uint64_t k[KPT];
+    uint64_t mn = ~0ull, mx = 0ull;
+#pragma unroll
+    for (uint32_t j = 0; j < KPT; ++j) {
+      const uint32_t i = tid + j * NT;
+      k[j] = i < n ? ord_of(__ldg(X + off + i), kt) : 0ull;
+      if (i < n) {
+        mn = k[j] < mn ? k[j] : mn;
+        mx = k[j] > mx ? k[j] : mx;
+      }
+    }
+    for (uint32_t d = tid; d < M; d += NT) H[d] = 0;
+    if (tid == 0) sh.n_big = 0;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+      const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+      const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+      mn = a < mn ? a : mn;
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) {
+      sh.mn[wid] = mn;
+      sh.mx[wid] = mx;
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t w = 0; w < NW; ++w) {
+      mn = sh.mn[w] < mn ? sh.mn[w] : mn;
+      mx = sh.mx[w] > mx ? sh.mx[w] : mx;
+    }
+    if (mn == mx) {  // one value (or one key): already sorted
+#pragma unroll
+      for (uint32_t j = 0; j < KPT; ++j) {
+        const uint32_t i = tid + j * NT;
+        if (i < n && PCF_IN_KEYS(off + i, status)) out[off + i] = bits_of_ord(k[j], kt);
+      }
+      __syncthreads();
+      continue;
+    }
+    const uint32_t nb = 64u - (uint32_t)__clzll((long long)(mx - mn));
+    const uint32_t sft = nb > m ? nb - m : 0u;
+    uint32_t dg[KPT], rk[KPT];
+#pragma unroll
+    for (uint32_t j = 0; j < KPT; ++j) {
+      const uint32_t i = tid + j * NT;
+      dg[j] = (uint32_t)((k[j] - mn) >> sft);
+      rk[j] = i < n ? atomicAdd(&H[hix(dg[j])], 1u) : 0u;
+    }
+    __syncthreads();
+    // exclusive scan of the part counts: thread t owns parts [t r, t r + r),
+    // stored at H[c * NT + t], c < r
+    {
+      const uint32_t rr = 1u << lr;
+      uint32_t sum = 0;
+      if (tid * rr < M)
+        for (uint32_t c = 0; c < rr; ++c) sum += H[(c << LNT) | tid];
+      const uint32_t inc = wscan(sum, lane);
+      if (lane == 31) sh.wsum[wid] = inc;
+      __syncthreads();
+      uint32_t run = inc - sum;
+#pragma unroll
+      for (uint32_t w = 0; w < NW; ++w) run += w < wid ? sh.wsum[w] : 0u;
+      if (tid * rr < M)
+        for (uint32_t c = 0; c < rr; ++c) {
+          const uint32_t v = H[(c << LNT) | tid];
+          H[(c << LNT) | tid] = run;
+          run += v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t j = 0; j < KPT; ++j) {
+      const uint32_t i = tid + j * NT;
+      if (i < n) {
+        const uint32_t p = H[hix(dg[j])] + rk[j];
+        if (PCF_IN(p, n, status)) B[p] = k[j];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t j = 0; j < KPT; ++j) {
+      const uint32_t p = tid + j * NT;
+      if (p < n) {
+        const uint64_t v = B[p];
+        const uint32_t d = (uint32_t)((v - mn) >> sft);
+        const uint32_t s = H[hix(d)];
+        const uint32_t e = d + 1 < M ? H[hix(d + 1)] : n;
+        const uint32_t c = e - s;
+        if (c > kLeafRank) {
+          if (p == s) big[atomicAdd(&sh.n_big, 1u)] = s | (c << 16);
+          continue;
+        }
+        uint32_t pos = p;
+        if (c > 1) pos = s + rank_in(B, s, e, p, v);
+        if (PCF_IN_KEYS(off + pos, status)) out[off + pos] = bits_of_ord(v, kt);
+      }
+    }
+    __syncthreads();
+    const uint32_t nbig = sh.n_big;
+    for (uint32_t b = wid; b < nbig; b += NW) {
+      const uint32_t s = big[b] & 0xFFFFu, c = big[b] >> 16;
+      Slice w;
+      w.A = B;
+      w.B = A2;
+      w.Av = w.Bv = nullptr;
+      std_sort<false>(w, s, c, lane);
+      for (uint32_t i = lane; i < c; i += 32)
+        if (PCF_IN_KEYS(off + s + i, status)) out[off + s + i] = bits_of_ord(B[s + i], kt);
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace onchip
 
 using namespace onchip;
@@ -1036,6 +1215,30 @@ static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const u
   return cudaGetLastError();
 }
 
+// the block-local sort of one size class: NT threads, 8 keys each
+template <uint32_t NT>
+static cudaError_t launch_leaf_sort(const LaunchCfg& c, const BRec* br, const uint32_t* list,
+                                    const uint32_t* count, const uint64_t* X, uint64_t* out) {
+  constexpr uint32_t KPT = 8;
+  const size_t smem = leaf_sort_smem(NT * KPT);
+  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT>);
+  if (e) return e;
+  static int per_sm_cache[64] = {0};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev))) return e;
+  int per_sm = dev >= 0 && dev < 64 ? per_sm_cache[dev] : 0;
+  if (per_sm <= 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT>, (int)NT,
+                                                      smem);
+    if (e) return e;
+    per_sm = per_sm > 0 ? per_sm : 1;
+    if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
+  }
+  k_leaf_sort<NT, KPT><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT, smem,
+                         c.stream>>>(br, list, count, X, out, c.kt, c.status);
+  return cudaGetLastError();
+}
+
 uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs) {
   // key-value sorts: the warp kernel (four slices per block), up to 1024
   // keys; keys only: one slice per block above 256 keys
@@ -1065,7 +1268,16 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
     const uint32_t hi = min(capw, leaf_cap);
     const OnchipGeo g = onchip_geometry(hi, P, c.pairs);
     const uint32_t* list = lists + (size_t)cls * nb;
-    if (cls > 0 && !c.pairs) {
+    if (c.leaf_sort && !c.pairs) {
+      // the whole bucket by the block-local Standard-Sort, NT = capw / 8
+      if (capw <= 256) e = launch_leaf_sort<32>(c, br, list, counts + cls, X, out);
+      else if (capw <= 512) e = launch_leaf_sort<64>(c, br, list, counts + cls, X, out);
+      else if (capw <= 1024) e = launch_leaf_sort<128>(c, br, list, counts + cls, X, out);
+      else if (capw <= 2048) e = launch_leaf_sort<256>(c, br, list, counts + cls, X, out);
+      else if (capw <= 4096) e = launch_leaf_sort<512>(c, br, list, counts + cls, X, out);
+      else e = launch_leaf_sort<1024>(c, br, list, counts + cls, X, out);
+      if (e) return e;
+    } else if (cls > 0 && !c.pairs) {
       // a CTA per bucket (one slice per CTA), more threads for larger buckets
       if (hi <= 1024) e = launch_cta_class<64>(c, br, list, counts + cls, g, X, out, P, ptab);
       else if (hi <= 2048) e = launch_cta_class<128>(c, br, list, counts + cls, g, X, out, P, ptab);

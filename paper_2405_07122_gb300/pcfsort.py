@@ -42,7 +42,7 @@ class Policy(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("max_digit_bits", ctypes.c_uint32), ("tile_log2", ctypes.c_uint32),
-                ("leaf_cap", ctypes.c_uint32)]
+                ("leaf_cap", ctypes.c_uint32), ("leaf_mode", ctypes.c_uint32)]
 
 
 class CallStats(ctypes.Structure):
@@ -174,14 +174,17 @@ class Context:
             Policy(a_num=a_num, b_num=b_num, c_num=c_num, d_num=d_num, den=den, model=m,
                    tau=tau, range_mode=r))))
 
-    def set_tuning(self, max_digit_bits=0, tile_log2=0, leaf_cap=0):
+    def set_tuning(self, max_digit_bits=0, tile_log2=0, leaf_cap=0, leaf_mode=0):
+        """leaf_mode: 1 = block-local sort of each on-chip bucket (keys only),
+        2 = the remaining Learned-Sort steps on chip; 0 keeps the current."""
         self._check(lib().pcf_ctx_set_tuning(self._h, ctypes.byref(
-            Tuning(max_digit_bits, tile_log2, leaf_cap))))
+            Tuning(max_digit_bits, tile_log2, leaf_cap, leaf_mode))))
 
     def tuning(self):
         t = Tuning()
         self._check(lib().pcf_ctx_get_tuning(self._h, ctypes.byref(t)))
-        return dict(max_digit_bits=t.max_digit_bits, tile_log2=t.tile_log2, leaf_cap=t.leaf_cap)
+        return dict(max_digit_bits=t.max_digit_bits, tile_log2=t.tile_log2, leaf_cap=t.leaf_cap,
+                    leaf_mode=t.leaf_mode)
 
     def reserve(self, n_total: int, pairs: bool = False):
         self._check(lib().pcf_ctx_reserve(self._h, n_total, 1 if pairs else 0))
