@@ -402,3 +402,35 @@ def test_std_sort_is_a_stable_sort(n):
     ku, vu = oracle.std_sort(u, v)
     order = np.argsort(u, kind="stable")
     assert np.array_equal(ku, u[order]) and np.array_equal(vu, v[order])
+
+
+def three_value_input(n_lo, n_mid, n_hi, seed):
+    """n_lo copies of 1.0, n_mid of 2.0 and n_hi of 3.0, shuffled."""
+    x = np.concatenate([np.full(n_lo, 1.0), np.full(n_mid, 2.0), np.full(n_hi, 3.0)])
+    np.random.Generator(np.random.PCG64(seed)).shuffle(x)
+    return x
+
+
+def test_failure_guard_fires_at_exactly_delta():
+    # Alg. 1 sends a bucket to Standard-Sort when |c_j| >= delta (reading R8),
+    # with delta the parent's.  n = 10^4: alpha = beta = gamma = delta = 1000.
+    # Three values 1, 2, 3: bins 0, beta/2 and beta; with alpha = gamma the
+    # bucket of bin k is b_k, so the three values fall in three buckets (b_0,
+    # b_{beta/2}, alpha) as long as 2 and 3 are each sampled (a 1000-draw
+    # sample misses a value with over 10% of the keys with probability
+    # below 1e-45).  Sizes 1000 (= delta), 999 (= delta - 1) and 8001: the
+    # first and the last reach the guard, the middle one is recursed (one
+    # value: sorted at once).
+    n = 10**4
+    assert oracle.params(n) == (1000, 1000, 1000, 1000)
+    x = three_value_input(1000, 999, 8001, 11)
+    k, _, st = oracle.sort(x, seed=4, with_stats=True)
+    assert np.array_equal(k, np.sort(x))
+    assert st["n_fallback"] == 2
+    assert st["fallback_keys"] == 1000 + 8001
+    assert st["n_bucketings"] == 1 and st["n_single"] == 1
+    # one key fewer in the first bucket: below the guard, recursed instead
+    x = three_value_input(999, 999, 8002, 12)
+    _, _, st = oracle.sort(x, seed=4, with_stats=True)
+    assert st["n_fallback"] == 1 and st["fallback_keys"] == 8002
+    assert st["n_single"] == 2

@@ -2,6 +2,9 @@
 buckets against the PCF model's at the points where the definition ties
 them together, the ordered-bucket property, and the final output against
 brute force.  (TEST INFRASTRUCTURE: CPU only.)"""
+import math
+from fractions import Fraction
+
 import numpy as np
 
 import oracle
@@ -97,3 +100,35 @@ def test_spline_sort_large_and_stats():
                          kind="stable")
         assert np.array_equal(vv, ref.astype(np.uint32)), kind
         assert st["n_bucketings"] >= 1
+
+
+def test_spline_buckets_with_alpha_not_gamma_are_exact_rationals():
+    # App. A.5 in exact reals: j = floor(F(x) gamma), F(x) = (b_{k-1} + f
+    # (b_k - b_{k-1})) / alpha.  Policy a = 3/4, b = c = 1/2 at n = 256:
+    # alpha = 64, beta = gamma = 16, so gamma / alpha = 1/4 (and beta / range
+    # = 16 / 64) are exact in binary64.  With lo = 0 and hi = 64 a key x sits
+    # at p = x / 4 in bin floor(x / 4) at f = (x mod 4) / 4; at the edges and
+    # the quarter points of every bin each step of R13 is exact, so the
+    # oracle's bucket must equal the rational floor.
+    P = oracle.Policy(3, 2, 2, 3, 4, 100, SPLINE)
+    g = np.random.Generator(np.random.PCG64(8))
+    grid = np.arange(0, 65, dtype=np.float64)              # 0, 1, ..., 64
+    rest = g.uniform(0.0, 64.0, 256 - grid.size)
+    x = np.concatenate([grid, rest])
+    g.shuffle(x)
+    L = oracle.level0(x, seed=21, policy=P)
+    assert (L["alpha"], L["beta"], L["gamma"]) == (64, 16, 16)
+    assert L["status"] == 0
+    a, c = L["alpha"], L["gamma"]
+    b = [int(v) for v in L["b"]]
+    keys, bk = L["keys"], bucket_of_each(L)
+    where = {float(v): i for i, v in enumerate(keys)}
+
+    def exact(k, f):
+        lo = b[k - 1] if k else 0
+        return min(math.floor((lo + f * (b[k] - lo)) / a * c), c)
+
+    for xv in range(0, 65):
+        k, f = (16, Fraction(0)) if xv == 64 else (xv // 4, Fraction(xv % 4, 4))
+        assert bk[where[float(xv)]] == exact(k, f), xv
+    assert max(bk) <= c
