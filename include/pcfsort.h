@@ -120,6 +120,16 @@ typedef struct {
   uint64_t kernel_launches;  /* this library's kernel launches in the call       */
   uint64_t fallback_splits;  /* fallback items split three ways around a value that
                                 dominates them (below / equal / above)          */
+  /* Alg. 1's decisions, for comparison with a sequential PCF Learned Sort:
+   * buckets whose size reached the failure guard |c_j| >= delta (at any
+   * level, on chip included) and their keys, and Learned-Sort calls that
+   * bucketed their input (a model built and every key appended).  Key-value
+   * sorts append stably and take every step of Alg. 1, so these equal a
+   * sequential run's; keys-only sorts may append equal-bucket keys in another
+   * order and finish on-chip buckets by a block-local sort (tuning leaf_mode). */
+  uint64_t guard_buckets;
+  uint64_t guard_keys;
+  uint64_t bucketings;
 } pcf_call_stats;
 
 /* Creates a context on `device`.  The context owns its workspace (grown on

@@ -716,6 +716,18 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
 }
 
 
+// The status word and the decision counters after it (DecisionCounters at
+// byte 16 of the status buffer), read back together.
+constexpr size_t kStatusReadBytes = 16 + sizeof(DecisionCounters);
+
+void take_counters(pcf_ctx* ctx) {
+  DecisionCounters d;
+  memcpy(&d, (const char*)ctx->h_status.p + 16, sizeof d);
+  ctx->stats.guard_buckets = d.guard_buckets;
+  ctx->stats.guard_keys = d.guard_keys;
+  ctx->stats.bucketings = d.bucketings;
+}
+
 // The whole sort of a batch of arrays.  Level-0 segments are the caller's
 // arrays; keys flow src -> tmp (pass 1) -> out (pass 2); leaf buckets are
 // finished in place in out; fallback buckets are merge-sorted in out.
@@ -742,7 +754,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   lc.leaf_sort = !pairs && ctx->tuning.leaf_mode == 1;
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
-  CK(cudaMemsetAsync(lc.status, 0, 16, st));
+  CK(cudaMemsetAsync(lc.status, 0, 64, st));
   CK(ensure_host(ctx->h_status, 64));
 #ifdef PCF_CHECKED
   // the key buffers' length, for the checked build's index checks
@@ -756,7 +768,7 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   // the largest bucket finished on chip (the alpha..delta table covers the
   // tuning's leaf_cap, at least this)
   const uint32_t cap = onchip_cap(ctx->tuning.leaf_cap, ctx->policy, pairs);
-  const size_t olist_per_bucket = (size_t)4 * onchip_classes(cap);
+  const size_t olist_per_bucket = (size_t)8 * onchip_classes(cap);
   CK(ensure_ptab(ctx, st));
   const uint16_t* ptab = as<uint16_t>(ctx->ptab);
   Timer tm(ctx, st);
@@ -1056,9 +1068,10 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       lo = rp->rec->levels[level_no];
     } else {
       CK(launch_xfer(st, ctx->h_lout.dp, d_lo, sizeof(LevelOut)));
-      CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
+      CK(launch_xfer(st, ctx->h_status.dp, lc.status, kStatusReadBytes));
       CK(cudaStreamSynchronize(st));
       lo = *(LevelOut*)ctx->h_lout.p;
+      take_counters(ctx);
       const uint32_t stw = *(uint32_t*)ctx->h_status.p;
       if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
       if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;
@@ -1137,8 +1150,9 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   }
   if (mode == RUN_CAPTURE) return PCF_OK;  // the replay reads the status word
   if (status_current) return PCF_OK;
-  CK(launch_xfer(st, ctx->h_status.dp, lc.status, 4));
+  CK(launch_xfer(st, ctx->h_status.dp, lc.status, kStatusReadBytes));
   CK(cudaStreamSynchronize(st));
+  take_counters(ctx);
   const uint32_t stw = *(uint32_t*)ctx->h_status.p;
   if (stw & STATUS_NAN) return PCF_ERR_INVALID_KEY;
   if (stw & STATUS_TIMEOUT) return PCF_ERR_TIMEOUT;

@@ -29,6 +29,21 @@ __device__ __forceinline__ bool pcf_aborted(const uint32_t* status) {
   return status && (*reinterpret_cast<const volatile uint32_t*>(status) & STATUS_ABORT) != 0;
 }
 
+// The status buffer of a sort (64 bytes, zeroed at the call's start):
+//   [0]  u32 status word (STATUS_*)
+//   [8]  u64 key-buffer length for the checked build's index checks
+//   [16] u64 x 3 counters of Alg. 1's decisions (DecisionCounters)
+// The counters record what the sort decided, for comparison with the
+// oracle: every bucket whose size reached the failure guard |c| >= delta
+// (any level, on chip included) and its keys, and every Learned-Sort call
+// that bucketed its input (a model was built and the keys were appended).
+struct DecisionCounters {
+  unsigned long long guard_buckets, guard_keys, bucketings;
+};
+__device__ __forceinline__ DecisionCounters* pcf_counters(const uint32_t* status) {
+  return reinterpret_cast<DecisionCounters*>(const_cast<uint32_t*>(status) + 4);
+}
+
 // SEG_NEEDRANGE: the samples' range (R14) was equal or degenerate; the
 // array's own range decides
 enum : uint32_t { SEG_BUCKET = 0, SEG_SINGLE = 1, SEG_DEGEN = 2, SEG_NEEDRANGE = 3 };
@@ -304,7 +319,9 @@ uint32_t onchip_classes(uint32_t leaf_cap);
 // The largest bucket finished on chip: leaf_cap (key-value sorts at most
 // 1024), halved until the policy's slice fits one block's shared memory.
 uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs);
-// lists: onchip_classes(leaf_cap) nb u32 of scratch; counts: kMaxClasses u32
+// lists: onchip_classes(leaf_cap) x nb x 8 bytes of scratch (u32 record
+// indices, or (offset, size) pairs for the block-local sort); counts:
+// kMaxClasses u32
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts);

@@ -133,6 +133,7 @@ __global__ void k_model(Seg* segs, uint32_t S, uint32_t kt, uint32_t model, uint
     g.status = make_bin_model(kt, lo, hi, g.beta, &g.bm) ? SEG_DEGEN : SEG_BUCKET;
   }
   if (g.status == SEG_BUCKET && model == MODEL_SPLINE) spline_set(&g.bm, g.alpha, g.gamma);
+  if (g.status == SEG_BUCKET && gate) atomicAdd(&pcf_counters(gate)->bucketings, 1ull);
 }
 
 // min / max of each segment's alpha samples (R2's positions), per CTA of
@@ -862,6 +863,16 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     v = sg.status == SEG_BUCKET && size > 0;
   }
   const Seg* sg = v ? &segs[s] : nullptr;
+  // Alg. 1's failure guard, counted per warp (the decision record)
+  {
+    const bool guard = v && size >= sg->delta;
+    const uint32_t gb = __ballot_sync(~0u, guard);
+    const uint32_t gk = __reduce_add_sync(~0u, guard ? size : 0u);
+    if (gb && (threadIdx.x & 31) == 0) {
+      atomicAdd(&pcf_counters(status)->guard_buckets, (unsigned long long)__popc(gb));
+      atomicAdd(&pcf_counters(status)->guard_keys, (unsigned long long)gk);
+    }
+  }
   // Standard-Sort (|c| >= delta, or |c| < tau inside the recursive call) of a
   // tiny bucket: insertion sort by this thread, X -> out
   const bool std_sort = v && (size >= sg->delta || size < tau);

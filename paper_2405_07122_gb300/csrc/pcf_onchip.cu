@@ -300,7 +300,8 @@ __device__ void std_sort(const Slice& w, uint32_t o, uint32_t c, uint32_t lane) 
 template <bool PAIRS, bool SPLINE, bool SRANGE>
 __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                            uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
-                           uint32_t& top, uint32_t lane, bool root, uint64_t rmn, uint64_t rmx) {
+                           uint32_t& top, uint32_t lane, bool root, uint64_t rmn, uint64_t rmx,
+                           DecisionCounters* dc) {
   const uint32_t o = it.o, n = it.n;
   constexpr bool spline = SPLINE;
   // alpha..delta and the sample stream: with the array's range taken after
@@ -373,6 +374,7 @@ __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, 
     }
   }
   const uint32_t alpha = q.x, beta = q.y, gamma = q.z, delta = q.w;
+  if (lane == 0) atomicAdd(&dc->bucketings, 1ull);
   for (uint32_t k = lane; k <= beta; k += 32) w.tab[k] = 0;
   for (uint32_t k = lane; k <= gamma; k += 32) w.cnt[k] = 0;
   __syncwarp();
@@ -492,6 +494,10 @@ __device__ bool learn_step(const Slice& w, const OnchipGeo& geo, const Item it, 
       const uint32_t c = w.cnt[j], e = w.cur[j], s = e - c;
       const uint64_t v = w.B[o + p];
       const bool stdc = c >= delta || c < P.tau;
+      if (p == s && c >= delta) {
+        atomicAdd(&dc->guard_buckets, 1ull);
+        atomicAdd(&dc->guard_keys, (unsigned long long)c);
+      }
       if (c == 1) {
         w.A[o + p] = v;
         if (PAIRS) w.Av[o + p] = w.Bv[o + p];
@@ -531,14 +537,18 @@ __device__ __forceinline__ uint32_t size_class(uint32_t n) {
   return n <= 256 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 8u;
 }
 
+// recs: entries are (offset, size) pairs (uint2, the block-local sort's
+// list) instead of record indices
 __global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t ncls,
-                             uint32_t* lists, uint32_t* counts, const uint32_t* gate) {
+                             uint32_t* lists, uint32_t* counts, const uint32_t* gate, int recs) {
   if (pcf_aborted(gate)) return;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31;
   uint32_t cls = kMaxClasses;
+  BRec r;
+  r.off = r.n = 0;
   if (i < nb) {
-    const BRec r = br[i];
+    r = br[i];
     if ((r.kind & BK_LEAF) && r.n > 0) cls = min(size_class(r.n), ncls - 1);
   }
 #pragma unroll
@@ -549,7 +559,11 @@ __global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t 
     uint32_t base = 0;
     if ((int)lane == leader) base = atomicAdd(&counts[k], (uint32_t)__popc(bal));
     base = __shfl_sync(~0u, base, leader);
-    if (cls == k) lists[(size_t)k * nb + base + __popc(bal & lanemask_lt_())] = i;
+    if (cls == k) {
+      const size_t at = (size_t)k * nb + base + __popc(bal & lanemask_lt_());
+      if (recs) reinterpret_cast<uint2*>(lists)[at] = make_uint2(r.off, r.n);
+      else lists[at] = i;
+    }
   }
 }
 
@@ -605,7 +619,7 @@ __global__ void __launch_bounds__(kWarps * 32, 8) k_onchip(const BRec* __restric
         if (it.std) std_sort<PAIRS>(w, it.o, it.n, lane);
         else
           ok = learn_step<PAIRS, SPLINE, SRANGE>(w, geo, it, r.seed, kt, P, ptab, top, lane, root,
-                                                 rmn, rmx);
+                                                 rmn, rmx, pcf_counters(status));
         root = false;
       }
     }
@@ -680,7 +694,7 @@ constexpr uint32_t kSampRegs = 3;
 template <uint32_t NT, bool SPLINE, bool SRANGE>
 __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item it, uint64_t seed,
                                uint32_t kt, const Policy& P, const uint16_t* __restrict__ ptab,
-                               CtaShared<NT>& sh, bool root) {
+                               CtaShared<NT>& sh, bool root, DecisionCounters* dc) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t o = it.o, n = it.n;
   const ushort4 q = __ldg(reinterpret_cast<const ushort4*>(ptab) + n);
@@ -788,6 +802,7 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     if (wid == 0) std_sort<false>(w, o, n, lane);
     return;
   }
+  if (tid == 0) atomicAdd(&dc->bucketings, 1ull);
   const BinModel bm = *w.bm;
 #pragma unroll
   for (uint32_t u = 0; u < kSampRegs; ++u) {
@@ -862,6 +877,10 @@ __device__ void learn_step_cta(const Slice& w, const OnchipGeo& geo, const Item 
     const uint32_t c = w.cnt[j], e = w.cur[j], s = e - c;
     const uint64_t v = w.B[o + p];
     const bool stdc = c >= delta || c < P.tau;
+    if (p == s && c >= delta) {
+      atomicAdd(&dc->guard_buckets, 1ull);
+      atomicAdd(&dc->guard_keys, (unsigned long long)c);
+    }
     if (c == 1) {
       w.A[o + p] = v;
     } else if (stdc && c <= kRank) {
@@ -944,7 +963,8 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
         if (wid == 0) std_sort<false>(w, it.o, it.n, lane);
       } else {
         learn_step_cta<NT, SPLINE, SRANGE>(w, geo, it, r.seed, kt, P, ptab, sh,
-                                           top == 1 && it.o == 0 && it.n == n);
+                                           top == 1 && it.o == 0 && it.n == n,
+                                           pcf_counters(status));
       }
       __syncthreads();
     }
@@ -968,22 +988,24 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
 // ascending order either way.
 //
 // One CTA of NT threads per bucket of at most NT * KPT keys:
-//   1. each thread loads KPT keys (order-preserving integers) into
-//      registers; the CTA reduces min and max;
-//   2. one equal-width split of [min, max] into M = 2^ceil(log2 n) parts:
-//      part(v) = (v - min) >> shift, shift chosen so that parts < M (an MSD
-//      radix digit of the key's offset from the minimum; it needs no model,
-//      no samples and no division); counts by shared atomics, an exclusive
-//      scan, and each key written to its part's range of B;
+//   1. the bucket's keys were staged in shared memory (P) by cp.async while
+//      the CTA sorted the previous bucket; each thread takes KPT of them
+//      (order-preserving integers) into registers and the CTA reduces min
+//      and max, then stages the next bucket;
+//   2. one equal-width split of [min, max] into M = 2^(ceil(log2 n) + OVS)
+//      parts: part(v) = (v - min) >> shift, shift chosen so that parts < M
+//      (an MSD radix digit of the key's offset from the minimum; no model,
+//      no samples, no division); 16-bit counts by shared atomics, their
+//      exclusive scan, and every key written to its part's range of B;
 //   3. every key's final position: its part's start plus its rank among the
 //      part's keys (smaller, or equal and earlier in B), written straight to
 //      the output (consecutive threads write nearly consecutive positions).
 //      Parts of more than kLeafRank keys (skewed or duplicate-heavy buckets)
-//      are listed and sorted afterwards by one warp each (rank, bitonic or
-//      merge sort in shared memory).
-// The count array is stored transposed (part d of thread chunk d / r at
-// column d % r), so that the scan's per-thread chunks are read without bank
-// conflicts.
+//      are listed and sorted afterwards by one warp each (leaf_big_part).
+// Counts are u16 pairs in 32-bit words, in groups of eight (one uint4); the
+// scan gives each thread q consecutive groups, stored transposed (group i of
+// thread t at uint4 index i * NT + t) so that its vector loads are free of
+// bank conflicts.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kLeafRank = 16;
 
@@ -994,49 +1016,111 @@ struct LeafShared {
   uint32_t n_big;
 };
 
-// B [cap] u64 | A2 [cap] u64 (merge scratch) | H [cap] u32 | big [cap / kLeafRank + 1] u32
+// B [cap] u64 | P [cap] u64 (the next bucket, staged) | H [2 cap] u32 (the
+// u16 counts; afterwards the merge scratch of the large parts) | big list
 __host__ __device__ inline size_t leaf_sort_smem(uint32_t cap) {
-  return (size_t)cap * 16 + (size_t)cap * 4 + ((size_t)cap / kLeafRank + 1) * 4 + 16;
+  return (size_t)cap * 24 + ((size_t)cap / kLeafRank + 1) * 4 + 16;
 }
 
-template <uint32_t NT, uint32_t KPT>
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// one part of more than kLeafRank keys, B[s, s + c): sorted by one warp
+// (scratch at the same offsets of S) and written to out[s, s + c)
+__device__ __noinline__ void leaf_big_part(uint64_t* B, uint64_t* S, uint32_t s, uint32_t c,
+                                           uint64_t* out, uint32_t off, uint32_t kt,
+                                           uint32_t lane, uint32_t* status) {
+  (void)status;
+  uint64_t mn = ~0ull, mx = 0ull;
+  for (uint32_t i = lane; i < c; i += 32) {
+    const uint64_t v = B[s + i];
+    mn = v < mn ? v : mn;
+    mx = v > mx ? v : mx;
+  }
+#pragma unroll
+  for (int d = 16; d; d >>= 1) {
+    const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
+    const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
+    mn = a < mn ? a : mn;
+    mx = b > mx ? b : mx;
+  }
+  if (mn != mx) {  // (one value: already in order)
+    Slice w;
+    w.A = B;
+    w.B = S;
+    w.Av = w.Bv = nullptr;
+    std_sort<false>(w, s, c, lane);
+  }
+  for (uint32_t i = lane; i < c; i += 32)
+    if (PCF_IN_KEYS(off + s + i, status)) out[off + s + i] = bits_of_ord(B[s + i], kt);
+  __syncwarp();
+}
+
+template <uint32_t NT, uint32_t KPT, uint32_t OVS>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
-    k_leaf_sort(const BRec* __restrict__ br, const uint32_t* __restrict__ list,
-                const uint32_t* __restrict__ count, const uint64_t* __restrict__ X, uint64_t* out,
-                uint32_t kt, uint32_t* status) {
+    k_leaf_sort(const uint2* __restrict__ list, const uint32_t* __restrict__ count,
+                const uint64_t* __restrict__ X, uint64_t* out, uint32_t kt, uint32_t* status) {
   constexpr uint32_t CAP = NT * KPT, NW = NT / 32;
   constexpr uint32_t LNT = NT == 32 ? 5 : NT == 64 ? 6 : NT == 128 ? 7 : NT == 256 ? 8
                          : NT == 512 ? 9 : 10;
+  constexpr uint32_t QMAX = (KPT << OVS) / 8 > 0 ? (KPT << OVS) / 8 : 1;
   static_assert((1u << LNT) == NT, "NT must be a power of two, 32..1024");
+  static_assert(KPT == 8 && OVS <= 2, "counts sized for KPT = 8, M <= 4 cap");
   if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ LeafShared<NT> sh;
   uint64_t* B = reinterpret_cast<uint64_t*>(smem_raw);
-  uint64_t* A2 = B + CAP;
-  uint32_t* H = reinterpret_cast<uint32_t*>(A2 + CAP);
-  uint32_t* big = H + CAP;
+  uint64_t* Pf = B + CAP;
+  uint32_t* H = reinterpret_cast<uint32_t*>(Pf + CAP);
+  uint32_t* big = H + 2 * CAP;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nitems = *count;
-  for (uint32_t li = blockIdx.x; li < nitems; li += gridDim.x) {
-    const BRec r = br[list[li]];
-    const uint32_t off = r.off, n = r.n;
-    const uint32_t m = n > 1 ? 32u - __clz(n - 1) : 0u;  // M = 2^m >= n parts
-    const uint32_t M = 1u << m;
-    const uint32_t lr = m > LNT ? m - LNT : 0u;          // r = 2^lr parts per thread chunk
-    const uint32_t rmask = (1u << lr) - 1u;
-    auto hix = [&](uint32_t d) -> uint32_t { return ((d & rmask) << LNT) | (d >> lr); };
+  const uint32_t G = gridDim.x;
+  uint32_t li = blockIdx.x;
+  if (li >= nitems) return;
+  uint2 rec = list[li];
+  uint2 rec1 = li + G < nitems ? list[li + G] : make_uint2(0u, 0u);
+#pragma unroll
+  for (uint32_t j = 0; j < KPT; ++j) {
+    const uint32_t i = tid + j * NT;
+    if (i < rec.y) cp_async8(Pf + i, X + rec.x + i);
+  }
+  cp_async_commit();
+  for (; li < nitems; li += G) {
+    const uint32_t off = rec.x, n = rec.y;
+    const uint2 rec2 = li + 2 * G < nitems ? list[li + 2 * G] : make_uint2(0u, 0u);
+    const uint32_t m = max(4u, (n > 1 ? 32u - __clz(n - 1) : 0u) + OVS);
+    const uint32_t M = 1u << m;                       // parts, >= 16
+    const uint32_t Gg = M >> 3;                       // groups of eight counts
+    const uint32_t lq = Gg > NT ? m - 3 - LNT : 0u;   // q = 2^lq groups per thread
+    const uint32_t qmask = (1u << lq) - 1u;
+    // u16 slot of part d
+    auto slot = [&](uint32_t d) -> uint32_t {
+      const uint32_t g = d >> 3;
+      return ((((g & qmask) << LNT) | (g >> lq)) << 3) | (d & 7u);
+    };
+    cp_async_wait_all();
+    __syncthreads();  // the bucket is staged in P (every thread's copies)
     uint64_t k[KPT];
     uint64_t mn = ~0ull, mx = 0ull;
 #pragma unroll
     for (uint32_t j = 0; j < KPT; ++j) {
       const uint32_t i = tid + j * NT;
-      k[j] = i < n ? ord_of(__ldg(X + off + i), kt) : 0ull;
+      k[j] = i < n ? ord_of(Pf[i], kt) : 0ull;
       if (i < n) {
         mn = k[j] < mn ? k[j] : mn;
         mx = k[j] > mx ? k[j] : mx;
       }
     }
-    for (uint32_t d = tid; d < M; d += NT) H[d] = 0;
+    for (uint32_t d = tid; d < (M >> 1); d += NT) H[d] = 0u;
     if (tid == 0) sh.n_big = 0;
 #pragma unroll
     for (int d = 16; d; d >>= 1) {
@@ -1049,7 +1133,14 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
       sh.mn[wid] = mn;
       sh.mx[wid] = mx;
     }
-    __syncthreads();
+    __syncthreads();  // P is free again; H zeroed
+    // stage the next bucket while this one is sorted
+#pragma unroll
+    for (uint32_t j = 0; j < KPT; ++j) {
+      const uint32_t i = tid + j * NT;
+      if (i < rec1.y) cp_async8(Pf + i, X + rec1.x + i);
+    }
+    cp_async_commit();
 #pragma unroll
     for (uint32_t w = 0; w < NW; ++w) {
       mn = sh.mn[w] < mn ? sh.mn[w] : mn;
@@ -1061,81 +1152,96 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
         const uint32_t i = tid + j * NT;
         if (i < n && PCF_IN_KEYS(off + i, status)) out[off + i] = bits_of_ord(k[j], kt);
       }
-      __syncthreads();
-      continue;
-    }
-    const uint32_t nb = 64u - (uint32_t)__clzll((long long)(mx - mn));
-    const uint32_t sft = nb > m ? nb - m : 0u;
-    uint32_t dg[KPT], rk[KPT];
+    } else {
+      const uint32_t nb = 64u - (uint32_t)__clzll((long long)(mx - mn));
+      const uint32_t sft = nb > m ? nb - m : 0u;
+      uint32_t sl[KPT], rk[KPT];
 #pragma unroll
-    for (uint32_t j = 0; j < KPT; ++j) {
-      const uint32_t i = tid + j * NT;
-      dg[j] = (uint32_t)((k[j] - mn) >> sft);
-      rk[j] = i < n ? atomicAdd(&H[hix(dg[j])], 1u) : 0u;
-    }
-    __syncthreads();
-    // exclusive scan of the part counts: thread t owns parts [t r, t r + r),
-    // stored at H[c * NT + t], c < r
-    {
-      const uint32_t rr = 1u << lr;
-      uint32_t sum = 0;
-      if (tid * rr < M)
-        for (uint32_t c = 0; c < rr; ++c) sum += H[(c << LNT) | tid];
-      const uint32_t inc = wscan(sum, lane);
-      if (lane == 31) sh.wsum[wid] = inc;
-      __syncthreads();
-      uint32_t run = inc - sum;
-#pragma unroll
-      for (uint32_t w = 0; w < NW; ++w) run += w < wid ? sh.wsum[w] : 0u;
-      if (tid * rr < M)
-        for (uint32_t c = 0; c < rr; ++c) {
-          const uint32_t v = H[(c << LNT) | tid];
-          H[(c << LNT) | tid] = run;
-          run += v;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (uint32_t j = 0; j < KPT; ++j) {
-      const uint32_t i = tid + j * NT;
-      if (i < n) {
-        const uint32_t p = H[hix(dg[j])] + rk[j];
-        if (PCF_IN(p, n, status)) B[p] = k[j];
+      for (uint32_t j = 0; j < KPT; ++j) {
+        const uint32_t i = tid + j * NT;
+        sl[j] = slot((uint32_t)((k[j] - mn) >> sft));
+        const uint32_t hs = (sl[j] & 1u) << 4;
+        rk[j] = i < n ? (atomicAdd(&H[sl[j] >> 1], 1u << hs) >> hs) & 0xFFFFu : 0u;
       }
-    }
-    __syncthreads();
+      __syncthreads();
+      // exclusive scan of the counts: thread t owns groups [t q, t q + q)
+      {
+        uint4* H4 = reinterpret_cast<uint4*>(H);
+        const uint32_t q = 1u << lq;
+        const bool own = tid * q < Gg;
+        uint4 gv[QMAX];
+        uint32_t sum = 0;
 #pragma unroll
-    for (uint32_t j = 0; j < KPT; ++j) {
-      const uint32_t p = tid + j * NT;
-      if (p < n) {
-        const uint64_t v = B[p];
-        const uint32_t d = (uint32_t)((v - mn) >> sft);
-        const uint32_t s = H[hix(d)];
-        const uint32_t e = d + 1 < M ? H[hix(d + 1)] : n;
-        const uint32_t c = e - s;
-        if (c > kLeafRank) {
-          if (p == s) big[atomicAdd(&sh.n_big, 1u)] = s | (c << 16);
-          continue;
+        for (uint32_t i = 0; i < QMAX; ++i) {
+          if (own && i < q) {
+            gv[i] = H4[(i << LNT) | tid];
+            // eight counts <= 8192 each: the packed halves never carry
+            const uint32_t t4 = gv[i].x + gv[i].y + gv[i].z + gv[i].w;
+            sum += (t4 & 0xFFFFu) + (t4 >> 16);
+          }
         }
-        uint32_t pos = p;
-        if (c > 1) pos = s + rank_in(B, s, e, p, v);
-        if (PCF_IN_KEYS(off + pos, status)) out[off + pos] = bits_of_ord(v, kt);
+        const uint32_t inc = wscan(sum, lane);
+        if (lane == 31) sh.wsum[wid] = inc;
+        __syncthreads();
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (uint32_t w = 0; w < NW; ++w) run += w < wid ? sh.wsum[w] : 0u;
+        auto ex2 = [&](uint32_t v) -> uint32_t {
+          const uint32_t lo = v & 0xFFFFu;
+          const uint32_t r = run | ((run + lo) << 16);
+          run += lo + (v >> 16);
+          return r;
+        };
+#pragma unroll
+        for (uint32_t i = 0; i < QMAX; ++i) {
+          if (own && i < q) {
+            uint4 o;
+            o.x = ex2(gv[i].x);
+            o.y = ex2(gv[i].y);
+            o.z = ex2(gv[i].z);
+            o.w = ex2(gv[i].w);
+            H4[(i << LNT) | tid] = o;
+          }
+        }
       }
+      __syncthreads();
+      const uint16_t* H16 = reinterpret_cast<const uint16_t*>(H);
+#pragma unroll
+      for (uint32_t j = 0; j < KPT; ++j) {
+        const uint32_t i = tid + j * NT;
+        if (i < n) {
+          const uint32_t p = (uint32_t)H16[sl[j]] + rk[j];
+          if (PCF_IN(p, n, status)) B[p] = k[j];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (uint32_t j = 0; j < KPT; ++j) {
+        const uint32_t p = tid + j * NT;
+        if (p < n) {
+          const uint64_t v = B[p];
+          const uint32_t d = (uint32_t)((v - mn) >> sft);
+          const uint32_t s = H16[slot(d)];
+          const uint32_t e = d + 1 < M ? (uint32_t)H16[slot(d + 1)] : n;
+          const uint32_t c = e - s;
+          uint32_t pos = p;
+          if (c > kLeafRank) {
+            if (p == s) big[atomicAdd(&sh.n_big, 1u)] = s | (c << 16);
+            continue;
+          }
+          if (c > 1) pos = s + rank_in(B, s, e, p, v);
+          if (PCF_IN_KEYS(off + pos, status)) out[off + pos] = bits_of_ord(v, kt);
+        }
+      }
+      __syncthreads();
+      const uint32_t nbig = sh.n_big;
+      for (uint32_t b = wid; b < nbig; b += NW)
+        leaf_big_part(B, reinterpret_cast<uint64_t*>(H), big[b] & 0xFFFFu, big[b] >> 16, out,
+                      off, kt, lane, status);
     }
-    __syncthreads();
-    const uint32_t nbig = sh.n_big;
-    for (uint32_t b = wid; b < nbig; b += NW) {
-      const uint32_t s = big[b] & 0xFFFFu, c = big[b] >> 16;
-      Slice w;
-      w.A = B;
-      w.B = A2;
-      w.Av = w.Bv = nullptr;
-      std_sort<false>(w, s, c, lane);
-      for (uint32_t i = lane; i < c; i += 32)
-        if (PCF_IN_KEYS(off + s + i, status)) out[off + s + i] = bits_of_ord(B[s + i], kt);
-      __syncwarp();
-    }
-    __syncthreads();
+    __syncthreads();  // B, H and the list are reused by the next bucket
+    rec = rec1;
+    rec1 = rec2;
   }
 }
 
@@ -1215,27 +1321,28 @@ static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const u
   return cudaGetLastError();
 }
 
-// the block-local sort of one size class: NT threads, 8 keys each
+// the block-local sort of one size class: NT threads, 8 keys each, parts
+// 2^(ceil(log2 n) + 1)
 template <uint32_t NT>
-static cudaError_t launch_leaf_sort(const LaunchCfg& c, const BRec* br, const uint32_t* list,
-                                    const uint32_t* count, const uint64_t* X, uint64_t* out) {
-  constexpr uint32_t KPT = 8;
+static cudaError_t launch_leaf_sort(const LaunchCfg& c, const uint2* list, const uint32_t* count,
+                                    const uint64_t* X, uint64_t* out) {
+  constexpr uint32_t KPT = 8, OVS = 1;
   const size_t smem = leaf_sort_smem(NT * KPT);
-  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT>);
+  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT, OVS>);
   if (e) return e;
   static int per_sm_cache[64] = {0};
   int dev = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   int per_sm = dev >= 0 && dev < 64 ? per_sm_cache[dev] : 0;
   if (per_sm <= 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT>, (int)NT,
-                                                      smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT, OVS>,
+                                                      (int)NT, smem);
     if (e) return e;
     per_sm = per_sm > 0 ? per_sm : 1;
     if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
   }
-  k_leaf_sort<NT, KPT><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT, smem,
-                         c.stream>>>(br, list, count, X, out, c.kt, c.status);
+  k_leaf_sort<NT, KPT, OVS><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT,
+                              smem, c.stream>>>(list, count, X, out, c.kt, c.status);
   return cudaGetLastError();
 }
 
@@ -1260,7 +1367,9 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
   const uint32_t ncls = onchip_classes(leaf_cap);
   cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kMaxClasses, c.stream);
   if (e) return e;
-  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts, c.status);
+  const bool recs = c.leaf_sort && !c.pairs;
+  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts, c.status,
+                                                        recs ? 1 : 0);
   count_launch(c);
   if ((e = cudaGetLastError())) return e;
   uint32_t cls = 0;
@@ -1268,14 +1377,15 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
     const uint32_t hi = min(capw, leaf_cap);
     const OnchipGeo g = onchip_geometry(hi, P, c.pairs);
     const uint32_t* list = lists + (size_t)cls * nb;
-    if (c.leaf_sort && !c.pairs) {
+    if (recs) {
       // the whole bucket by the block-local Standard-Sort, NT = capw / 8
-      if (capw <= 256) e = launch_leaf_sort<32>(c, br, list, counts + cls, X, out);
-      else if (capw <= 512) e = launch_leaf_sort<64>(c, br, list, counts + cls, X, out);
-      else if (capw <= 1024) e = launch_leaf_sort<128>(c, br, list, counts + cls, X, out);
-      else if (capw <= 2048) e = launch_leaf_sort<256>(c, br, list, counts + cls, X, out);
-      else if (capw <= 4096) e = launch_leaf_sort<512>(c, br, list, counts + cls, X, out);
-      else e = launch_leaf_sort<1024>(c, br, list, counts + cls, X, out);
+      const uint2* rl = reinterpret_cast<const uint2*>(lists) + (size_t)cls * nb;
+      if (capw <= 256) e = launch_leaf_sort<32>(c, rl, counts + cls, X, out);
+      else if (capw <= 512) e = launch_leaf_sort<64>(c, rl, counts + cls, X, out);
+      else if (capw <= 1024) e = launch_leaf_sort<128>(c, rl, counts + cls, X, out);
+      else if (capw <= 2048) e = launch_leaf_sort<256>(c, rl, counts + cls, X, out);
+      else if (capw <= 4096) e = launch_leaf_sort<512>(c, rl, counts + cls, X, out);
+      else e = launch_leaf_sort<1024>(c, rl, counts + cls, X, out);
       if (e) return e;
     } else if (cls > 0 && !c.pairs) {
       // a CTA per bucket (one slice per CTA), more threads for larger buckets

@@ -49,7 +49,9 @@ class CallStats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_uint64), ("global_passes", ctypes.c_uint64),
                 ("leaf_buckets", ctypes.c_uint64), ("fallback_buckets", ctypes.c_uint64),
                 ("fallback_keys", ctypes.c_uint64), ("bytes_moved", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64), ("fallback_splits", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64), ("fallback_splits", ctypes.c_uint64),
+                ("guard_buckets", ctypes.c_uint64), ("guard_keys", ctypes.c_uint64),
+                ("bucketings", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -349,34 +349,3 @@ def test_host_batch_pipelined(ctx, pinned):
     for u, h in zip(us, hu):
         ref, _ = oracle.sort(u)
         assert same_bits(h.numpy().view(np.uint64), ref)
-
-
-@pytest.mark.parametrize("dist", ["normal"])
-def test_full_size_config2(ctx, dist):
-    # n = 10^8 (the benchmark's array size): exact comparison with the oracle
-    x = W.f64_keys(dist, 10**8, 1)
-    got = gpu_sort(ctx, x, seed=0)
-    ref, _ = oracle.sort(x, seed=0)
-    assert same_bits(got, ref)
-
-
-@pytest.mark.parametrize("dist", ["lognormal", "exponential", "mixture"])
-def test_full_size_config2_properties(ctx, dist):
-    # n = 10^8: sorted under the total order and a permutation of the input
-    x = W.f64_keys(dist, 10**8, {"lognormal": 2, "exponential": 3, "mixture": 4}[dist])
-    t = to_dev(x)
-    out = torch.empty_like(t)
-    ctx.sort_keys(t, out, key_type="f64")
-    # IEEE total order as a signed int64 key: negative values flip their
-    # 63 magnitude bits, non-negative values keep their bits
-    low63 = torch.tensor(2**63 - 1, dtype=torch.int64, device="cuda")
-    bits = out.view(torch.int64)
-    ordk = torch.where(bits < 0, bits ^ low63, bits)
-    assert bool((ordk[1:] >= ordk[:-1]).all())
-    ib = t.view(torch.int64)
-    ordi = torch.where(ib < 0, ib ^ low63, ib)
-    assert bool((torch.sort(ordi).values == ordk).all())
-    # sampled order statistics: numpy's selection at fixed ranks
-    idx = np.array([0, 12345, 5 * 10**7, 10**8 - 1])
-    ref = np.partition(x, idx)[idx]
-    assert same_bits(out.cpu().numpy()[idx], ref)
