@@ -97,7 +97,7 @@ typedef struct {
  * Standard-Sort of the whole bucket (one equal-width MSD split of its range,
  * then ranks within the parts), 2 = the remaining Learned-Sort steps of
  * Algorithm 1 run in shared memory.  Key-value sorts always take 2.
- * Zero fields keep the current value.  Default: {11, 14, 4096, 1}. */
+ * Zero fields keep the current value.  Default: {11, 14, 8192, 1}. */
 typedef struct {
   uint32_t max_digit_bits;
   uint32_t tile_log2;

@@ -1,8 +1,10 @@
 """Autotuner for the speed-only knobs of the library (pcf_tuning).
 
 The knobs are the widest bucket-id digit scattered per global pass
-(max_digit_bits), the keys per count tile (tile_log2) and the largest
-bucket finished on chip (leaf_cap).  None of them changes alpha, beta,
+(max_digit_bits), the keys per count tile (tile_log2), the largest bucket
+finished on chip (leaf_cap) and how keys-only sorts finish it (leaf_mode: a
+block-local sort, or the remaining Learned-Sort steps).  None of them
+changes alpha, beta,
 gamma, delta, tau or the output, so the tuner may pick any of them; it times
 each candidate on a sample of the caller's workload with CUDA events and keeps
 the fastest.  Results are cached in a JSON file keyed by workload class.
@@ -15,8 +17,9 @@ from . import pcfsort
 
 DEFAULT_GRID = {
     "max_digit_bits": (10, 11),
-    "tile_log2": (14, 15),
-    "leaf_cap": (1024, 4096),
+    "tile_log2": (13, 14),
+    "leaf_cap": (2048, 8192),
+    "leaf_mode": (1, 2),
 }
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")

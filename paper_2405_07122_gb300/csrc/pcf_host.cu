@@ -104,7 +104,7 @@ struct pcf_ctx {
   int device = 0;
   int num_sms = 0;
   Policy policy{3, 3, 3, 3, 4, MODEL_PCF, 100, RANGE_ARRAY, 0};
-  pcf_tuning tuning{11, 14, 4096, 1};
+  pcf_tuning tuning{11, 14, 8192, 1};
   std::string last_err;
   pcf_call_stats stats{};
   bool timing = false;
@@ -768,7 +768,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   // the largest bucket finished on chip (the alpha..delta table covers the
   // tuning's leaf_cap, at least this)
   const uint32_t cap = onchip_cap(ctx->tuning.leaf_cap, ctx->policy, pairs);
-  const size_t olist_per_bucket = (size_t)8 * onchip_classes(cap);
+  const size_t olist_per_bucket =
+      (size_t)8 * (lc.leaf_sort ? leaf_sort_classes(cap) : onchip_classes(cap));
   CK(ensure_ptab(ctx, st));
   const uint16_t* ptab = as<uint16_t>(ctx->ptab);
   Timer tm(ctx, st);

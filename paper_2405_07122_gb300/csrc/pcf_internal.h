@@ -316,12 +316,16 @@ OnchipGeo onchip_geometry(uint32_t capw, const Policy& P, bool pairs);
 // 8192 keys; onchip_classes(cap) of them are used below leaf_cap = cap.
 constexpr uint32_t kMaxClasses = 6;
 uint32_t onchip_classes(uint32_t leaf_cap);
+// The block-local sort's classes (0, 64], (64, 128], (128, 256], (256, 512],
+// ... up to leaf_cap: leaf_sort_classes(cap) of them, at most kMaxLeafClasses.
+constexpr uint32_t kMaxLeafClasses = 8;
+uint32_t leaf_sort_classes(uint32_t leaf_cap);
 // The largest bucket finished on chip: leaf_cap (key-value sorts at most
 // 1024), halved until the policy's slice fits one block's shared memory.
 uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs);
-// lists: onchip_classes(leaf_cap) x nb x 8 bytes of scratch (u32 record
-// indices, or (offset, size) pairs for the block-local sort); counts:
-// kMaxClasses u32
+// lists: (block-local sort: leaf_sort_classes, else onchip_classes)(leaf_cap)
+// x nb x 8 bytes of scratch (u32 record indices, or (offset, size) pairs
+// for the block-local sort); counts: kMaxLeafClasses u32
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts);

@@ -657,13 +657,13 @@ __global__ void __launch_bounds__(256, 2) k_scatter1(const Seg* segs, uint32_t S
   if (g.status != SEG_BUCKET) return;
   const uint32_t tt = t - tile_base[s];
   const uint32_t D = 1u << g.b1;
-  ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, true);
   const uint32_t seg_base = cmat[g.cbase1];  // exclusive prefix at the segment's first entry
+  const uint64_t tile_off = g.off + (uint64_t)tt * tile_keys;
+  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, g.off + g.n - tile_off);
+  ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, true);
   for (uint32_t d = threadIdx.x; d < D; d += 256)
     sm.gofs[d] = (uint32_t)g.off + (cmat[g.cbase1 + (uint64_t)d * g.tiles1 + tt] - seg_base);
   __syncthreads();
-  const uint64_t tile_off = g.off + (uint64_t)tt * tile_keys;
-  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, g.off + g.n - tile_off);
   scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, kb.jbuf, g.b2, kb.src, kb.src_v, nullptr, kb.tmp,
                          kb.tmp_v, kb.tmp_aux, status);
 }
@@ -738,18 +738,35 @@ __global__ void __launch_bounds__(256) k_hist2(const Group* groups, uint32_t n_g
   __syncthreads();
   const uint64_t base = gr.off + (uint64_t)tt * tile_keys;
   const uint64_t end = min(gr.off + gr.n, base + tile_keys);
-  constexpr int U = 16;
-  for (uint64_t i0 = base; i0 < end; i0 += 256 * U) {
-    uint32_t d[U];
+  // 16-byte loads of eight digits over the aligned middle, single digits
+  // at the ragged ends
+  const uint64_t a0 = min(end, (base + 7) & ~(uint64_t)7), a1 = max(a0, end & ~(uint64_t)7);
+  {
+    // fewer than 8 digits at each end: threads 0-7 the head, 8-15 the tail
+    // (every lane takes part, as the warp-aggregated increment needs)
+    const uint64_t i = threadIdx.x < 8 ? base + threadIdx.x : a1 + (threadIdx.x - 8);
+    const bool v = threadIdx.x < 8 ? i < a0 : (threadIdx.x < 16 && i < end);
+    hist_inc(hist, v ? (uint32_t)__ldg(aux + i) : 0u, v, agg);
+  }
+  const uint4* v4 = reinterpret_cast<const uint4*>(aux + a0);
+  const uint32_t n4 = (uint32_t)((a1 - a0) >> 3);
+  constexpr int U = 2;
+  for (uint32_t q0 = 0; q0 < n4; q0 += 256 * U) {
+    uint4 w[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
-      d[u] = i < end ? (uint32_t)__ldg(aux + i) : 0u;
+      const uint32_t q = q0 + (uint32_t)u * 256 + threadIdx.x;
+      w[u] = q < n4 ? __ldg(v4 + q) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint64_t i = i0 + (uint64_t)u * 256 + threadIdx.x;
-      hist_inc(hist, d[u], i < end, agg);
+      const bool v = q0 + (uint32_t)u * 256 + threadIdx.x < n4;
+      const uint32_t ws[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        hist_inc(hist, ws[h] & 0xFFFFu, v, agg);
+        hist_inc(hist, ws[h] >> 16, v, agg);
+      }
     }
   }
   __syncthreads();
@@ -772,13 +789,13 @@ __global__ void __launch_bounds__(256, 2) k_scatter2(const Group* groups, uint32
   if (segs[gr.seg].b2 == 0) return;  // one-digit id: copied, not scattered
   const uint32_t D = 1u << segs[gr.seg].b2;
   const uint32_t tt = t - g_tile_scan[G];
-  ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, false);
   const uint32_t gbase = cmat2[gr.cbase];
+  const uint64_t tile_off = gr.off + (uint64_t)tt * tile_keys;
+  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, gr.off + gr.n - tile_off);
+  ScatterSmem sm = carve_scatter(smem_raw, D, PAIRS, false);
   for (uint32_t d = threadIdx.x; d < D; d += 256)
     sm.gofs[d] = (uint32_t)gr.off + (cmat2[gr.cbase + (uint64_t)d * gr.tiles + tt] - gbase);
   __syncthreads();
-  const uint64_t tile_off = gr.off + (uint64_t)tt * tile_keys;
-  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, gr.off + gr.n - tile_off);
   scatter_tile<2, PAIRS>(sm, D, tile_off, tile_n, nullptr, 0, kb.tmp, kb.tmp_v, kb.tmp_aux, kb.out,
                          kb.out_v, nullptr, status);
 }
@@ -1437,8 +1454,8 @@ cudaError_t launch_scatter1(const LaunchCfg& c, const Seg* segs, uint32_t S,
     count_launch(c);
   } else {
     if ((e = set_smem(k_scatter1<false>, sm))) return e;
-    k_scatter1<false><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb, tpool,
-                                                       cmat, c.status);
+    k_scatter1<false><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb,
+                                                                tpool, cmat, c.status);
     count_launch(c);
   }
   return cudaGetLastError();
@@ -1493,9 +1510,8 @@ cudaError_t launch_scatter2(const LaunchCfg& c, const Group* groups, uint32_t n_
     count_launch(c);
   } else {
     if ((e = set_smem(k_scatter2<false>, sm))) return e;
-    k_scatter2<false><<<n_tiles_bound, 256, sm, c.stream>>>(groups, n_groups, segs, g_tile_scan,
-                                                            total_tiles, tile_keys, kb, cmat2,
-                                                            c.status);
+    k_scatter2<false><<<n_tiles_bound, 256, sm, c.stream>>>(
+        groups, n_groups, segs, g_tile_scan, total_tiles, tile_keys, kb, cmat2, c.status);
     count_launch(c);
   }
   return cudaGetLastError();

@@ -128,6 +128,20 @@ __device__ __forceinline__ uint32_t rank_in(const uint64_t* K, uint32_t s, uint3
   return r;
 }
 
+// The same rank for keys whose offsets from a common base m differ only in
+// their low 32 bits (keys of one part of a split whose shift is at most
+// 32): the low words of the offsets decide.  vl = low word of v - m.
+__device__ __forceinline__ uint32_t rank_in_lo32(const uint64_t* K, uint32_t s, uint32_t e,
+                                                 uint32_t p, uint32_t vl, uint32_t ml) {
+  const uint32_t* K32 = reinterpret_cast<const uint32_t*>(K);
+  uint32_t r = 0;
+  for (uint32_t t = s; t < e; ++t) {
+    const uint32_t ul = K32[2 * t] - ml;
+    r += (ul < vl || (ul == vl && t < p)) ? 1u : 0u;
+  }
+  return r;
+}
+
 // [o, o + c) of A ranked into B, then copied back; c <= kRank * 32.  Ties are
 // broken by position, so equal keys keep their order (stable).
 template <bool PAIRS>
@@ -537,22 +551,29 @@ __device__ __forceinline__ uint32_t size_class(uint32_t n) {
   return n <= 256 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 8u;
 }
 
-// recs: entries are (offset, size) pairs (uint2, the block-local sort's
-// list) instead of record indices
+// The block-local sort's classes: (0, 64], (64, 128], (128, 256], then
+// doubling up to leaf_cap.
+__device__ __forceinline__ uint32_t leaf_size_class(uint32_t n) {
+  return n <= 64 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 6u;
+}
+
+// recs: entries are (offset, size) pairs (uint2) in the block-local sort's
+// classes instead of record indices in the Learned-Sort kernels' classes
 __global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t ncls,
                              uint32_t* lists, uint32_t* counts, const uint32_t* gate, int recs) {
   if (pcf_aborted(gate)) return;
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31;
-  uint32_t cls = kMaxClasses;
+  uint32_t cls = kMaxLeafClasses;
   BRec r;
   r.off = r.n = 0;
   if (i < nb) {
     r = br[i];
-    if ((r.kind & BK_LEAF) && r.n > 0) cls = min(size_class(r.n), ncls - 1);
+    if ((r.kind & BK_LEAF) && r.n > 0)
+      cls = min(recs ? leaf_size_class(r.n) : size_class(r.n), ncls - 1);
   }
 #pragma unroll
-  for (uint32_t k = 0; k < kMaxClasses; ++k) {
+  for (uint32_t k = 0; k < kMaxLeafClasses; ++k) {
     const uint32_t bal = __ballot_sync(~0u, cls == k);
     if (!bal) continue;
     const int leader = __ffs(bal) - 1;
@@ -1073,7 +1094,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
                          : NT == 512 ? 9 : 10;
   constexpr uint32_t QMAX = (KPT << OVS) / 8 > 0 ? (KPT << OVS) / 8 : 1;
   static_assert((1u << LNT) == NT, "NT must be a power of two, 32..1024");
-  static_assert(KPT == 8 && OVS <= 2, "counts sized for KPT = 8, M <= 4 cap");
+  static_assert(OVS <= 2 && KPT >= 1, "counts sized for M <= 4 cap");
   if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ LeafShared<NT> sh;
@@ -1229,7 +1250,10 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
             if (p == s) big[atomicAdd(&sh.n_big, 1u)] = s | (c << 16);
             continue;
           }
-          if (c > 1) pos = s + rank_in(B, s, e, p, v);
+          if (c > 1)
+            pos = s + (sft <= 32 ? rank_in_lo32(B, s, e, p, (uint32_t)v - (uint32_t)mn,
+                                                (uint32_t)mn)
+                                 : rank_in(B, s, e, p, v));
           if (PCF_IN_KEYS(off + pos, status)) out[off + pos] = bits_of_ord(v, kt);
         }
       }
@@ -1271,6 +1295,12 @@ static int num_sms_of_current_device() {
     cached[dev] = v > 0 ? v : 148;
   }
   return cached[dev];
+}
+
+uint32_t leaf_sort_classes(uint32_t leaf_cap) {
+  uint32_t k = 1;
+  for (uint32_t capw = 64; capw < leaf_cap && k < kMaxLeafClasses; capw *= 2) ++k;
+  return k;
 }
 
 uint32_t onchip_classes(uint32_t leaf_cap) {
@@ -1321,12 +1351,12 @@ static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const u
   return cudaGetLastError();
 }
 
-// the block-local sort of one size class: NT threads, 8 keys each, parts
-// 2^(ceil(log2 n) + 1)
-template <uint32_t NT>
+// the block-local sort of one size class: NT threads, KPT keys each,
+// parts 2^(ceil(log2 n) + 1)
+template <uint32_t NT, uint32_t KPT>
 static cudaError_t launch_leaf_sort(const LaunchCfg& c, const uint2* list, const uint32_t* count,
                                     const uint64_t* X, uint64_t* out) {
-  constexpr uint32_t KPT = 8, OVS = 1;
+  constexpr uint32_t OVS = 1;
   const size_t smem = leaf_sort_smem(NT * KPT);
   cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT, OVS>);
   if (e) return e;
@@ -1364,30 +1394,41 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts) {
   if (!nb) return cudaSuccess;
   // size classes (0, 256], (256, 512], (512, 1024], ... clipped to leaf_cap
-  const uint32_t ncls = onchip_classes(leaf_cap);
-  cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kMaxClasses, c.stream);
-  if (e) return e;
   const bool recs = c.leaf_sort && !c.pairs;
+  const uint32_t ncls = recs ? leaf_sort_classes(leaf_cap) : onchip_classes(leaf_cap);
+  cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kMaxLeafClasses, c.stream);
+  if (e) return e;
   k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts, c.status,
                                                         recs ? 1 : 0);
   count_launch(c);
   if ((e = cudaGetLastError())) return e;
+  if (recs) {
+    // the whole bucket by the block-local Standard-Sort: a warp for up to
+    // 256 keys (2, 4 or 8 per lane), then NT = capw / 8 threads
+    for (uint32_t cls = 0, capw = 64; cls < ncls; ++cls, capw *= 2) {
+      const uint2* rl = reinterpret_cast<const uint2*>(lists) + (size_t)cls * nb;
+      const uint32_t* cnt = counts + cls;
+      switch (capw) {
+        case 64: e = launch_leaf_sort<32, 2>(c, rl, cnt, X, out); break;
+        case 128: e = launch_leaf_sort<32, 4>(c, rl, cnt, X, out); break;
+        case 256: e = launch_leaf_sort<32, 8>(c, rl, cnt, X, out); break;
+        case 512: e = launch_leaf_sort<64, 8>(c, rl, cnt, X, out); break;
+        case 1024: e = launch_leaf_sort<128, 8>(c, rl, cnt, X, out); break;
+        case 2048: e = launch_leaf_sort<256, 8>(c, rl, cnt, X, out); break;
+        case 4096: e = launch_leaf_sort<512, 8>(c, rl, cnt, X, out); break;
+        default: e = launch_leaf_sort<1024, 8>(c, rl, cnt, X, out); break;
+      }
+      if (e) return e;
+      count_launch(c);
+    }
+    return cudaSuccess;
+  }
   uint32_t cls = 0;
   for (uint32_t capw = 256, lo = 0; lo < leaf_cap; capw *= 2, ++cls) {
     const uint32_t hi = min(capw, leaf_cap);
     const OnchipGeo g = onchip_geometry(hi, P, c.pairs);
     const uint32_t* list = lists + (size_t)cls * nb;
-    if (recs) {
-      // the whole bucket by the block-local Standard-Sort, NT = capw / 8
-      const uint2* rl = reinterpret_cast<const uint2*>(lists) + (size_t)cls * nb;
-      if (capw <= 256) e = launch_leaf_sort<32>(c, rl, counts + cls, X, out);
-      else if (capw <= 512) e = launch_leaf_sort<64>(c, rl, counts + cls, X, out);
-      else if (capw <= 1024) e = launch_leaf_sort<128>(c, rl, counts + cls, X, out);
-      else if (capw <= 2048) e = launch_leaf_sort<256>(c, rl, counts + cls, X, out);
-      else if (capw <= 4096) e = launch_leaf_sort<512>(c, rl, counts + cls, X, out);
-      else e = launch_leaf_sort<1024>(c, rl, counts + cls, X, out);
-      if (e) return e;
-    } else if (cls > 0 && !c.pairs) {
+    if (cls > 0 && !c.pairs) {
       // a CTA per bucket (one slice per CTA), more threads for larger buckets
       if (hi <= 1024) e = launch_cta_class<64>(c, br, list, counts + cls, g, X, out, P, ptab);
       else if (hi <= 2048) e = launch_cta_class<128>(c, br, list, counts + cls, g, X, out, P, ptab);

@@ -24,9 +24,10 @@ def test_cache_round_trip(tmp_path):
 
 def test_default_grid_is_speed_only():
     # only pcf_tuning knobs: none of them changes alpha..delta, tau or the output
-    assert set(autotune.DEFAULT_GRID) == {"max_digit_bits", "tile_log2", "leaf_cap"}
+    assert set(autotune.DEFAULT_GRID) == {"max_digit_bits", "tile_log2", "leaf_cap", "leaf_mode"}
     for v in autotune.DEFAULT_GRID["leaf_cap"]:
         assert 64 <= v <= 8192 and v & (v - 1) == 0
+    assert set(autotune.DEFAULT_GRID["leaf_mode"]) <= {1, 2}
 
 
 class _FakeContext:
