@@ -4,10 +4,9 @@ The knobs are the widest bucket-id digit scattered per global pass
 (max_digit_bits), the keys per count tile (tile_log2), the largest bucket
 finished on chip (leaf_cap) and how keys-only sorts finish it (leaf_mode: a
 block-local sort, or the remaining Learned-Sort steps).  None of them
-changes alpha, beta,
-gamma, delta, tau or the output, so the tuner may pick any of them; it times
-each candidate on a sample of the caller's workload with CUDA events and keeps
-the fastest.  Results are cached in a JSON file keyed by workload class.
+changes alpha, beta, gamma, delta, tau or the output, so the tuner may pick
+any of them; it times each candidate on a sample of the caller's workload
+with CUDA events and keeps the fastest.  Results are cached in a JSON file keyed by workload class.
 """
 import itertools
 import json
