@@ -26,9 +26,15 @@
  *     d_in may equal d_out (in-place sort); otherwise the ranges must not
  *     overlap.  Keys are 8-byte aligned, values 4-byte aligned.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- *   - Calls are issued on `stream` and return when the sort is complete on
- *     the device, except where stated.  A context serialises its own calls;
- *     use one context per host thread.
+ *   - Calls are issued on `stream`, ordered after the work already queued
+ *     there, and return when the sort is complete on the device, except
+ *     where stated.  They block because Algorithm 1's recursion is
+ *     data-dependent: each global level ends with the host reading back the
+ *     level's record (how many buckets go on to the next level, to the
+ *     standard sort, or are finished on chip), which sizes the next level's
+ *     launches.  A replayed sort graph (pcf_graph_*) runs the whole sort with
+ *     no such read-back.  pcf_ctx_sync returns the last sort's status.
+ *     A context serialises its own calls; use one context per host thread.
  *   - Errors are returned, never raised: no call aborts, traps or exits.
  *     On PCF_ERR_INVALID_KEY (a NaN key) the output buffers are not written.
  *     n = 0 and n = 1 succeed without device work other than a copy.
@@ -147,6 +153,24 @@ pcf_status pcf_ctx_get_tuning(const pcf_ctx* ctx, pcf_tuning* out);
 pcf_status pcf_ctx_reserve(pcf_ctx* ctx, uint64_t n_total, int pairs);
 /* Counters of the last sort on this context. */
 pcf_status pcf_ctx_last_stats(const pcf_ctx* ctx, pcf_call_stats* out);
+/* Waits for the work queued on `stream` and returns the status of the
+ * context's last sort (PCF_OK before any).  Sorts already return their
+ * status when they finish; this is the stream-ordered way to read it. */
+pcf_status pcf_ctx_sync(pcf_ctx* ctx, void* stream);
+
+/* Device workspace for sorting n_total keys in S arrays (pairs != 0: with
+ * u32 values) with the policy and tuning of ctx (NULL: the defaults): an
+ * upper bound, in bytes, on what a context grows to for such a sort (the
+ * key-sized scratch of 14 bytes per key, 18 with values, plus the level
+ * tables, sized for S arrays of equal length at level 0 and for every key
+ * reaching a deeper level).  The context allocates on demand; this figure
+ * lets a caller budget device memory before the call (or reserve it with
+ * pcf_ctx_reserve, which pre-allocates the key-sized part).  *out = 0 for
+ * n_total = 0.  PCF_ERR_INVALID_ARG: n_total > 2^32 - 1, or S = 0 with keys. */
+pcf_status pcf_workspace_bytes(const pcf_ctx* ctx, uint64_t n_total, uint32_t S,
+                               pcf_key_type kt, int pairs, uint64_t* out);
+/* Device bytes the context holds now (the sum of its workspace buffers). */
+pcf_status pcf_ctx_workspace_held(const pcf_ctx* ctx, uint64_t* out);
 
 /* Sorts n keys (Algorithm 1, PCF model of Sec. 3.3) from d_in into d_out. */
 pcf_status pcf_sort_keys(pcf_ctx* ctx, const void* d_in, void* d_out, uint64_t n,
@@ -168,6 +192,18 @@ pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_
                               const uint64_t* h_offsets, uint32_t S, pcf_key_type kt,
                               uint64_t seed, void* stream);
 
+/* pcf_sort_segmented with the S+1 offsets in DEVICE memory (u64, 8-byte
+ * aligned; the rules of h_offsets apply) and n_cap the number of keys the
+ * key (and value) buffers hold.  The offsets are read on `stream`, after
+ * the work queued there (a kernel that produced them on that stream need
+ * not be waited for), through the context's pinned staging buffer; offsets
+ * that break the rules, or end beyond n_cap, return PCF_ERR_INVALID_ARG with
+ * nothing written. */
+pcf_status pcf_sort_segmented_dev(pcf_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
+                                  void* d_keys_out, uint32_t* d_vals_out,
+                                  const uint64_t* d_offsets, uint32_t S, uint64_t n_cap,
+                                  pcf_key_type kt, uint64_t seed, void* stream);
+
 /* Allocation-free batched sort of small arrays (keys only; the paper has no
  * counterpart: it is an interface for callers that must not allocate device
  * memory during a call -- cudaMalloc/cudaFree synchronise the whole device,
@@ -182,6 +218,9 @@ pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_
  * Scratch: one fixed device array of the library (about 2.9 MB per device),
  * its address resolved by cudaGetSymbolAddress on the first call on each
  * device; make that first call before any stream capture on the device.
+ * The address is kept for the life of the process: after cudaDeviceReset
+ * on a device, do not call this entry point on that device again.
+ * `stream` must belong to the current device (else PCF_ERR_INVALID_ARG).
  * Calls no allocating CUDA or library function.  All calls on a device share
  * the scratch: calls in flight at the same time on one device race and give
  * undefined results -- serialise them.

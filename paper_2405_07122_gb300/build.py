@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False, extra=None, checked: bool 
         extra = list(extra or []) + ["-DPCF_CHECKED"]
     os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "pcfsort.h"))
+    headers += [os.path.join(ROOT, "include", h) for h in ("pcfsort.h", "pcfsort_debug.h")]
     objs, jobs = [], []
     for s in SOURCES:
         src = os.path.join(CSRC, s)

@@ -18,6 +18,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pcfsort.h"
+#include "../../include/pcfsort_debug.h"
 #include "pcf_internal.h"
 
 
@@ -122,6 +123,8 @@ struct pcf_ctx {
   HostBuf h_stage, h_lout, h_status, h_items;
   HostBuf h_stage_small;  // range records of the on-chip arrays (level 0)
   HostBuf h_fb;           // fallback items and their tables, both ways
+  HostBuf h_offs;         // device offsets of pcf_sort_segmented_dev, read back
+  pcf_status last_status = PCF_OK;  // of the last sort (pcf_ctx_sync)
   DevBuf ptab;            // alpha..delta for n = 0..leaf_cap (u16 x 4)
   uint64_t ptab_key = 0;  // policy/cap the table was built for
   ParamCache pcache;
@@ -715,6 +718,86 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
   return PCF_OK;
 }
 
+
+// Device bytes a context holds (every workspace buffer's capacity).
+uint64_t workspace_held(const pcf_ctx* c) {
+  const DevBuf* bufs[] = {&c->tmp_k, &c->tmp_v, &c->tmp_aux, &c->host_keys, &c->segs, &c->bases,
+                          &c->tpool, &c->done, &c->cmat1, &c->cmat2, &c->sw, &c->groups,
+                          &c->gtiles, &c->gcent, &c->gtot, &c->leaf, &c->next, &c->fb, &c->lout,
+                          &c->status, &c->misc, &c->fb_items, &c->fb_bases, &c->fb_lohi,
+                          &c->small_items, &c->segs_b, &c->pcols, &c->pbsums, &c->olist,
+                          &c->jbuf, &c->small_segs, &c->fb_cnt, &c->bcounts, &c->bmax, &c->ptab,
+                          &c->pipe_keys};
+  uint64_t b = 0;
+  for (const DevBuf* d : bufs) b += d->cap;
+  return b;
+}
+
+// An upper bound on the workspace a sort of n keys in S arrays grows a
+// context to, following the sizes run_sort asks for.  Level buffers are
+// reused from level to level, so each takes the larger of two cases: level
+// 0 with S arrays of equal size (floor(n_s^(c)) summed over the arrays is
+// largest when they are equal), and a later level of n / (cap + 1)
+// (sub)arrays of cap + 1 keys (every key one level further down, in the
+// smallest (sub)arrays a level takes).  Standard-sort rounds are bounded by
+// items of more than 1024 keys, each split in at most three parts.  Every
+// buffer is allocated a quarter larger than asked (ensure()).
+uint64_t workspace_bound(const Policy& P, const pcf_tuning& tu, uint64_t n, uint32_t S,
+                         bool pairs) {
+  if (n == 0) return 0;
+  const uint32_t cap = onchip_cap(tu.leaf_cap, P, pairs);
+  const bool leaf_sort = !pairs && tu.leaf_mode == 1;
+  const uint64_t olist_per = 8ull * (leaf_sort ? leaf_sort_classes(cap) : onchip_classes(cap));
+  auto grow = [](uint64_t b) { return b + b / 4; };
+  enum { LEAF, NEXT, FB, TPOOL, SW, CMAT1, GROUPS, GTILES, GCENT, CMAT2, OLIST, PLAN, PLAN2,
+         PCOLS, PBSUMS, NNEED };
+  uint64_t need[NNEED] = {0};
+  ParamCache pc;
+  auto level = [&](uint64_t rows, uint64_t size, uint64_t n_level) {
+    if (!rows) return;
+    std::vector<InSeg> in(rows);
+    uint64_t off = 0;
+    for (uint64_t r = 0; r < rows; ++r) {
+      in[r] = InSeg{off, size, 0, 0, 0};
+      off += size;
+    }
+    Plan pl;
+    plan_level(P, tu, pc, in, pl);
+    const uint64_t max_items = std::max<uint64_t>(pl.n_buckets, rows) + 16;
+    const uint64_t scan_max =
+        std::max(std::max(pl.cmat1, pl.cmat2_bound), std::max(pl.tpool, pl.n_buckets));
+    const uint64_t s_max = std::min<uint64_t>(pl.n_buckets, n_level / (cap + 1)) + 1;
+    const uint64_t v[NNEED] = {
+        max_items * sizeof(BRec), max_items * 4, max_items * sizeof(FbItem), pl.tpool * 4,
+        ((scan_max + kScanTile - 1) / kScanTile + (pl.n_groups + kScanTile - 1) / kScanTile + 8) * 8,
+        pl.cmat1 * 4, pl.n_groups * sizeof(Group), pl.n_groups * 4, pl.n_groups * 4,
+        pl.cmat2_bound * 4, pl.n_buckets * olist_per, plan_layout(rows).bytes,
+        plan_layout(s_max).bytes, (uint64_t)PC_NCOL * s_max * 4,
+        (uint64_t)PC_NCOL * ((s_max + 2047) / 2048) * 4};
+    for (int i = 0; i < NNEED; ++i) need[i] = std::max(need[i], v[i]);
+  };
+  const uint64_t per = (n + S - 1) / S;
+  if (per > cap) level(S, per, n);
+  level(n / (cap + 1), cap + 1, n);
+  // the arrays of at most cap keys, straight to the on-chip kernels
+  const uint64_t small = per <= cap ? S : 0;
+  uint64_t b = 0;
+  for (int i = 0; i < NNEED; ++i) b += grow(need[i]);
+  // the plan buffers are two (this level's and the next's)
+  b += grow(std::max(need[PLAN], need[PLAN2])) - grow(need[PLAN]);
+  b += grow(small * sizeof(Seg) + (small + 1) * 4) + grow(small * sizeof(BRec) + 64);
+  b += grow(std::max<uint64_t>(small * olist_per, need[OLIST])) - grow(need[OLIST]);
+  b += grow(n * 8) + grow(n * 2) + grow(n * 4) + (pairs ? grow(n * 4) : 0);
+  // standard-sort rounds
+  const uint64_t nf = 3 * (n / 1025 + S) + 1;
+  const uint64_t mp = n / kMergeTile + nf;
+  b += grow(6 * nf * sizeof(FbItem)) + grow((6 * nf + 4) * 4) + grow(9 * nf * 8 + nf * 4 + 64);
+  b += grow(3 * (mp + 1) * 4);
+  b += grow(((3 * (mp + 1) + kScanTile - 1) / kScanTile + 8) * 8);
+  // status, level record, misc, the on-chip parameter table
+  b += grow(64) + grow(sizeof(LevelOut) + 64) + grow(256) + grow((uint64_t)(tu.leaf_cap + 1) * 8);
+  return b;
+}
 
 // The status word and the decision counters after it (DecisionCounters at
 // byte 16 of the status buffer), read back together.
@@ -1325,6 +1408,30 @@ pcf_status pcf_ctx_get_tuning(const pcf_ctx* ctx, pcf_tuning* out) {
   return PCF_OK;
 }
 
+pcf_status pcf_workspace_bytes(const pcf_ctx* ctx, uint64_t n_total, uint32_t S, pcf_key_type kt,
+                               int pairs, uint64_t* out) {
+  if (!out || (kt != PCF_KEY_F64 && kt != PCF_KEY_U64)) return PCF_ERR_INVALID_ARG;
+  if (n_total > 0xFFFFFFFFull || (n_total && S == 0)) return PCF_ERR_INVALID_ARG;
+  const Policy P = ctx ? ctx->policy : Policy{3, 3, 3, 3, 4, MODEL_PCF, 100, RANGE_ARRAY, 0};
+  const pcf_tuning tu = ctx ? ctx->tuning : pcf_tuning{11, 14, 8192, 1};
+  if (!policy_ok(P)) return PCF_ERR_INVALID_ARG;
+  *out = workspace_bound(P, tu, n_total, S, pairs != 0);
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_workspace_held(const pcf_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return PCF_ERR_INVALID_ARG;
+  *out = workspace_held(ctx);
+  return PCF_OK;
+}
+
+pcf_status pcf_ctx_sync(pcf_ctx* ctx, void* stream) {
+  if (!ctx) return PCF_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return ctx->last_status;
+}
+
 pcf_status pcf_ctx_reserve(pcf_ctx* ctx, uint64_t n_total, int pairs) {
   if (!ctx) return PCF_ERR_INVALID_ARG;
   CK(cudaSetDevice(ctx->device));
@@ -1378,6 +1485,7 @@ static pcf_status sort_common(pcf_ctx* ctx, const void* kin, const uint32_t* vin
                                (uint32_t)kt, pairs, (cudaStream_t)stream);
   // a call that fails part-way returns with none of its work in flight
   if (r != PCF_OK) cudaStreamSynchronize((cudaStream_t)stream);
+  ctx->last_status = r;
   return r;
 }
 
@@ -1411,6 +1519,25 @@ pcf_status pcf_sort_segmented(pcf_ctx* ctx, const void* d_keys_in, const uint32_
   const bool pairs = d_vals_in != nullptr || d_vals_out != nullptr;
   return sort_common(ctx, d_keys_in, d_vals_in, d_keys_out, d_vals_out, segs, h_offsets[S], kt,
                      pairs, stream);
+}
+
+pcf_status pcf_sort_segmented_dev(pcf_ctx* ctx, const void* d_keys_in, const uint32_t* d_vals_in,
+                                  void* d_keys_out, uint32_t* d_vals_out,
+                                  const uint64_t* d_offsets, uint32_t S, uint64_t n_cap,
+                                  pcf_key_type kt, uint64_t seed, void* stream) {
+  if (!ctx || (!d_offsets && S) || ((uintptr_t)d_offsets & 7)) return PCF_ERR_INVALID_ARG;
+  if (S == 0) return PCF_OK;
+  if (S == 0xFFFFFFFFu) return PCF_ERR_INVALID_ARG;
+  const cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device));
+  CK(ensure_host(ctx->h_offs, ((size_t)S + 1) * 8));
+  // read on the sort's stream: after whatever produced the offsets there
+  CK(launch_xfer(st, ctx->h_offs.dp, d_offsets, ((size_t)S + 1) * 8));
+  CK(cudaStreamSynchronize(st));
+  const uint64_t* h = (const uint64_t*)ctx->h_offs.p;
+  if (h[S] > n_cap) return PCF_ERR_INVALID_ARG;  // (the rest is checked below)
+  return pcf_sort_segmented(ctx, d_keys_in, d_vals_in, d_keys_out, d_vals_out, h, S, kt, seed,
+                            stream);
 }
 
 pcf_status pcf_graph_create(pcf_graph** out, const pcf_ctx* like, const void* d_keys_in,

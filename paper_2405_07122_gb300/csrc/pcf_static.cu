@@ -43,11 +43,13 @@ constexpr uint32_t kStBadOffsets = 0x100u;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStBytes];
 
-// Scratch address of each device, resolved once (cudaGetSymbolAddress).
+// Scratch address of each device (cudaGetSymbolAddress), kept once it was
+// resolved; a failed lookup is not kept, so a later call tries again.  A
+// device reset (cudaDeviceReset) makes a kept address stale: after one, the
+// process must not call this entry point on that device again.
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
+std::mutex g_addr_mu;
 void* g_addr[kMaxDevices];
-cudaError_t g_addr_err[kMaxDevices];
 
 // One thread per array: checks its offsets and writes its record (the
 // caller's array s is Learned-Sort at depth 0 with seed + s); one thread per
@@ -112,13 +114,27 @@ extern "C" pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_k
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PCF_ERR_CUDA;
+  // the stream must belong to the current device (the scratch is per device)
+  {
+    int sdev = -1;
+    if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) return PCF_ERR_CUDA;
+    if (sdev != dev) return PCF_ERR_INVALID_ARG;
+  }
   // first call on a device: resolve the scratch address (before any stream
   // capture on that device)
-  std::call_once(g_once[dev], [dev] {
-    g_addr_err[dev] = cudaGetSymbolAddress(&g_addr[dev], g_static_scratch);
-  });
-  if (g_addr_err[dev] != cudaSuccess) return PCF_ERR_CUDA;
-  unsigned char* base = (unsigned char*)g_addr[dev];
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_addr_mu);
+    if (!g_addr[dev]) {
+      void* a = nullptr;
+      if (cudaGetSymbolAddress(&a, g_static_scratch) != cudaSuccess || !a) {
+        cudaGetLastError();
+        return PCF_ERR_CUDA;
+      }
+      g_addr[dev] = a;
+    }
+    base = (unsigned char*)g_addr[dev];
+  }
   BRec* brec = (BRec*)(base + kOffBrec);
   uint16_t* ptab = (uint16_t*)(base + kOffPtab);
   uint32_t* status = (uint32_t*)(base + kOffStatus);

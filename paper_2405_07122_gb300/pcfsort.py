@@ -95,6 +95,12 @@ def lib():
             "pcf_graph_info": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_u64),
                                ctypes.POINTER(_u64)],
             "pcf_graph_destroy": [_vp],
+            "pcf_sort_segmented_dev": [_vp, _vp, _vp, _vp, _vp, _vp, _u32, _u64, ctypes.c_int,
+                                       _u64, _vp],
+            "pcf_ctx_sync": [_vp, _vp],
+            "pcf_workspace_bytes": [_vp, _u64, _u32, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(_u64)],
+            "pcf_ctx_workspace_held": [_vp, ctypes.POINTER(_u64)],
             "pcf_debug_scan": [_vp, _vp, _u64, _u32, _u64, _vp],
             "pcf_debug_level0": [_vp, _vp, _u64, ctypes.c_int, _u64, ctypes.POINTER(_u64),
                                  ctypes.POINTER(_u32), _u64],
@@ -236,6 +242,41 @@ class Context:
             ko.data_ptr(), None if vo is None else vo.data_ptr(),
             offs.ctypes.data_as(ctypes.POINTER(_u64)), S, kt, seed, _stream_ptr(stream)))
         return ko, vo
+
+    def sort_segmented_dev(self, keys_in, offsets_dev, vals_in=None, keys_out=None, vals_out=None,
+                           key_type=None, seed=0, stream=None):
+        """offsets_dev: DEVICE tensor of S+1 segment boundaries (8-byte
+        integers on the keys' device), read by the library on `stream`."""
+        kt = _kt(key_type or ("f64" if str(keys_in.dtype) == "torch.float64" else "u64"))
+        if (offsets_dev.element_size() != 8 or not offsets_dev.is_contiguous()
+                or offsets_dev.device != keys_in.device or offsets_dev.numel() < 1
+                or str(offsets_dev.dtype) not in ("torch.int64", "torch.uint64")):
+            raise ValueError("offsets_dev: a contiguous 8-byte integer tensor on the keys' device")
+        ko = keys_in if keys_out is None else keys_out
+        vo = vals_in if vals_out is None else vals_out
+        n_cap = min(keys_in.numel(), ko.numel())
+        if vals_in is not None:
+            n_cap = min(n_cap, vals_in.numel(), vo.numel())
+        self._check(lib().pcf_sort_segmented_dev(
+            self._h, keys_in.data_ptr(), None if vals_in is None else vals_in.data_ptr(),
+            ko.data_ptr(), None if vo is None else vo.data_ptr(), offsets_dev.data_ptr(),
+            offsets_dev.numel() - 1, n_cap, kt, seed, _stream_ptr(stream)))
+        return ko, vo
+
+    def sync(self, stream=None):
+        """Waits for `stream` and returns the last sort's status code."""
+        return int(lib().pcf_ctx_sync(self._h, _stream_ptr(stream)))
+
+    def workspace_held(self):
+        """Device bytes the context holds."""
+        v = _u64(0)
+        self._check(lib().pcf_ctx_workspace_held(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def workspace_bytes(self, n_total, n_arrays=1, key_type="f64", pairs=False):
+        """Upper bound on the workspace a sort of n_total keys in n_arrays
+        arrays grows this context to (its policy and tuning)."""
+        return workspace_bytes(n_total, n_arrays, key_type, pairs, ctx=self)
 
     def sort_keys_host(self, host_keys, key_type=None, seed=0, stream=None):
         """End-to-end: sorts a host tensor/array (ideally pinned) in place."""
@@ -389,12 +430,36 @@ def sort_segmented_static(keys_in, offsets_dev, n_total, keys_out=None, key_type
     last value.  Calls on one device must not overlap."""
     kt = _kt(key_type or ("f64" if str(keys_in.dtype) == "torch.float64" else "u64"))
     ko = keys_in if keys_out is None else keys_out
+    # the C call trusts n_total and the buffers: check them here
+    for name, t in (("keys_in", keys_in), ("keys_out", ko), ("offsets_dev", offsets_dev)):
+        if t.element_size() != 8 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(name + ": a contiguous 8-byte CUDA tensor")
+    if str(offsets_dev.dtype) not in ("torch.int64", "torch.uint64"):
+        raise ValueError("offsets_dev: int64 or uint64")
+    import torch
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in (keys_in, ko, offsets_dev)):
+        raise ValueError("every tensor on the current CUDA device")
+    if offsets_dev.numel() < 1 or not 0 <= n_total <= min(keys_in.numel(), ko.numel()):
+        raise ValueError("n_total must fit the key buffers")
     rc = lib().pcf_sort_segmented_static(keys_in.data_ptr(), ko.data_ptr(),
                                          offsets_dev.data_ptr(), offsets_dev.numel() - 1,
                                          n_total, kt, seed, _stream_ptr(stream))
     if rc:
         raise PcfError(rc)
     return ko
+
+
+def workspace_bytes(n_total, n_arrays=1, key_type="f64", pairs=False, ctx=None):
+    """pcf_workspace_bytes: upper bound on the device workspace of a sort of
+    n_total keys in n_arrays arrays (ctx's policy and tuning, else the
+    defaults)."""
+    v = _u64(0)
+    rc = lib().pcf_workspace_bytes(None if ctx is None else ctx._h, n_total, n_arrays,
+                                   _kt(key_type), 1 if pairs else 0, ctypes.byref(v))
+    if rc:
+        raise PcfError(rc)
+    return int(v.value)
 
 
 def root_floor_host(n, p, q):

@@ -21,14 +21,58 @@ def P():
     return pcfsort
 
 
+def _declared(*headers):
+    names = set()
+    for h in headers:
+        hdr = open(os.path.join(ROOT, "include", h)).read()
+        names |= set(re.findall(r"\b(pcf_[a-z0-9_]+)\s*\(", hdr))
+    return names
+
+
 def test_exports_every_declared_symbol(P):
-    hdr = open(os.path.join(ROOT, "include", "pcfsort.h")).read()
-    declared = set(re.findall(r"\b(pcf_[a-z0-9_]+)\s*\(", hdr))
-    assert {"pcf_sort_keys", "pcf_sort_pairs", "pcf_sort_segmented"} <= declared
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert headers == ["pcfsort.h", "pcfsort_debug.h"]
+    declared = _declared(*headers)
+    assert {"pcf_sort_keys", "pcf_sort_pairs", "pcf_sort_segmented", "pcf_sort_segmented_dev",
+            "pcf_workspace_bytes", "pcf_ctx_sync", "pcf_status_string"} <= declared
     L = P.lib()
     for name in sorted(declared):
         assert hasattr(L, name), name
     assert P.version() >= 100
+    # the self-test hooks are declared in the debug header, not the interface
+    assert all(n.startswith("pcf_debug_") for n in _declared("pcfsort_debug.h"))
+    assert not any(n.startswith("pcf_debug_") for n in _declared("pcfsort.h"))
+
+
+def test_every_export_is_declared(P):
+    # every pcf_* function the library exports has a declaration in include/
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True,
+                         text=True)
+    if out.returncode:
+        pytest.skip("nm not available")
+    exported = {l.split()[-1] for l in out.stdout.splitlines()
+                if l.split() and l.split()[-1].startswith("pcf_")}
+    assert exported, out.stdout[:200]
+    assert exported <= _declared("pcfsort.h", "pcfsort_debug.h"), exported - _declared(
+        "pcfsort.h", "pcfsort_debug.h")
+
+
+def test_workspace_bound_on_the_host(P):
+    # the bound follows the planner on the host: the key-sized scratch of 14
+    # bytes per key (18 with values) is a floor, and it grows with n
+    last = 0
+    for n in (1, 1000, 10**5, 10**6, 10**8):
+        b = P.workspace_bytes(n)
+        assert b >= 14 * n and b > last
+        assert P.workspace_bytes(n, pairs=True) >= 18 * n
+        last = b
+    assert P.workspace_bytes(0) == 0
+    assert P.workspace_bytes(10**6, n_arrays=1000) > 0
+    with pytest.raises(P.PcfError):
+        P.workspace_bytes(10**6, n_arrays=0)
+    with pytest.raises(P.PcfError):
+        P.workspace_bytes(2**32)
 
 
 def test_status_strings(P):

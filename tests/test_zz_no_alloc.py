@@ -91,9 +91,22 @@ def test_rejections(P):
     big = torch.zeros(P.STATIC_MAX_ARRAYS + 2, dtype=torch.int64, device="cuda")
     with pytest.raises(P.PcfError):
         P.sort_segmented_static(d, big, 0, keys_out=out, key_type="f64")
+    huge = torch.zeros(P.STATIC_MAX_KEYS + 1, dtype=torch.float64, device="cuda")
     with pytest.raises(P.PcfError):
-        P.sort_segmented_static(d, torch.tensor([0, 1], device="cuda"), P.STATIC_MAX_KEYS + 1,
-                                keys_out=out, key_type="f64")
+        P.sort_segmented_static(huge, torch.tensor([0, 1], device="cuda"), P.STATIC_MAX_KEYS + 1,
+                                key_type="f64")
+    # arguments the binding checks before calling in: n_total beyond the
+    # buffers, 4-byte offsets, a non-contiguous tensor
+    o2 = torch.tensor([0, 2048, 4096], device="cuda")
+    with pytest.raises(ValueError):
+        P.sort_segmented_static(d, o2, 4097, keys_out=out, key_type="f64")
+    with pytest.raises(ValueError):
+        P.sort_segmented_static(d[:100], o2, 4096, keys_out=out, key_type="f64")
+    with pytest.raises(ValueError):
+        P.sort_segmented_static(d, o2.to(torch.int32), 4096, keys_out=out, key_type="f64")
+    with pytest.raises(ValueError):
+        P.sort_segmented_static(d[::2], torch.tensor([0, 2048], device="cuda"), 2048,
+                                keys_out=out[:2048], key_type="f64")
     # NaN: rejected, output untouched
     y = x[:2000].copy()
     y[777] = np.nan
