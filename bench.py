@@ -344,8 +344,17 @@ def main():
     # this workload passes through the global passes and the on-chip finish)
     achieved = dom_b * n / (dom_ms / 1e3) / 1e9
     step_s = ms / args.steps / 1e3
+    # the whole sort against the copy peak first (the target is defined on
+    # it): the bytes the passes it ran must move (the library's pass model),
+    # and the 48 B/key minimum of one bucketing level (range 8, predict 8,
+    # move 16, finish 16)
+    roofline_job = {"frac_measured_passes": moved / args.steps / step_s / 1e9 / peak,
+                    "bytes_measured_passes": moved / args.steps,
+                    "frac_algorithmic": 48 * 4 * n / step_s / 1e9 / peak,
+                    "bytes_algorithmic": 48 * 4 * n, "peak": peak, "peak_kind": peak_kind}
     line = {
-        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "roofline_job": roofline_job,
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -369,13 +378,6 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": stage_traffic(dom, n), "bytes_per_key": dom_b,
                      "copy_kernel_gbs": copy_gbs},
-        # the whole sort against the copy peak: the bytes the passes it ran
-        # must move (the library's pass model), and the 48 B/key minimum of
-        # one bucketing level (range 8, predict 8, move 16, finish 16)
-        "roofline_job": {"bytes_measured_passes": moved / args.steps,
-                         "frac_measured_passes": moved / args.steps / step_s / 1e9 / peak,
-                         "bytes_algorithmic": 48 * 4 * n,
-                         "frac_algorithmic": 48 * 4 * n / step_s / 1e9 / peak},
         "stage_ms_per_array": {k: v / (t_steps * 4) for k, v in stages.items()},
         "clocks": clk.summary(),
     }
@@ -395,6 +397,61 @@ def main():
 # ---------------------------------------------------------------------------
 # secondary configurations (not the driver's default line)
 # ---------------------------------------------------------------------------
+def secondary_roofline(torch, ctx, run, n_global, n_total, peak, peak_kind):
+    """Stage times of one more run (CUDA events on the sort's stream) and the
+    dominant stage's roofline.  Algorithmic bytes: the global passes move
+    every key of the arrays they bucket (n_global, level 0 counted once: a
+    lower bound where keys take further levels), the on-chip finish reads
+    and writes every key not sent to the standard sort, the standard sort at
+    least one read and write of its keys."""
+    ctx.enable_timing(True)
+    run()
+    torch.cuda.synchronize()
+    st = ctx.stage_ms()
+    stats = ctx.last_stats()
+    ctx.enable_timing(False)
+    fb = stats["fallback_keys"]
+    algo = {k: KERNEL_BYTES[k] * n_global for k in
+            ("range", "hist1_scan", "scatter1", "hist2_scan", "scatter2")}
+    algo["leaf"] = KERNEL_BYTES["leaf"] * (n_total - fb)
+    algo["fallback"] = 16 * fb
+    cand = {k: v for k, v in st.items() if k in algo and v > 0 and algo[k] > 0}
+    dom = max(cand, key=cand.get)
+    achieved = algo[dom] / (cand[dom] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "bytes": algo[dom]}
+    return roof, st, stats
+
+
+def oracle_sample(arrays, vals=None, threads=1):
+    """The CPU oracle, as it stands, on host arrays: (Gkeys/s, keys, seconds,
+    threads used).  threads > 1: one array per host thread (its C calls
+    release the GIL)."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.lib()
+    total = sum(int(a.size) for a in arrays)
+
+    def one(i):
+        oracle.sort(arrays[i], None if vals is None else vals[i])
+
+    t0 = time.perf_counter()
+    if threads > 1:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(one, range(len(arrays))))
+    else:
+        for i in range(len(arrays)):
+            one(i)
+    secs = time.perf_counter() - t0
+    return total / secs / 1e9, total, secs, threads
+
+
+def _cpu_line(v, total, secs, cores, what):
+    return {"value": v, "unit": "Gkeys/s", "cores": cores, "kind": "oracle",
+            "sample": "%s (%d keys, %.1f s)" % (what, total, secs)}
+
+
 def _device_sort_timer(torch):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -417,14 +474,23 @@ def run_secondary(args):
     from paper_2405_07122_gb300 import pcfsort
     timed = _device_sort_timer(torch)
     ctx = pcfsort.Context(0)
+    peak, peak_kind = peaks()
+    cpu = not args.no_cpu_baseline
     line = {"impl": "ours", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "unit": "Gkeys/s"}
     if args.workload == "small":
-        x = torch.from_numpy(W.f64_keys("uniform", 10**6, 0)).cuda()
+        xh = W.f64_keys("uniform", 10**6, 0)
+        x = torch.from_numpy(xh).cuda()
         o = torch.empty_like(x)
-        ms = timed(lambda: ctx.sort_keys(x, o, key_type="f64"), max(args.steps, 10))
+        run = lambda: ctx.sort_keys(x, o, key_type="f64")  # noqa: E731
+        ms = timed(run, max(args.steps, 10))
+        roof, st, stats = secondary_roofline(torch, ctx, run, 10**6, 10**6, peak, peak_kind)
         line.update(metric=METRIC, value=1e6 / ms / 1e6, ms_per_sort=ms, dtype="f64",
+                    roofline=roof, stage_ms=st,
+                    plain_form="this line is the plain per-array form",
                     config={"workload": "plain PCF sort, n = 10^6 float64 Uniform[0,1), keys only"})
+        if cpu:
+            line["cpu_baseline"] = _cpu_line(*oracle_sample([xh]), "the same 10^6 keys")
     elif args.workload == "zipf":
         n = 2**28
         k = W.zipf_u64(n, seed=5)
@@ -432,16 +498,26 @@ def run_secondary(args):
         tk = torch.from_numpy(k.view(np.int64)).cuda()
         tv = torch.from_numpy(v.view(np.int32)).cuda()
         ko, vo = torch.empty_like(tk), torch.empty_like(tv)
-        ms = timed(lambda: ctx.sort_pairs(tk, tv, ko, vo, key_type="u64"), max(1, args.steps))
+        run = lambda: ctx.sort_pairs(tk, tv, ko, vo, key_type="u64")  # noqa: E731
+        ms = timed(run, max(1, args.steps))
         st = ctx.last_stats()
-        # sorted as unsigned keys, and equal keys in input order (payload = index)
+        # sorted as unsigned keys, equal keys in input order (payload = index),
+        # and every payload still with its key
         flip = torch.tensor(-2**63, dtype=torch.int64, device="cuda")
         a, b = ko[:-1] ^ flip, ko[1:] ^ flip
         assert bool(((a < b) | ((a == b) & (vo[:-1] < vo[1:]))).all()), "pairs not stably sorted"
+        assert bool((tk[vo.long()] == ko).all()), "a payload left its key"
+        assert bool((torch.sort(vo).values == tv).all()), "payloads not a permutation"
+        roof, stages, _ = secondary_roofline(torch, ctx, run, n, n, peak, peak_kind)
         line.update(metric=METRIC, value=n / ms / 1e6, ms_per_sort=ms, dtype="u64",
-                    stats=st,
+                    stats=st, roofline=roof, stage_ms=stages,
+                    plain_form="this line is the plain per-array form",
                     config={"workload": "PCF sort, n = 2^28 uint64 keys, Zipf(1.2) over 10^7 "
                                         "hashed values, uint32 payload = index (stable pairs)"})
+        if cpu:
+            m = 1 << 24
+            line["cpu_baseline"] = _cpu_line(*oracle_sample([k[:m]], [v[:m]]),
+                                             "the first 2^24 key-value pairs")
     elif args.workload == "dupinject":
         # the appendix's adversarial input at GPU scale: 5x10^7 Normal(0,1)
         # keys plus as many copies of one value drawn in [min, max], shuffled
@@ -449,16 +525,24 @@ def run_secondary(args):
         n = x.size
         t = torch.from_numpy(x).cuda()
         o = torch.empty_like(t)
-        ms = timed(lambda: ctx.sort_keys(t, o, key_type="f64"), max(3, args.steps))
+        run = lambda: ctx.sort_keys(t, o, key_type="f64")  # noqa: E731
+        ms = timed(run, max(3, args.steps))
         st = ctx.last_stats()
         b = o.view(torch.int64)
         flip = torch.tensor(2**63 - 1, dtype=torch.int64, device="cuda")
         ok = torch.where(b < 0, b ^ flip, b)
         assert bool((ok[1:] >= ok[:-1]).all()), "output not sorted"
+        roof, stages, _ = secondary_roofline(torch, ctx, run, n, n, peak, peak_kind)
         line.update(metric=METRIC, value=n / ms / 1e6, ms_per_sort=ms, dtype="f64", stats=st,
+                    roofline=roof, stage_ms=stages,
+                    plain_form="this line is the plain per-array form",
                     config={"workload": "duplicate injection (appendix): 5x10^7 Normal(0,1) "
                                         "float64 keys + 5x10^7 copies of one value in [min, max], "
                                         "shuffled, keys only", "n": n})
+        if cpu:
+            sub = W.inject_duplicates(W.f64_keys("normal", 5 * 10**6, 9), seed=9)
+            line["cpu_baseline"] = _cpu_line(*oracle_sample([sub]),
+                                             "the same recipe at 5x10^6 + 5x10^6 keys")
     elif args.workload == "failsweep":
         # Sec. 4.2: level-0 bucketing of R = 100 uniform arrays of 10^6 keys
         # at every grid setting of the six heat maps (two of a, b, c, d
@@ -527,8 +611,22 @@ def run_secondary(args):
                 ctx.sort_keys(t[a:b], o[a:b], key_type="f64", seed=s)
         ms_p = timed(plain, 1)
         assert bool((o == batched_out).all()), "batched and plain outputs differ"
+        roof, stages, _ = secondary_roofline(
+            torch, ctx, lambda: ctx.sort_segmented(t, offs, keys_out=o, key_type="f64"),
+            int(sum(b - a for a, b in zip(offs[:-1], offs[1:]) if b - a > 8192)), total, peak,
+            peak_kind)
         graph.close()
         tctx.close()
+        if cpu:
+            # the oracle on the first 256 arrays: one array per host core, and
+            # single-threaded
+            sample = [keys[int(offs[i]):int(offs[i + 1])] for i in range(256)]
+            ncores = os.cpu_count() or 1
+            line["cpu_baseline"] = _cpu_line(*oracle_sample(sample, threads=ncores),
+                                             "the first 256 arrays, one array per core")
+            line["cpu_baseline_1core"] = _cpu_line(*oracle_sample(sample[:64]),
+                                                   "the first 64 arrays, one core")
+        line.update(roofline=roof, stage_ms=stages)
         line.update(metric=METRIC, value=total / ms_g / 1e6, ms_per_batch=ms_g,
                     graph={"captured": ginfo["captured"], "every_launch_replayed": all(replayed),
                            "launches": len(replayed)},
@@ -555,50 +653,84 @@ def run_secondary(args):
             pools[("u64", d)] = (torch.round(f * 4294967296.0).to(torch.int64) +
                                  torch.tensor(-2**63, dtype=torch.int64, device="cuda"))
         torch.cuda.synchronize()
-        srv = serve.SortServer(device=0, workers=4, mem_budget=64 << 30, batch_keys=1 << 27)
         rng = np.random.Generator(np.random.PCG64(8))
-        handles = []
-        pending = []
+        reqs = [(ta, pools[(kt, dist)][off:off + n], kt)
+                for (ta, n, kt, dist, _s), off in
+                ((r, int(rng.integers(0, pool_n - r[1] + 1))) for r in stream)]
 
-        def consume():
-            # the client takes each result as it completes (and lets it go),
-            # so finished outputs do not pile up on the device
-            keep = []
-            for h in pending:
-                if h.done.is_set():
-                    h.out = None
-                else:
-                    keep.append(h)
-            pending[:] = keep
+        def serve_run(items, paced):
+            """Submits items (arrival time, keys, type); paced: at their
+            arrival times, else all at once (the server's capacity).  The
+            client takes each result as it completes and releases it."""
+            srv = serve.SortServer(device=0, workers=4, mem_budget=64 << 30,
+                                   batch_keys=1 << 27)
+            handles, pending = [], []
 
-        t0 = time.perf_counter()
-        for (ta, nreq, kt, dist, _seed) in stream:
-            now = time.perf_counter() - t0
-            if ta > now:
-                time.sleep(ta - now)
-            off = int(rng.integers(0, pool_n - nreq + 1))
-            h = srv.submit(pools[(kt, dist)][off:off + nreq], kt)
-            handles.append(h)
-            pending.append(h)
-            consume()
-        for h in handles:
-            h.done.wait()
-            h.out = None
-        t1 = time.perf_counter()
-        srv.close()
-        errors = [h.error for h in handles if h.error is not None]
-        if errors:
-            raise RuntimeError("%d of %d requests failed, first: %r" % (len(errors), len(handles),
-                                                                     errors[0]))
-        keys_done = sum(h.n for h in handles)
-        lat = serve.latency_summary(handles)
+            def consume(block=False):
+                keep = []
+                for h in pending:
+                    if block:
+                        h.done.wait()
+                    if h.done.is_set():
+                        h.release()
+                    else:
+                        keep.append(h)
+                pending[:] = keep
+
+            t0 = time.perf_counter()
+            for ta, keys, kt in items:
+                if paced:
+                    now = time.perf_counter() - t0
+                    if ta > now:
+                        time.sleep(ta - now)
+                h = srv.submit(keys, kt)
+                handles.append(h)
+                pending.append(h)
+                consume()
+            consume(block=True)
+            t1 = time.perf_counter()
+            srv.close()
+            errors = [h.error for h in handles if h.error is not None]
+            if errors:
+                raise RuntimeError("%d of %d requests failed, first: %r"
+                                   % (len(errors), len(handles), errors[0]))
+            keys_done = sum(h.n for h in handles)
+            return keys_done / (t1 - t0) / 1e9, serve.latency_summary(handles), keys_done
+
+        value, lat, keys_done = serve_run(reqs, True)
+        # capacity: the first 4000 requests submitted at once (the queue
+        # never runs dry), and the same requests sorted one by one with
+        # pcf_sort_keys on one stream (the plain per-request form)
+        head = reqs[:4000]
+        cap, cap_lat, cap_keys = serve_run(head, False)
+        obuf = torch.empty(max(k.numel() for _, k, _ in head), dtype=torch.int64,
+                           device="cuda")
+
+        def plain():
+            for _, k, kt in head:
+                o = obuf[:k.numel()]
+                ctx.sort_keys(k, o if k.dtype == torch.int64 else o.view(torch.float64),
+                              key_type=kt)
+        ms_plain = timed(plain, 1)
         line.update(metric="served sorted Gkeys/s (sustained)",
-                    value=keys_done / (t1 - t0) / 1e9, latency=lat, requests=len(handles),
+                    value=value, latency=lat, requests=len(reqs),
                     offered_gkeys_per_s=keys_done / args.duration / 1e9, dtype="f64|u64",
+                    capacity={"value": cap, "unit": "Gkeys/s", "latency": cap_lat,
+                              "requests": len(head),
+                              "how": "the first 4000 requests submitted at once"},
+                    plain_form={"value": cap_keys / (ms_plain / 1e3) / 1e9, "unit": "Gkeys/s",
+                                "how": "the same 4000 requests, one pcf_sort_keys call each, "
+                                       "one stream"},
                     config={"workload": "serving loop: Poisson arrivals 2000/s, sizes "
                                         "floor(2^U(12,26)), f64 or u64, 5 distributions, "
-                                        "64 GB admission budget, 4 streams",
+                                        "64 GB admission budget (resident result pool), "
+                                        "4 streams",
                             "duration_s": args.duration})
+        if cpu:
+            smp = [k.cpu().numpy() for _, k, _ in head[:20]]
+            smp = [a if a.dtype == np.float64 else a.view(np.uint64) for a in smp]
+            line["cpu_baseline"] = _cpu_line(*oracle_sample(smp),
+                                             "the first 20 requests, one core")
     ctx.close()
     print(json.dumps(line), flush=True)
     return 0
