@@ -315,7 +315,7 @@ __device__ __forceinline__ bool hist1_pcf(const BinModel& bm, const Seg& g, uint
   return nan;
 }
 
-__global__ void __launch_bounds__(256) k_hist1(const Seg* segs, uint32_t S,
+__global__ void __launch_bounds__(256, 4) k_hist1(const Seg* segs, uint32_t S,
                                                const uint32_t* tile_base, uint32_t tile_keys,
                                                const uint64_t* __restrict__ keys, uint32_t kt,
                                                const uint32_t* __restrict__ tpool,

@@ -1013,20 +1013,20 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
 //      the CTA sorted the previous bucket; each thread takes KPT of them
 //      (order-preserving integers) into registers and the CTA reduces min
 //      and max, then stages the next bucket;
-//   2. one equal-width split of [min, max] into M = 2^(ceil(log2 n) + OVS)
-//      parts: part(v) = (v - min) >> shift, shift chosen so that parts < M
-//      (an MSD radix digit of the key's offset from the minimum; no model,
-//      no samples, no division); 16-bit counts by shared atomics, their
-//      exclusive scan, and every key written to its part's range of B;
+//   2. one equal-width split of [min, max] into M = 2^ceil(log2 n) parts:
+//      part(v) = (v - min) >> shift, shift chosen so that parts < M (an MSD
+//      radix digit of the key's offset from the minimum; no model, no
+//      samples, no division); counts by shared atomics, an exclusive scan
+//      that leaves every part's (start, count) packed in one word, and every
+//      key written to its part's range of B with that word beside it (W);
 //   3. every key's final position: its part's start plus its rank among the
 //      part's keys (smaller, or equal and earlier in B), written straight to
 //      the output (consecutive threads write nearly consecutive positions).
 //      Parts of more than kLeafRank keys (skewed or duplicate-heavy buckets)
 //      are listed and sorted afterwards by one warp each (leaf_big_part).
-// Counts are u16 pairs in 32-bit words, in groups of eight (one uint4); the
-// scan gives each thread q consecutive groups, stored transposed (group i of
-// thread t at uint4 index i * NT + t) so that its vector loads are free of
-// bank conflicts.
+// The counts are stored transposed (part d of thread chunk d / r at column
+// d % r, r = M / NT parts per thread), so that the scan's per-thread chunks
+// are read without bank conflicts.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kLeafRank = 16;
 
@@ -1037,8 +1037,9 @@ struct LeafShared {
   uint32_t n_big;
 };
 
-// B [cap] u64 | P [cap] u64 (the next bucket, staged) | H [2 cap] u32 (the
-// u16 counts; afterwards the merge scratch of the large parts) | big list
+// B [cap] u64 | P [cap] u64 (the next bucket, staged) | H [cap] u32 (part
+// counts, then (start, count) words) | W [cap] u32 (each slot's part word)
+// | big list.  H and W together are the merge scratch of the large parts.
 __host__ __device__ inline size_t leaf_sort_smem(uint32_t cap) {
   return (size_t)cap * 24 + ((size_t)cap / kLeafRank + 1) * 4 + 16;
 }
@@ -1055,7 +1056,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // one part of more than kLeafRank keys, B[s, s + c): sorted by one warp
-// (scratch at the same offsets of S) and written to out[s, s + c)
+// (scratch at the same offsets of S) and written to out[off + s, ...)
 __device__ __noinline__ void leaf_big_part(uint64_t* B, uint64_t* S, uint32_t s, uint32_t c,
                                            uint64_t* out, uint32_t off, uint32_t kt,
                                            uint32_t lane, uint32_t* status) {
@@ -1085,23 +1086,23 @@ __device__ __noinline__ void leaf_big_part(uint64_t* B, uint64_t* S, uint32_t s,
   __syncwarp();
 }
 
-template <uint32_t NT, uint32_t KPT, uint32_t OVS>
+template <uint32_t NT, uint32_t KPT>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
     k_leaf_sort(const uint2* __restrict__ list, const uint32_t* __restrict__ count,
                 const uint64_t* __restrict__ X, uint64_t* out, uint32_t kt, uint32_t* status) {
   constexpr uint32_t CAP = NT * KPT, NW = NT / 32;
   constexpr uint32_t LNT = NT == 32 ? 5 : NT == 64 ? 6 : NT == 128 ? 7 : NT == 256 ? 8
                          : NT == 512 ? 9 : 10;
-  constexpr uint32_t QMAX = (KPT << OVS) / 8 > 0 ? (KPT << OVS) / 8 : 1;
   static_assert((1u << LNT) == NT, "NT must be a power of two, 32..1024");
-  static_assert(OVS <= 2 && KPT >= 1, "counts sized for M <= 4 cap");
+  static_assert(KPT >= 1 && (KPT & (KPT - 1)) == 0 && CAP <= 8192, "KPT a power of two");
   if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ LeafShared<NT> sh;
   uint64_t* B = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* Pf = B + CAP;
   uint32_t* H = reinterpret_cast<uint32_t*>(Pf + CAP);
-  uint32_t* big = H + 2 * CAP;
+  uint32_t* Wp = H + CAP;
+  uint32_t* big = Wp + CAP;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nitems = *count;
   const uint32_t G = gridDim.x;
@@ -1118,16 +1119,11 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
   for (; li < nitems; li += G) {
     const uint32_t off = rec.x, n = rec.y;
     const uint2 rec2 = li + 2 * G < nitems ? list[li + 2 * G] : make_uint2(0u, 0u);
-    const uint32_t m = max(4u, (n > 1 ? 32u - __clz(n - 1) : 0u) + OVS);
-    const uint32_t M = 1u << m;                       // parts, >= 16
-    const uint32_t Gg = M >> 3;                       // groups of eight counts
-    const uint32_t lq = Gg > NT ? m - 3 - LNT : 0u;   // q = 2^lq groups per thread
-    const uint32_t qmask = (1u << lq) - 1u;
-    // u16 slot of part d
-    auto slot = [&](uint32_t d) -> uint32_t {
-      const uint32_t g = d >> 3;
-      return ((((g & qmask) << LNT) | (g >> lq)) << 3) | (d & 7u);
-    };
+    const uint32_t m = n > 1 ? 32u - __clz(n - 1) : 0u;  // M = 2^m >= n parts, M <= CAP
+    const uint32_t M = 1u << m;
+    const uint32_t lr = m > LNT ? m - LNT : 0u;          // r = 2^lr parts per thread chunk
+    const uint32_t rmask = (1u << lr) - 1u;
+    auto hix = [&](uint32_t d) -> uint32_t { return ((d & rmask) << LNT) | (d >> lr); };
     cp_async_wait_all();
     __syncthreads();  // the bucket is staged in P (every thread's copies)
     uint64_t k[KPT];
@@ -1141,7 +1137,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
         mx = k[j] > mx ? k[j] : mx;
       }
     }
-    for (uint32_t d = tid; d < (M >> 1); d += NT) H[d] = 0u;
+    for (uint32_t d = tid; d < M; d += NT) H[d] = 0u;
     if (tid == 0) sh.n_big = 0;
 #pragma unroll
     for (int d = 16; d; d >>= 1) {
@@ -1176,63 +1172,46 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
     } else {
       const uint32_t nb = 64u - (uint32_t)__clzll((long long)(mx - mn));
       const uint32_t sft = nb > m ? nb - m : 0u;
-      uint32_t sl[KPT], rk[KPT];
+      uint32_t hx[KPT], rk[KPT];
 #pragma unroll
       for (uint32_t j = 0; j < KPT; ++j) {
         const uint32_t i = tid + j * NT;
-        sl[j] = slot((uint32_t)((k[j] - mn) >> sft));
-        const uint32_t hs = (sl[j] & 1u) << 4;
-        rk[j] = i < n ? (atomicAdd(&H[sl[j] >> 1], 1u << hs) >> hs) & 0xFFFFu : 0u;
+        hx[j] = hix((uint32_t)((k[j] - mn) >> sft));
+        rk[j] = i < n ? atomicAdd(&H[hx[j]], 1u) : 0u;
       }
       __syncthreads();
-      // exclusive scan of the counts: thread t owns groups [t q, t q + q)
+      // exclusive scan: thread t owns parts [t r, t r + r), at H[c NT + t];
+      // each entry becomes start | count << 16 (both at most 8192)
       {
-        uint4* H4 = reinterpret_cast<uint4*>(H);
-        const uint32_t q = 1u << lq;
-        const bool own = tid * q < Gg;
-        uint4 gv[QMAX];
+        const uint32_t rr = 1u << lr;
+        const bool own = tid * rr < M;
         uint32_t sum = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < QMAX; ++i) {
-          if (own && i < q) {
-            gv[i] = H4[(i << LNT) | tid];
-            // eight counts <= 8192 each: the packed halves never carry
-            const uint32_t t4 = gv[i].x + gv[i].y + gv[i].z + gv[i].w;
-            sum += (t4 & 0xFFFFu) + (t4 >> 16);
-          }
-        }
+        if (own)
+          for (uint32_t c = 0; c < rr; ++c) sum += H[(c << LNT) | tid];
         const uint32_t inc = wscan(sum, lane);
         if (lane == 31) sh.wsum[wid] = inc;
         __syncthreads();
         uint32_t run = inc - sum;
 #pragma unroll
         for (uint32_t w = 0; w < NW; ++w) run += w < wid ? sh.wsum[w] : 0u;
-        auto ex2 = [&](uint32_t v) -> uint32_t {
-          const uint32_t lo = v & 0xFFFFu;
-          const uint32_t r = run | ((run + lo) << 16);
-          run += lo + (v >> 16);
-          return r;
-        };
-#pragma unroll
-        for (uint32_t i = 0; i < QMAX; ++i) {
-          if (own && i < q) {
-            uint4 o;
-            o.x = ex2(gv[i].x);
-            o.y = ex2(gv[i].y);
-            o.z = ex2(gv[i].z);
-            o.w = ex2(gv[i].w);
-            H4[(i << LNT) | tid] = o;
+        if (own)
+          for (uint32_t c = 0; c < rr; ++c) {
+            const uint32_t v = H[(c << LNT) | tid];
+            H[(c << LNT) | tid] = run | (v << 16);
+            run += v;
           }
-        }
       }
       __syncthreads();
-      const uint16_t* H16 = reinterpret_cast<const uint16_t*>(H);
 #pragma unroll
       for (uint32_t j = 0; j < KPT; ++j) {
         const uint32_t i = tid + j * NT;
         if (i < n) {
-          const uint32_t p = (uint32_t)H16[sl[j]] + rk[j];
-          if (PCF_IN(p, n, status)) B[p] = k[j];
+          const uint32_t sc = H[hx[j]];
+          const uint32_t p = (sc & 0xFFFFu) + rk[j];
+          if (PCF_IN(p, n, status)) {
+            B[p] = k[j];
+            Wp[p] = sc;
+          }
         }
       }
       __syncthreads();
@@ -1241,19 +1220,17 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
         const uint32_t p = tid + j * NT;
         if (p < n) {
           const uint64_t v = B[p];
-          const uint32_t d = (uint32_t)((v - mn) >> sft);
-          const uint32_t s = H16[slot(d)];
-          const uint32_t e = d + 1 < M ? (uint32_t)H16[slot(d + 1)] : n;
-          const uint32_t c = e - s;
+          const uint32_t sc = Wp[p];
+          const uint32_t s = sc & 0xFFFFu, c = sc >> 16;
           uint32_t pos = p;
           if (c > kLeafRank) {
-            if (p == s) big[atomicAdd(&sh.n_big, 1u)] = s | (c << 16);
+            if (p == s) big[atomicAdd(&sh.n_big, 1u)] = sc;
             continue;
           }
           if (c > 1)
-            pos = s + (sft <= 32 ? rank_in_lo32(B, s, e, p, (uint32_t)v - (uint32_t)mn,
+            pos = s + (sft <= 32 ? rank_in_lo32(B, s, s + c, p, (uint32_t)v - (uint32_t)mn,
                                                 (uint32_t)mn)
-                                 : rank_in(B, s, e, p, v));
+                                 : rank_in(B, s, s + c, p, v));
           if (PCF_IN_KEYS(off + pos, status)) out[off + pos] = bits_of_ord(v, kt);
         }
       }
@@ -1263,7 +1240,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
         leaf_big_part(B, reinterpret_cast<uint64_t*>(H), big[b] & 0xFFFFu, big[b] >> 16, out,
                       off, kt, lane, status);
     }
-    __syncthreads();  // B, H and the list are reused by the next bucket
+    __syncthreads();  // B, H, W and the list are reused by the next bucket
     rec = rec1;
     rec1 = rec2;
   }
@@ -1351,27 +1328,25 @@ static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const u
   return cudaGetLastError();
 }
 
-// the block-local sort of one size class: NT threads, KPT keys each,
-// parts 2^(ceil(log2 n) + 1)
+// the block-local sort of one size class: NT threads, KPT keys each
 template <uint32_t NT, uint32_t KPT>
 static cudaError_t launch_leaf_sort(const LaunchCfg& c, const uint2* list, const uint32_t* count,
                                     const uint64_t* X, uint64_t* out) {
-  constexpr uint32_t OVS = 1;
   const size_t smem = leaf_sort_smem(NT * KPT);
-  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT, OVS>);
+  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT>);
   if (e) return e;
   static int per_sm_cache[64] = {0};
   int dev = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   int per_sm = dev >= 0 && dev < 64 ? per_sm_cache[dev] : 0;
   if (per_sm <= 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT, OVS>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT>,
                                                       (int)NT, smem);
     if (e) return e;
     per_sm = per_sm > 0 ? per_sm : 1;
     if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
   }
-  k_leaf_sort<NT, KPT, OVS><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT,
+  k_leaf_sort<NT, KPT><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT,
                               smem, c.stream>>>(list, count, X, out, c.kt, c.status);
   return cudaGetLastError();
 }
