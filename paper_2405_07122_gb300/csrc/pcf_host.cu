@@ -1120,16 +1120,20 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
       ctx->stats.bytes_moved += n_level * (2 /*hist2*/ + 10 + 8 /*scatter2*/) +
                                 (pairs ? n_level * 8 : 0);
     }
-    // buckets: Alg. 1's per-bucket decision, then the on-chip finish
+    // buckets: Alg. 1's per-bucket decision (for the block-local leaf sort
+    // it also lists the leaf buckets by size class), then the on-chip finish
     uint32_t* next_flag = as<uint32_t>(ctx->next);
+    uint32_t* leaf_counts = (uint32_t*)((char*)ctx->misc.p + 128);
+    CK(ensure(ctx->olist, (size_t)L.n_buckets * olist_per_bucket));
+    if (lc.leaf_sort) CK(cudaMemsetAsync(leaf_counts, 0, 4 * kMaxLeafClasses, st));
     CK(launch_buckets(lc, d_segs, S, L.n_buckets, L.dp.bb, as<Group>(ctx->groups),
                       as<uint32_t>(ctx->cmat1), as<uint32_t>(ctx->cmat2), L.two_pass, cap,
                       (uint32_t)ctx->policy.tau, X, Xv, out_k, out_v, as<BRec>(ctx->leaf),
-                      next_flag, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items));
-    CK(ensure(ctx->olist, (size_t)L.n_buckets * olist_per_bucket));
+                      next_flag, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items,
+                      lc.leaf_sort ? as<uint2>(ctx->olist) : nullptr,
+                      lc.leaf_sort ? leaf_counts : nullptr, leaf_sort_classes(cap)));
     CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k, out_v,
-                     ctx->policy, ptab, as<uint32_t>(ctx->olist),
-                     (uint32_t*)((char*)ctx->misc.p + 128)));
+                     ctx->policy, ptab, as<uint32_t>(ctx->olist), leaf_counts, lc.leaf_sort));
     tm.mark(6);
     // the next level's plan, built on the device into the other buffer; a
     // next-level (sub)array holds more than cap keys, which bounds its rows

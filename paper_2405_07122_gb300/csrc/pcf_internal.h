@@ -284,7 +284,9 @@ cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint
                            const uint32_t* cmat1, const uint32_t* cmat2, bool two_pass,
                            uint32_t leaf_cap, uint32_t tau, const uint64_t* X, const uint32_t* Xv,
                            uint64_t* out_k, uint32_t* out_v, BRec* brec, uint32_t* next_flag,
-                           FbItem* fb, LevelOut* lo, uint32_t max_items);
+                           FbItem* fb, LevelOut* lo, uint32_t max_items,
+                           uint2* leaf_lists = nullptr, uint32_t* leaf_counts = nullptr,
+                           uint32_t leaf_classes = 0);
 // builds the next level's plan from the flagged buckets (next_flag[B] = 1
 // for a bucket of the next level; scanned in place), s_max rows at most;
 // n_flagged receives the number of (sub)arrays
@@ -320,15 +322,21 @@ uint32_t onchip_classes(uint32_t leaf_cap);
 // ... up to leaf_cap: leaf_sort_classes(cap) of them, at most kMaxLeafClasses.
 constexpr uint32_t kMaxLeafClasses = 8;
 uint32_t leaf_sort_classes(uint32_t leaf_cap);
+__device__ __forceinline__ uint32_t leaf_size_class(uint32_t n) {
+  return n <= 64 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 6u;
+}
 // The largest bucket finished on chip: leaf_cap (key-value sorts at most
 // 1024), halved until the policy's slice fits one block's shared memory.
 uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs);
 // lists: (block-local sort: leaf_sort_classes, else onchip_classes)(leaf_cap)
 // x nb x 8 bytes of scratch (u32 record indices, or (offset, size) pairs
 // for the block-local sort); counts: kMaxLeafClasses u32
+// prelisted: the block-local sort's class lists and counts were already
+// written (by k_buckets), so they are not built from the records again
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
-                          Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts);
+                          Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts,
+                          bool prelisted = false);
 cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                             const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
                             uint64_t* ord_lohi);

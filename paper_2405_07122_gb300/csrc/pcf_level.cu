@@ -828,7 +828,8 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
                                                  const uint32_t* __restrict__ Xv, uint64_t* out_k,
                                                  uint32_t* out_v, BRec* brec, uint32_t* next_flag,
                                                  FbItem* fb, LevelOut* lo, uint32_t max_items,
-                                                 uint32_t* status) {
+                                                 uint2* leaf_lists, uint32_t* leaf_counts,
+                                                 uint32_t leaf_classes, uint32_t* status) {
   if (pcf_aborted(status)) return;
   // [kTiny][256] (transposed: thread t owns column t, so accesses are
   // conflict-free)
@@ -933,6 +934,22 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
   if (in) next_flag[B] = is_next ? 1u : 0u;
   const uint32_t i_leaf = warp_append(&lo->n_leaf, is_leaf);
   (void)i_leaf;
+  // the block-local sort's class lists, (offset, size) per leaf bucket
+  if (leaf_lists) {
+    const uint32_t cls = is_leaf ? min(leaf_size_class(size), leaf_classes - 1) : kMaxLeafClasses;
+#pragma unroll
+    for (uint32_t k = 0; k < kMaxLeafClasses; ++k) {
+      const uint32_t bal = __ballot_sync(~0u, cls == k);
+      if (!bal) continue;
+      const int leader = __ffs(bal) - 1;
+      uint32_t base = 0;
+      if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(&leaf_counts[k], (uint32_t)__popc(bal));
+      base = __shfl_sync(~0u, base, leader);
+      if (cls == k)
+        leaf_lists[(size_t)k * n_buckets + base + __popc(bal & lanemask_lt())] =
+            make_uint2((uint32_t)off, size);
+    }
+  }
   const uint32_t i_next = warp_append(&lo->n_next, is_next);
   (void)i_next;
   const uint32_t i_fb = warp_append(&lo->n_fb, is_fb);
@@ -1522,16 +1539,19 @@ cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint
                            const uint32_t* cmat2, bool two_pass, uint32_t leaf_cap, uint32_t tau,
                            const uint64_t* X, const uint32_t* Xv, uint64_t* out_k, uint32_t* out_v,
                            BRec* brec, uint32_t* next_flag, FbItem* fb, LevelOut* lo,
-                           uint32_t max_items) {
+                           uint32_t max_items, uint2* leaf_lists, uint32_t* leaf_counts,
+                           uint32_t leaf_classes) {
   if (!n_buckets) return cudaSuccess;
   if (c.pairs)
     k_buckets<true><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
         segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
-        c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, c.status);
+        c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, nullptr, nullptr, 0,
+        c.status);
   else
     k_buckets<false><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
         segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
-        c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, c.status);
+        c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, leaf_lists, leaf_counts,
+        leaf_classes, c.status);
   count_launch(c);
   return cudaGetLastError();
 }

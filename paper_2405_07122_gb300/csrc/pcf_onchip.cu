@@ -551,12 +551,6 @@ __device__ __forceinline__ uint32_t size_class(uint32_t n) {
   return n <= 256 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 8u;
 }
 
-// The block-local sort's classes: (0, 64], (64, 128], (128, 256], then
-// doubling up to leaf_cap.
-__device__ __forceinline__ uint32_t leaf_size_class(uint32_t n) {
-  return n <= 64 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 6u;
-}
-
 // recs: entries are (offset, size) pairs (uint2) in the block-local sort's
 // classes instead of record indices in the Learned-Sort kernels' classes
 __global__ void k_leaf_lists(const BRec* __restrict__ br, uint32_t nb, uint32_t ncls,
@@ -1366,17 +1360,21 @@ uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs) {
 
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
-                          Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts) {
+                          Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts,
+                          bool prelisted) {
   if (!nb) return cudaSuccess;
   // size classes (0, 256], (256, 512], (512, 1024], ... clipped to leaf_cap
   const bool recs = c.leaf_sort && !c.pairs;
   const uint32_t ncls = recs ? leaf_sort_classes(leaf_cap) : onchip_classes(leaf_cap);
-  cudaError_t e = cudaMemsetAsync(counts, 0, 4 * kMaxLeafClasses, c.stream);
-  if (e) return e;
-  k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts, c.status,
-                                                        recs ? 1 : 0);
-  count_launch(c);
-  if ((e = cudaGetLastError())) return e;
+  cudaError_t e = cudaSuccess;
+  if (!(prelisted && recs)) {
+    e = cudaMemsetAsync(counts, 0, 4 * kMaxLeafClasses, c.stream);
+    if (e) return e;
+    k_leaf_lists<<<(nb + 255) / 256, 256, 0, c.stream>>>(br, nb, ncls, lists, counts, c.status,
+                                                          recs ? 1 : 0);
+    count_launch(c);
+    if ((e = cudaGetLastError())) return e;
+  }
   if (recs) {
     // the whole bucket by the block-local Standard-Sort: a warp for up to
     // 256 keys (2, 4 or 8 per lane), then NT = capw / 8 threads

@@ -104,12 +104,14 @@ def test_new_data_same_plan_replays(P, ctx):
     g.close()
 
 
-def test_new_data_other_plan_sorts_again(P, ctx):
+def test_new_data_other_plan_sorts_again(P):
     n = 2**22
     offs = _offsets([n])
     xu = W.f64_keys("uniform", n, 3)
     xl = W.f64_keys("lognormal", n, 4)
-    # precondition: LogNormal keys take a second global level, Uniform none
+    # precondition: LogNormal keys take a second global level (its densest
+    # level-0 buckets exceed 2048 keys), Uniform none
+    ctx = P.Context(0, tuning=dict(leaf_cap=2048))
     tmp = torch.empty_like(_dev(xl))
     ctx.sort_keys(_dev(xl), tmp, key_type="f64")
     assert ctx.last_stats()["levels"] >= 2
@@ -135,6 +137,7 @@ def test_new_data_other_plan_sorts_again(P, ctx):
     torch.cuda.synchronize()
     _check(o, xu, offs, 5)
     g.close()
+    ctx.close()
 
 
 @pytest.mark.parametrize("kt", ["f64", "u64"])
