@@ -1031,11 +1031,12 @@ struct LeafShared {
   uint32_t n_big;
 };
 
-// B [cap] u64 | P [cap] u64 (the next bucket, staged) | H [cap] u32 (part
-// counts, then (start, count) words) | W [cap] u32 (each slot's part word)
-// | big list.  H and W together are the merge scratch of the large parts.
-__host__ __device__ inline size_t leaf_sort_smem(uint32_t cap) {
-  return (size_t)cap * 24 + ((size_t)cap / kLeafRank + 1) * 4 + 16;
+// B [cap] u64 | P [cap] u64 (the next bucket, staged) | W [cap] u32 (each
+// slot's part word) | H [cap << ovs] u32 (part counts, then (start, count)
+// words) | big list.  W and H together are the merge scratch of the large
+// parts.
+__host__ __device__ inline size_t leaf_sort_smem(uint32_t cap, uint32_t ovs) {
+  return (size_t)cap * 20 + ((size_t)cap << ovs) * 4 + ((size_t)cap / kLeafRank + 1) * 4 + 16;
 }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
@@ -1080,7 +1081,7 @@ __device__ __noinline__ void leaf_big_part(uint64_t* B, uint64_t* S, uint32_t s,
   __syncwarp();
 }
 
-template <uint32_t NT, uint32_t KPT>
+template <uint32_t NT, uint32_t KPT, uint32_t OVS>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
     k_leaf_sort(const uint2* __restrict__ list, const uint32_t* __restrict__ count,
                 const uint64_t* __restrict__ X, uint64_t* out, uint32_t kt, uint32_t* status) {
@@ -1094,9 +1095,9 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
   __shared__ LeafShared<NT> sh;
   uint64_t* B = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* Pf = B + CAP;
-  uint32_t* H = reinterpret_cast<uint32_t*>(Pf + CAP);
-  uint32_t* Wp = H + CAP;
-  uint32_t* big = Wp + CAP;
+  uint32_t* Wp = reinterpret_cast<uint32_t*>(Pf + CAP);
+  uint32_t* H = Wp + CAP;
+  uint32_t* big = H + (CAP << OVS);
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nitems = *count;
   const uint32_t G = gridDim.x;
@@ -1113,7 +1114,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
   for (; li < nitems; li += G) {
     const uint32_t off = rec.x, n = rec.y;
     const uint2 rec2 = li + 2 * G < nitems ? list[li + 2 * G] : make_uint2(0u, 0u);
-    const uint32_t m = n > 1 ? 32u - __clz(n - 1) : 0u;  // M = 2^m >= n parts, M <= CAP
+    const uint32_t m = (n > 1 ? 32u - __clz(n - 1) : 0u) + OVS;  // M = 2^m >= n parts
     const uint32_t M = 1u << m;
     const uint32_t lr = m > LNT ? m - LNT : 0u;          // r = 2^lr parts per thread chunk
     const uint32_t rmask = (1u << lr) - 1u;
@@ -1231,7 +1232,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
       __syncthreads();
       const uint32_t nbig = sh.n_big;
       for (uint32_t b = wid; b < nbig; b += NW)
-        leaf_big_part(B, reinterpret_cast<uint64_t*>(H), big[b] & 0xFFFFu, big[b] >> 16, out,
+        leaf_big_part(B, reinterpret_cast<uint64_t*>(Wp), big[b] & 0xFFFFu, big[b] >> 16, out,
                       off, kt, lane, status);
     }
     __syncthreads();  // B, H, W and the list are reused by the next bucket
@@ -1322,25 +1323,26 @@ static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const u
   return cudaGetLastError();
 }
 
-// the block-local sort of one size class: NT threads, KPT keys each
-template <uint32_t NT, uint32_t KPT>
+// the block-local sort of one size class: NT threads, KPT keys each, parts
+// 2^(ceil(log2 n) + OVS)
+template <uint32_t NT, uint32_t KPT, uint32_t OVS = 0u>
 static cudaError_t launch_leaf_sort(const LaunchCfg& c, const uint2* list, const uint32_t* count,
                                     const uint64_t* X, uint64_t* out) {
-  const size_t smem = leaf_sort_smem(NT * KPT);
-  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT>);
+  const size_t smem = leaf_sort_smem(NT * KPT, OVS);
+  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT, OVS>);
   if (e) return e;
   static int per_sm_cache[64] = {0};
   int dev = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   int per_sm = dev >= 0 && dev < 64 ? per_sm_cache[dev] : 0;
   if (per_sm <= 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT, OVS>,
                                                       (int)NT, smem);
     if (e) return e;
     per_sm = per_sm > 0 ? per_sm : 1;
     if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
   }
-  k_leaf_sort<NT, KPT><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT,
+  k_leaf_sort<NT, KPT, OVS><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT,
                               smem, c.stream>>>(list, count, X, out, c.kt, c.status);
   return cudaGetLastError();
 }
