@@ -1112,7 +1112,10 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
   }
   cp_async_commit();
   for (; li < nitems; li += G) {
-    const uint32_t off = rec.x, n = rec.y;
+    // a record larger than this class holds is an internal error (flagged,
+    // nothing written for it)
+    if (rec.y > CAP && tid == 0) atomicOr(status, STATUS_INTERNAL);
+    const uint32_t off = rec.x, n = rec.y <= CAP ? rec.y : 0u;
     const uint2 rec2 = li + 2 * G < nitems ? list[li + 2 * G] : make_uint2(0u, 0u);
     const uint32_t m = (n > 1 ? 32u - __clz(n - 1) : 0u) + OVS;  // M = 2^m >= n parts
     const uint32_t M = 1u << m;
@@ -1158,7 +1161,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
       mn = sh.mn[w] < mn ? sh.mn[w] : mn;
       mx = sh.mx[w] > mx ? sh.mx[w] : mx;
     }
-    if (mn == mx) {  // one value (or one key): already sorted
+    if (mn >= mx) {  // one value (or one key, or none): already sorted
 #pragma unroll
       for (uint32_t j = 0; j < KPT; ++j) {
         const uint32_t i = tid + j * NT;
