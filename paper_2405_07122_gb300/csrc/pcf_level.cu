@@ -61,21 +61,38 @@ __global__ void __launch_bounds__(256) k_range(Seg* segs, uint32_t S, const uint
   const uint64_t end = min(off + n, base + kRangeTile);
   uint64_t mn = ~0ull, mx = 0ull;
   bool nan = false;
-  uint64_t i = base + threadIdx.x;
-  for (; i + 3 * 256 < end; i += 4 * 256) {
-    uint64_t b0 = ld_nc(keys + i), b1 = ld_nc(keys + i + 256), b2 = ld_nc(keys + i + 512),
-             b3 = ld_nc(keys + i + 768);
-    if (check_nan) nan |= is_nan_bits(b0) | is_nan_bits(b1) | is_nan_bits(b2) | is_nan_bits(b3);
-    uint64_t o0 = ord_of(b0, kt), o1 = ord_of(b1, kt), o2 = ord_of(b2, kt), o3 = ord_of(b3, kt);
-    mn = min(mn, min(min(o0, o1), min(o2, o3)));
-    mx = max(mx, max(max(o0, o1), max(o2, o3)));
-  }
-  for (; i < end; i += 256) {
-    uint64_t b = ld_nc(keys + i);
+  auto take = [&](uint64_t b) {
     if (check_nan) nan |= is_nan_bits(b);
-    uint64_t o = ord_of(b, kt);
+    const uint64_t o = ord_of(b, kt);
     mn = min(mn, o);
     mx = max(mx, o);
+  };
+  // 16-byte loads of two keys over the 16-byte aligned middle [a0, a1); the
+  // key buffers are 8-byte aligned, so at most one key at each end is loaded
+  // on its own
+  const uint64_t a0 = min(end, base + (((uintptr_t)(keys + base) & 15u) ? 1u : 0u));
+  const uint64_t a1 = a0 + ((end - a0) & ~(uint64_t)1);
+  if (threadIdx.x == 0 && base < a0) take(ld_nc(keys + base));
+  if (threadIdx.x == 32 && a1 < end) take(ld_nc(keys + a1));
+  const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(keys + a0);
+  const uint32_t n2 = (uint32_t)((a1 - a0) >> 1);
+  uint32_t q = threadIdx.x;
+  for (; q + 3 * 256 < n2; q += 4 * 256) {
+    const ulonglong2 w0 = __ldg(v2 + q), w1 = __ldg(v2 + q + 256), w2 = __ldg(v2 + q + 512),
+                     w3 = __ldg(v2 + q + 768);
+    take(w0.x);
+    take(w0.y);
+    take(w1.x);
+    take(w1.y);
+    take(w2.x);
+    take(w2.y);
+    take(w3.x);
+    take(w3.y);
+  }
+  for (; q < n2; q += 256) {
+    const ulonglong2 w = __ldg(v2 + q);
+    take(w.x);
+    take(w.y);
   }
   for (int d = 16; d; d >>= 1) {
     mn = min(mn, (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d));

@@ -349,3 +349,17 @@ def test_host_batch_pipelined(ctx, pinned):
     for u, h in zip(us, hu):
         ref, _ = oracle.sort(u)
         assert same_bits(h.numpy().view(np.uint64), ref)
+
+
+@pytest.mark.parametrize("start", [0, 1, 3])
+def test_buffers_at_any_8_byte_offset(ctx, start):
+    # key buffers that start 8 bytes past a 16-byte boundary (a slice at an
+    # odd index): the vector loads must begin at the first aligned key
+    x = W.f64_keys("normal", 3 * 10**5 + 7, 30 + start)
+    t = to_dev(x)
+    src = t[start:]
+    out = torch.empty(src.numel() + 1, dtype=torch.float64, device="cuda")[1:]
+    ctx.sort_keys(src, out, key_type="f64")
+    torch.cuda.synchronize()
+    ref, _ = oracle.sort(x[start:])
+    assert same_bits(out.cpu().numpy(), ref)
