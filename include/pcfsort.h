@@ -254,9 +254,13 @@ pcf_status pcf_sort_segmented_static(const void* d_keys_in, void* d_keys_out,
  * and returns when they are sorted.  It replays the graph; a guard kernel
  * at each level's end compares the device's own plan with the recorded one,
  * and on a difference every later kernel of the graph returns at once and
- * the call sorts the input again without the graph, keeping the new plan
- * and capturing again (*replayed = 0).  The output is the same either way
- * (the unique sorted order).  A sort whose recording sent buckets to the
+ * the call sorts the input again without the graph (*replayed = 0).  The
+ * graph keeps its capture, unless the plan of this input is the one the
+ * previous miss met too: then it captures that plan instead.  After a miss
+ * the next launch sorts without the graph first and replays again once an
+ * input takes the captured plan, so inputs whose plans keep changing cost
+ * one plain sort each.  The output is the same either way (the unique
+ * sorted order).  A sort whose recording sent buckets to the
  * standard sort (duplicate-heavy input; its rounds are planned on the host)
  * is not captured: its launches sort without the graph.
  *

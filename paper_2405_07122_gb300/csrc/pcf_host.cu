@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -719,6 +720,30 @@ pcf_status run_fallback(pcf_ctx* ctx, const LaunchCfg& lc, std::vector<FbItem> w
 }
 
 
+// The addresses of every buffer a context holds, hashed: a captured graph's
+// nodes point into them, so a graph captured under another signature may
+// point at freed memory and must not be replayed.
+uint64_t buffers_signature(const pcf_ctx* c) {
+  const void* ptrs[] = {c->tmp_k.p, c->tmp_v.p, c->tmp_aux.p, c->host_keys.p, c->segs.p,
+                        c->bases.p, c->tpool.p, c->done.p, c->cmat1.p, c->cmat2.p, c->sw.p,
+                        c->groups.p, c->gtiles.p, c->gcent.p, c->gtot.p, c->leaf.p, c->next.p,
+                        c->fb.p, c->lout.p, c->status.p, c->misc.p, c->fb_items.p,
+                        c->fb_bases.p, c->fb_lohi.p, c->small_items.p, c->segs_b.p, c->pcols.p,
+                        c->pbsums.p, c->olist.p, c->jbuf.p, c->small_segs.p, c->fb_cnt.p,
+                        c->bcounts.p, c->bmax.p, c->ptab.p, c->pipe_keys.p, c->h_stage.p,
+                        c->h_lout.p, c->h_status.p, c->h_items.p, c->h_stage_small.p, c->h_fb.p,
+                        c->h_offs.p};
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over the addresses
+  for (const void* q : ptrs) {
+    uint64_t v = (uint64_t)(uintptr_t)q;
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xFFu;
+      h *= 1099511628211ull;
+    }
+  }
+  return h;
+}
+
 // Device bytes a context holds (every workspace buffer's capacity).
 uint64_t workspace_held(const pcf_ctx* c) {
   const DevBuf* bufs[] = {&c->tmp_k, &c->tmp_v, &c->tmp_aux, &c->host_keys, &c->segs, &c->bases,
@@ -1264,11 +1289,15 @@ struct pcf_graph {
   uint64_t n = 0;  // keys in all segments (0: every launch has nothing to do)
   uint32_t kt = 0;
   bool pairs = false;
-  SortRecord rec;
+  SortRecord rec;              // the plan the graph holds
+  SortRecord pending;          // the plan of the last input that missed it
+  bool has_pending = false;
+  bool last_missed = false;    // the last launch did not replay
   DevBuf d_blob;               // the recording's read-backs on the device, for the guards
   HostBuf arena;               // the captured standard-sort rounds' uploads
   cudaStream_t cs = nullptr;   // the stream captures run on
   cudaGraphExec_t exec = nullptr;
+  uint64_t sig = 0;            // the context's buffers_signature when exec was captured
   uint64_t replays = 0, eager_runs = 0;
   ~pcf_graph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1278,24 +1307,75 @@ struct pcf_graph {
 
 namespace {
 
-// Sorts the graph's input once without a graph, keeping its host decisions,
-// then captures the same sort from them.  If the capture fails the graph's
-// launches sort without it.
+// The decisions a capture depends on (what the guards compare): per level
+// the next level's plan and the standard-sort items, and every read-back of
+// the standard-sort rounds.
+bool same_plan(const SortRecord& a, const SortRecord& b) {
+  if (a.levels.size() != b.levels.size() || a.fb_lists.size() != b.fb_lists.size() ||
+      a.rounds.size() != b.rounds.size())
+    return false;
+  for (size_t i = 0; i < a.levels.size(); ++i) {
+    const LevelOut &x = a.levels[i], &y = b.levels[i];
+    if (x.n_fb != y.n_fb || x.max_fb_n != y.max_fb_n ||
+        memcmp(&x.plan, &y.plan, sizeof(PlanTotals)) != 0)
+      return false;
+  }
+  for (size_t i = 0; i < a.fb_lists.size(); ++i) {
+    if (a.fb_lists[i].size() != b.fb_lists[i].size() ||
+        memcmp(a.fb_lists[i].data(), b.fb_lists[i].data(),
+               a.fb_lists[i].size() * sizeof(FbItem)) != 0)
+      return false;
+  }
+  for (size_t i = 0; i < a.rounds.size(); ++i)
+    for (int k = 0; k < 4; ++k)
+      if (a.rounds[i].got[k] != b.rounds[i].got[k]) return false;
+  return true;
+}
+
+// Sorts the graph's input once without a graph, keeping its host decisions.
+// A new graph captures the same sort from them.  A graph whose plan the
+// input missed keeps its capture unless the plan just recorded is the one
+// the previous miss recorded too (a plan that comes back is worth a
+// capture; one input's plan alone is not: on inputs whose plans keep
+// changing every launch would pay a capture).  If the capture fails the
+// graph's launches sort without it.
 pcf_status graph_build(pcf_graph* g, cudaStream_t st) {
   pcf_ctx* ctx = g->ctx;
-  if (g->exec) {
-    cudaGraphExecDestroy(g->exec);
-    g->exec = nullptr;
-  }
-  g->rec = SortRecord{};
+  SortRecord nrec;
   pcf_status r = run_sort(ctx, g->in_k, g->in_v, g->out_k, g->out_v, g->segs, g->kt, g->pairs, st,
-                          0xFFFFFFFFu, kSpinLimit, RUN_RECORD, &g->rec);
+                          0xFFFFFFFFu, kSpinLimit, RUN_RECORD, &nrec);
   if (r != PCF_OK) {
     cudaStreamSynchronize(st);
     return r;
   }
   ++g->eager_runs;
   if (g->n == 0) return PCF_OK;  // nothing to capture (no status buffers either)
+  const bool first = g->eager_runs == 1;
+  // a capture made before one of the context's buffers moved is stale
+  if (g->exec && g->sig != buffers_signature(ctx)) {
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  const bool captured_plan = !first && same_plan(nrec, g->rec);
+  if (g->exec && captured_plan) {  // the captured plan holds again: replay next time
+    g->last_missed = false;
+    g->has_pending = false;
+    return PCF_OK;
+  }
+  const bool repeat = captured_plan || (g->has_pending && same_plan(nrec, g->pending));
+  if (!first && !repeat) {
+    g->pending = std::move(nrec);
+    g->has_pending = true;
+    g->last_missed = true;
+    return PCF_OK;
+  }
+  g->last_missed = false;
+  if (g->exec) {
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  g->rec = std::move(nrec);
+  g->has_pending = false;
   // the read-backs the guards compare with, in one device blob
   const SortRecord& rec = g->rec;
   Replay rp;
@@ -1321,6 +1401,7 @@ pcf_status graph_build(pcf_graph* g, cudaStream_t st) {
   rp.d_blob = (const uint8_t*)g->d_blob.p;
   rp.arena = &g->arena;
   CK(cudaStreamBeginCapture(g->cs, cudaStreamCaptureModeThreadLocal));
+  g->sig = buffers_signature(ctx);
   g_capturing = true;
   r = run_sort(ctx, g->in_k, g->in_v, g->out_k, g->out_v, g->segs, g->kt, g->pairs, g->cs,
                0xFFFFFFFFu, kSpinLimit, RUN_CAPTURE, nullptr, &rp);
@@ -1616,7 +1697,15 @@ pcf_status pcf_graph_launch(pcf_graph* g, void* stream, int* replayed) {
   pcf_ctx* ctx = g->ctx;
   const cudaStream_t st = (cudaStream_t)stream;
   CK(cudaSetDevice(ctx->device));
-  if (g->exec) {
+  if (g->exec && g->sig != buffers_signature(ctx)) {
+    // a workspace buffer has moved since the capture: its nodes are stale
+    cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
+  // after a miss the next input is sorted without the graph first (its
+  // plan decides whether the graph replays again): inputs whose plans keep
+  // changing pay one eager sort each, not a replay cut short and a sort
+  if (g->exec && !g->last_missed) {
     CK(cudaGraphLaunch(g->exec, st));
     CK(launch_xfer(st, ctx->h_status.dp, ctx->status.p, 4));
     CK(cudaStreamSynchronize(st));
@@ -1631,6 +1720,7 @@ pcf_status pcf_graph_launch(pcf_graph* g, void* stream, int* replayed) {
     if (stw & (STATUS_INTERNAL | STATUS_BOUNDS)) return PCF_ERR_INTERNAL;
     // STATUS_REPLAN: this input takes another plan than the recorded one;
     // the graph stopped at that level's end and left the input as it was
+    g->last_missed = true;
   }
   return graph_build(g, st);
 }

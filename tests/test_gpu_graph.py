@@ -124,18 +124,29 @@ def test_new_data_other_plan_sorts_again(P):
     assert g.launch() is False  # the guard saw another plan: sorted again
     torch.cuda.synchronize()
     _check(o, xl, offs, 5)
-    info = g.info()
-    assert info["captured"] and info["eager_runs"] == 2
-    # recaptured from the new recording: the same input now replays
-    o.zero_()
-    assert g.launch() is True
-    torch.cuda.synchronize()
-    _check(o, xl, offs, 5)
-    # and back: the Uniform input no longer takes the recorded plan
-    t.copy_(_dev(xu))
-    assert g.launch() is False
-    torch.cuda.synchronize()
-    _check(o, xu, offs, 5)
+    assert g.info()["eager_runs"] == 2
+    # The graph keeps its capture after one miss, and captures a missed plan
+    # when it comes back on the next launch, or at once when the miss moved
+    # a workspace buffer (its nodes would point at freed memory).  Either
+    # way the same input replays within two more launches, and every output
+    # is the sorted input.
+    def settle(x):
+        t.copy_(_dev(x))
+        seen = []
+        for _ in range(3):
+            o.zero_()
+            seen.append(g.launch())
+            torch.cuda.synchronize()
+            _check(o, x, offs, 5)
+            if seen[-1]:
+                break
+        assert seen[-1] is True, seen
+        return seen
+
+    settle(xl)
+    assert settle(xu)[0] is False  # the LogNormal plan is held: Uniform misses first
+    assert settle(xu) == [True]
+    assert settle(xl)[0] is False
     g.close()
     ctx.close()
 
