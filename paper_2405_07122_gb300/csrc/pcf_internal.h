@@ -159,6 +159,67 @@ struct KeyBufs {
   const uint32_t* jbuf; // bucket id of every key of the level (written by k_hist1)
 };
 
+
+// ---- bulk (1-D tensor-memory-accelerator) copies into shared memory ----
+// A CTA stages a run of keys by one cp.async.bulk that completes on an
+// mbarrier; the consumers wait on the barrier's phase.  Every wait is
+// bounded by the global timer, so a copy that never lands ends the kernel
+// with STATUS_TIMEOUT instead of hanging it.
+// bounded waits on the staging barrier: about two seconds of the global
+// timer (each try_wait suspends for a hardware-chosen while)
+constexpr uint64_t kBulkWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+  // make the initialised barrier visible to the bulk-copy (async) proxy
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// one arrival that also expects `bytes` of bulk-copy transactions
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// waits (bounded) for the barrier's phase `parity` to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it >= (1u << 30)) return false;
+    if ((it & 63u) == 0) {
+      const uint64_t t = global_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > kBulkWaitNs) return false;
+    }
+  }
+}
+
+
 // ---- checked builds (-DPCF_CHECKED) ----
 // Index checks in place of a memory checker: a computed index is tested
 // against its buffer before the access; one out of bounds sets STATUS_BOUNDS

@@ -658,6 +658,220 @@ __device__ void scatter_tile(const ScatterSmem& sm, uint32_t D, uint64_t tile_of
 }
 
 // ---------------------------------------------------------------------------
+// The same stable scatter for keys-only sorts, with the sub-tiles staged by
+// bulk copies.  Two stages alternate: while the CTA ranks and writes one
+// sub-tile, the next one is already in flight into the other stage (one
+// cp.async.bulk for the keys and one for the digit words, completing on the
+// stage's mbarrier).  A consumed stage then serves as the staging area of
+// the digit-sorted sub-tile (keys, and the digit / carried low digit as u16
+// beside them) before the copy two sub-tiles ahead is issued into it.  The
+// ranks and the order of the write-out are those of scatter_tile.
+// ---------------------------------------------------------------------------
+template <int PASS>
+struct BulkStage {
+  static constexpr uint32_t kKeySlots = kScatterSub + 2;  // +2: 16-byte alignment shift
+  // digit words: pass 1 u32 bucket ids, pass 2 u16 low digits (+ shift slack)
+  static constexpr uint32_t kWordBytes = PASS == 1 ? (kScatterSub + 4) * 4 : (kScatterSub + 8) * 2;
+  static constexpr uint32_t kBytes = kKeySlots * 8 + ((kWordBytes + 15) & ~15u);
+};
+
+__host__ __device__ inline size_t scatter_bulk_smem_bytes(uint32_t D, int pass) {
+  size_t b = (size_t)8 * D * 2 + (size_t)D * 2 * 2 + (size_t)D * 4;
+  b = (b + 15) & ~(size_t)15;
+  b += 2 * (size_t)(pass == 1 ? BulkStage<1>::kBytes : BulkStage<2>::kBytes);
+  return b + 16;  // two mbarriers
+}
+
+// Issues the copy of keys [g0, g0 + n) and their digit words into stage st.
+// The 16-byte-aligned middle of each array goes by bulk copy; the at most
+// one key and three (pass 1) or seven (pass 2) words at the ragged ends are
+// loaded by threads 32.. with plain loads.
+template <int PASS>
+__device__ __forceinline__ void bulk_stage_issue(uint8_t* st, uint64_t* bar, const uint64_t* keys,
+                                                 const void* words, uint64_t g0, uint32_t n,
+                                                 uint32_t tid) {
+  constexpr uint32_t WB = PASS == 1 ? 4u : 2u;       // bytes per word
+  constexpr uint32_t WA = 16u / WB;                  // words per 16 bytes
+  uint64_t* K = reinterpret_cast<uint64_t*>(st);
+  uint8_t* Wd = st + BulkStage<PASS>::kKeySlots * 8;
+  const uint64_t kq = (reinterpret_cast<uintptr_t>(keys) >> 3) & 1u;
+  const uint64_t wq = (reinterpret_cast<uintptr_t>(words) / WB) & (WA - 1);
+  const uint64_t e = g0 + n;
+  // keys: slot of key g0 + i is i + ks
+  const uint32_t ks = (uint32_t)((g0 + kq) & 1u);
+  const uint64_t ka0 = min(e, ((g0 + kq + 1) & ~(uint64_t)1) - kq);
+  const uint64_t ka1 = max(ka0, ((e + kq) & ~(uint64_t)1) - kq);
+  // words: slot of word g0 + i is i + ws
+  const uint32_t ws = (uint32_t)((g0 + wq) & (WA - 1));
+  const uint64_t wa0 = min(e, ((g0 + wq + (uint64_t)(WA - 1)) & ~(uint64_t)(WA - 1)) - wq);
+  const uint64_t wa1 = max(wa0, ((e + wq) & ~(uint64_t)(WA - 1)) - wq);
+  if (tid == 0) {
+    const uint32_t kb = (uint32_t)(ka1 - ka0) * 8u, wb = (uint32_t)(wa1 - wa0) * WB;
+    mbar_arrive_tx(bar, kb + wb);
+    if (kb) bulk_g2s(K + (ka0 - g0 + ks), keys + ka0, kb, bar);
+    if (wb)
+      bulk_g2s(Wd + (size_t)(wa0 - g0 + ws) * WB,
+               reinterpret_cast<const uint8_t*>(words) + wa0 * WB, wb, bar);
+  }
+  // ragged ends: thread 32 + h for h < 2 the keys, then the words
+  if (tid >= 32 && tid < 32 + 2 + 2 * (WA - 1)) {
+    const uint32_t h = tid - 32;
+    if (h == 0) {
+      if (ka0 > g0) K[ks] = __ldg(keys + g0);
+    } else if (h == 1) {
+      if (ka1 < e) K[ka1 - g0 + ks] = __ldg(keys + ka1);
+    } else {
+      const uint32_t u = h - 2;  // 0 .. 2 (WA - 1) - 1
+      const uint64_t g = u < WA - 1 ? g0 + u : wa1 + (u - (WA - 1));
+      const bool v = u < WA - 1 ? g < wa0 : g < e;
+      if (v) {
+        if (PASS == 1)
+          reinterpret_cast<uint32_t*>(Wd)[g - g0 + ws] =
+              __ldg(reinterpret_cast<const uint32_t*>(words) + g);
+        else
+          reinterpret_cast<uint16_t*>(Wd)[g - g0 + ws] =
+              __ldg(reinterpret_cast<const uint16_t*>(words) + g);
+      }
+    }
+  }
+}
+
+// One count tile of a keys-only scatter, sub-tiles staged by bulk copies.
+// sm_stage: the two stages; bars: their mbarriers (initialised, phases in
+// ph).  Returns false when a staging wait gave up (STATUS_TIMEOUT set).
+template <int PASS>
+__device__ bool scatter_tile_bulk(const ScatterSmem& sm, uint8_t* stages, uint64_t* bars,
+                                  uint32_t D, uint64_t tile_off, uint32_t tile_n,
+                                  const void* __restrict__ words, uint32_t b2,
+                                  const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
+                                  uint16_t* __restrict__ dst_aux, uint32_t* status) {
+  (void)status;
+  const uint32_t tid = threadIdx.x, w = tid >> 5, l = tid & 31;
+  const uint32_t low_mask = (1u << b2) - 1u;
+  constexpr uint32_t WA = PASS == 1 ? 4u : 8u;
+  const uint32_t nsubs = (tile_n + kScatterSub - 1) / kScatterSub;
+  uint32_t ph = 0;  // bit b: the phase stage b waits for next
+  // the first two sub-tiles
+  for (uint32_t s = 0; s < 2 && s < nsubs; ++s)
+    bulk_stage_issue<PASS>(stages + (size_t)s * BulkStage<PASS>::kBytes, bars + s, src, words,
+                           tile_off + (uint64_t)s * kScatterSub,
+                           min(kScatterSub, tile_n - s * kScatterSub), tid);
+  for (uint32_t s = 0; s < nsubs; ++s) {
+    const uint32_t b = s & 1u;
+    uint8_t* st = stages + (size_t)b * BulkStage<PASS>::kBytes;
+    uint64_t* K = reinterpret_cast<uint64_t*>(st);
+    uint8_t* Wd = st + BulkStage<PASS>::kKeySlots * 8;
+    const uint64_t g0 = tile_off + (uint64_t)s * kScatterSub;
+    const uint32_t nsub = min(kScatterSub, tile_n - s * kScatterSub);
+    const uint32_t ks = (uint32_t)((g0 + ((reinterpret_cast<uintptr_t>(src) >> 3) & 1u)) & 1u);
+    const uint32_t ws = (uint32_t)((g0 + (reinterpret_cast<uintptr_t>(words) /
+                                          (PASS == 1 ? 4u : 2u))) & (WA - 1));
+    {
+      uint4* z = reinterpret_cast<uint4*>(sm.wcnt);  // 8*D u16, D a power of two >= 1
+      const uint32_t nz = (8 * D * 2 + 15) / 16;
+      for (uint32_t i = tid; i < nz; i += 256) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    const bool ok = mbar_wait(bars + b, (ph >> b) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(status, STATUS_TIMEOUT);
+      // one more bounded wait for each copy in flight before leaving
+      mbar_wait(bars + b, (ph >> b) & 1u);
+      if (s + 1 < nsubs) mbar_wait(bars + (b ^ 1u), (ph >> (b ^ 1u)) & 1u);
+      return false;
+    }
+    ph ^= 1u << b;
+    uint64_t key[kItems];
+    uint32_t dig[kItems], aux[kItems], rank[kItems];
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t li = w * (32 * kItems) + (uint32_t)k * 32 + l;
+      const bool v = li < nsub;
+      key[k] = v ? K[li + ks] : 0ull;
+      if (PASS == 1) {
+        const uint32_t j = v ? reinterpret_cast<const uint32_t*>(Wd)[li + ws] : 0u;
+        dig[k] = j >> b2;
+        aux[k] = j & low_mask;
+      } else {
+        dig[k] = v ? (uint32_t)reinterpret_cast<const uint16_t*>(Wd)[li + ws] : 0u;
+        aux[k] = 0u;
+      }
+    }
+    uint16_t* my = sm.wcnt + (size_t)w * D;
+    uint32_t* myw = reinterpret_cast<uint32_t*>(my);
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t li = w * (32 * kItems) + (uint32_t)k * 32 + l;
+      uint32_t prior = 0;
+      if (li < nsub) {
+        const uint32_t sh = (dig[k] & 1u) * 16u;
+        prior = (atomicAdd(&myw[dig[k] >> 1], 1u << sh) >> sh) & 0xFFFFu;
+      }
+      rank[k] = prior;
+    }
+    __syncthreads();  // every thread holds its items: the stage is free
+    for (uint32_t d = tid; d < D; d += 256) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) {
+        uint32_t c = sm.wcnt[(size_t)ww * D + d];
+        sm.wcnt[(size_t)ww * D + d] = (uint16_t)run;
+        run += c;
+      }
+      sm.dtot[d] = (uint16_t)run;
+    }
+    __syncthreads();
+    {
+      __shared__ uint32_t sh8[8];
+      const uint32_t per = (D + 255) / 256;
+      const uint32_t d0 = min(D, tid * per), d1 = min(D, d0 + per);
+      uint32_t sum = 0;
+      for (uint32_t d = d0; d < d1; ++d) sum += sm.dtot[d];
+      uint32_t tot;
+      uint32_t ex = block_excl_scan256(sum, sh8, &tot);
+      for (uint32_t d = d0; d < d1; ++d) {
+        sm.dbase[d] = (uint16_t)ex;
+        ex += sm.dtot[d];
+      }
+    }
+    __syncthreads();
+    // the digit-sorted sub-tile in the consumed stage: keys in K, digit and
+    // carried low digit as u16 in the word area
+    uint16_t* sdig = reinterpret_cast<uint16_t*>(Wd);
+    uint16_t* saux = sdig + kScatterSub;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t li = w * (32 * kItems) + (uint32_t)k * 32 + l;
+      if (li < nsub) {
+        const uint32_t pos = sm.dbase[dig[k]] + my[dig[k]] + rank[k];
+        if (!PCF_IN(pos, nsub, status)) continue;
+        K[pos] = key[k];
+        sdig[pos] = (uint16_t)dig[k];
+        if (PASS == 1) saux[pos] = (uint16_t)aux[k];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      const uint32_t pos = tid + (uint32_t)k * 256u;
+      if (pos < nsub) {
+        const uint32_t d = sdig[pos];
+        const uint64_t o = (uint64_t)sm.gofs[d] + (pos - sm.dbase[d]);
+        if (!PCF_IN_KEYS(o, status)) continue;
+        dst[o] = K[pos];
+        if (PASS == 1) dst_aux[o] = saux[pos];
+      }
+    }
+    __syncthreads();  // the stage is read out
+    for (uint32_t d = tid; d < D; d += 256) sm.gofs[d] += sm.dtot[d];
+    if (s + 2 < nsubs)
+      bulk_stage_issue<PASS>(st, bars + b, src, words, g0 + 2ull * kScatterSub,
+                             min(kScatterSub, tile_n - (s + 2) * kScatterSub), tid);
+    __syncthreads();
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // k_scatter1: pass 1 (src -> tmp), digit = high bits of the bucket id
 // ---------------------------------------------------------------------------
 template <bool PAIRS>
@@ -683,6 +897,71 @@ __global__ void __launch_bounds__(256, 2) k_scatter1(const Seg* segs, uint32_t S
   __syncthreads();
   scatter_tile<1, PAIRS>(sm, D, tile_off, tile_n, kb.jbuf, g.b2, kb.src, kb.src_v, nullptr, kb.tmp,
                          kb.tmp_v, kb.tmp_aux, status);
+}
+
+// k_scatter1 for keys-only sorts with the sub-tiles staged by bulk copies
+__global__ void __launch_bounds__(256, 2) k_scatter1_bulk(const Seg* segs, uint32_t S,
+                                                        const uint32_t* tile_base,
+                                                        uint32_t tile_keys, KeyBufs kb,
+                                                        const uint32_t* __restrict__ cmat,
+                                                        uint32_t* status) {
+  if (pcf_aborted(status)) return;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint32_t t = blockIdx.x;
+  const uint32_t s = upper_bound_dev(tile_base, S + 1, t) - 1;
+  const Seg& g = segs[s];
+  if (g.status != SEG_BUCKET) return;
+  const uint32_t tt = t - tile_base[s];
+  const uint32_t D = 1u << g.b1;
+  const uint32_t seg_base = cmat[g.cbase1];
+  const uint64_t tile_off = g.off + (uint64_t)tt * tile_keys;
+  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, g.off + g.n - tile_off);
+  ScatterSmem sm = carve_scatter(smem_raw, D, false, false);
+  uint8_t* stages = reinterpret_cast<uint8_t*>(sm.skey);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + 2 * (size_t)BulkStage<1>::kBytes);
+  if (threadIdx.x == 0) {
+    mbar_init(bars);
+    mbar_init(bars + 1);
+  }
+  for (uint32_t d = threadIdx.x; d < D; d += 256)
+    sm.gofs[d] = (uint32_t)g.off + (cmat[g.cbase1 + (uint64_t)d * g.tiles1 + tt] - seg_base);
+  __syncthreads();
+  scatter_tile_bulk<1>(sm, stages, bars, D, tile_off, tile_n, kb.jbuf, g.b2, kb.src, kb.tmp,
+                       kb.tmp_aux, status);
+}
+
+// k_scatter2 for keys-only sorts with the sub-tiles staged by bulk copies
+__global__ void __launch_bounds__(256, 2) k_scatter2_bulk(const Group* groups, uint32_t n_groups,
+                                                        const Seg* segs,
+                                                        const uint32_t* g_tile_scan,
+                                                        const uint64_t* total_tiles,
+                                                        uint32_t tile_keys, KeyBufs kb,
+                                                        const uint32_t* __restrict__ cmat2,
+                                                        uint32_t* status) {
+  if (pcf_aborted(status)) return;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint32_t t = blockIdx.x;
+  if (t >= *total_tiles) return;
+  const uint32_t G = upper_bound_dev(g_tile_scan, n_groups, t) - 1;
+  const Group gr = groups[G];
+  if (segs[gr.seg].b2 == 0) return;  // one-digit id: copied, not scattered
+  const uint32_t D = 1u << segs[gr.seg].b2;
+  const uint32_t tt = t - g_tile_scan[G];
+  const uint32_t gbase = cmat2[gr.cbase];
+  const uint64_t tile_off = gr.off + (uint64_t)tt * tile_keys;
+  const uint32_t tile_n = (uint32_t)min((uint64_t)tile_keys, gr.off + gr.n - tile_off);
+  ScatterSmem sm = carve_scatter(smem_raw, D, false, false);
+  uint8_t* stages = reinterpret_cast<uint8_t*>(sm.skey);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + 2 * (size_t)BulkStage<2>::kBytes);
+  if (threadIdx.x == 0) {
+    mbar_init(bars);
+    mbar_init(bars + 1);
+  }
+  for (uint32_t d = threadIdx.x; d < D; d += 256)
+    sm.gofs[d] = (uint32_t)gr.off + (cmat2[gr.cbase + (uint64_t)d * gr.tiles + tt] - gbase);
+  __syncthreads();
+  scatter_tile_bulk<2>(sm, stages, bars, D, tile_off, tile_n, kb.tmp_aux, 0, kb.tmp, kb.out,
+                       nullptr, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -1468,6 +1747,10 @@ cudaError_t launch_scan(const LaunchCfg& c, uint32_t* data, uint64_t n, const ui
   return cudaGetLastError();
 }
 
+// The bulk-staged scatters run where two CTAs still fit an SM's shared
+// memory (228 KB, 1 KB of it reserved per CTA)
+constexpr size_t kBulkSmemMax = 113 * 1024;
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
@@ -1485,6 +1768,12 @@ cudaError_t launch_scatter1(const LaunchCfg& c, const Seg* segs, uint32_t S,
     if ((e = set_smem(k_scatter1<true>, sm))) return e;
     k_scatter1<true><<<n_tiles, 256, sm, c.stream>>>(segs, S, tile_base, tile_keys, kb, tpool, cmat,
                                                       c.status);
+    count_launch(c);
+  } else if (scatter_bulk_smem_bytes(dmax, 1) <= kBulkSmemMax) {
+    const size_t smb = scatter_bulk_smem_bytes(dmax, 1);
+    if ((e = set_smem(k_scatter1_bulk, smb))) return e;
+    k_scatter1_bulk<<<n_tiles, 256, smb, c.stream>>>(segs, S, tile_base, tile_keys, kb, cmat,
+                                                     c.status);
     count_launch(c);
   } else {
     if ((e = set_smem(k_scatter1<false>, sm))) return e;
@@ -1541,6 +1830,12 @@ cudaError_t launch_scatter2(const LaunchCfg& c, const Group* groups, uint32_t n_
     k_scatter2<true><<<n_tiles_bound, 256, sm, c.stream>>>(groups, n_groups, segs, g_tile_scan,
                                                            total_tiles, tile_keys, kb, cmat2,
                                                            c.status);
+    count_launch(c);
+  } else if (scatter_bulk_smem_bytes(dmax, 2) <= kBulkSmemMax) {
+    const size_t smb = scatter_bulk_smem_bytes(dmax, 2);
+    if ((e = set_smem(k_scatter2_bulk, smb))) return e;
+    k_scatter2_bulk<<<n_tiles_bound, 256, smb, c.stream>>>(
+        groups, n_groups, segs, g_tile_scan, total_tiles, tile_keys, kb, cmat2, c.status);
     count_launch(c);
   } else {
     if ((e = set_smem(k_scatter2<false>, sm))) return e;

@@ -1003,27 +1003,28 @@ __global__ void __launch_bounds__(NT, NT <= 64 ? 16 : 512 / NT) k_onchip_cta(con
 // ascending order either way.
 //
 // One CTA of NT threads per bucket of at most NT * KPT keys:
-//   1. the bucket's keys were staged in shared memory (P) by cp.async while
-//      the CTA sorted the previous bucket; each thread takes KPT of them
-//      (order-preserving integers) into registers and the CTA reduces min
-//      and max, then stages the next bucket;
+//   1. the bucket's keys were staged in shared memory (P) by one bulk copy
+//      (the tensor memory accelerator's 1-D form, completing on an mbarrier)
+//      while the CTA sorted the previous bucket; each thread takes KPT of
+//      them into registers as order-preserving integers, and the CTA reduces
+//      min and max (32-bit warp reductions of the high, then the low words),
+//      then stages the next bucket;
 //   2. one equal-width split of [min, max] into M = 2^ceil(log2 n) parts:
 //      part(v) = (v - min) >> shift, shift chosen so that parts < M (an MSD
 //      radix digit of the key's offset from the minimum; no model, no
 //      samples, no division); counts by shared atomics, an exclusive scan
-//      that leaves every part's (start, count) packed in one word, and every
-//      key written to its part's range of B with that word beside it (W);
+//      (each thread a contiguous chunk of parts) that leaves every part's
+//      (start, count) packed in one word, and every key written to its
+//      part's range of B with that word beside it (W);
 //   3. every key's final position: its part's start plus its rank among the
 //      part's keys (smaller, or equal and earlier in B), written straight to
 //      the output (consecutive threads write nearly consecutive positions).
 //      Parts of more than kLeafRank keys (skewed or duplicate-heavy buckets)
 //      are listed and sorted afterwards by one warp each (leaf_big_part).
-// The counts are stored transposed (part d of thread chunk d / r at column
-// d % r, r = M / NT parts per thread), so that the scan's per-thread chunks
-// are read without bank conflicts.
+// The key type is a template parameter, so the order conversions of u64
+// keys vanish.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kLeafRank = 16;
-
 template <uint32_t NT>
 struct LeafShared {
   uint64_t mn[NT / 32], mx[NT / 32];
@@ -1031,23 +1032,51 @@ struct LeafShared {
   uint32_t n_big;
 };
 
-// B [cap] u64 | P [cap] u64 (the next bucket, staged) | W [cap] u32 (each
-// slot's part word) | H [cap << ovs] u32 (part counts, then (start, count)
-// words) | big list.  W and H together are the merge scratch of the large
-// parts.
+// B [cap] u64 | P [cap + 2] u64 (the next bucket, staged; key i at slot
+// i + (offset & 1), so that the bulk copy lands on a 16-byte boundary) |
+// W [cap] u32 (each slot's part word) | H [cap << ovs] u32 (part counts, then
+// (start, count) words) | big list | mbarrier.  W and H together are the
+// merge scratch of the large parts.
 __host__ __device__ inline size_t leaf_sort_smem(uint32_t cap, uint32_t ovs) {
-  return (size_t)cap * 20 + ((size_t)cap << ovs) * 4 + ((size_t)cap / kLeafRank + 1) * 4 + 16;
+  const size_t big = (((size_t)cap / kLeafRank + 1) * 4 + 15) & ~(size_t)15;
+  return (size_t)cap * 20 + 16 + ((size_t)cap << ovs) * 4 + big + 16;
 }
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+// 64-bit warp min / max from two 32-bit reductions (high words, then the
+// low words of the lanes holding the extreme high word)
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+  const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+  const uint32_t h = __reduce_min_sync(~0u, hi);
+  const uint32_t l = __reduce_min_sync(~0u, hi == h ? lo : 0xFFFFFFFFu);
+  return ((uint64_t)h << 32) | l;
 }
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+  const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+  const uint32_t h = __reduce_max_sync(~0u, hi);
+  const uint32_t l = __reduce_max_sync(~0u, hi == h ? lo : 0u);
+  return ((uint64_t)h << 32) | l;
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+
+// Stages bucket (off, n) into P: one thread issues the bulk copy of the
+// 16-byte-aligned middle and arrives on the barrier; the keys at either
+// ragged end (at most one each) are loaded by threads 32 and 33 (or 0 and 1
+// in a one-warp CTA), which runs beside the thread issuing the copy.
+// q: 1 when X itself sits 8 bytes past a 16-byte boundary (keys at index
+// i with i + q even start a 16-byte word)
+template <uint32_t NT>
+__device__ __forceinline__ void leaf_stage(uint64_t* P, uint64_t* bar, const uint64_t* X,
+                                           uint32_t q, uint32_t off, uint32_t n, uint32_t tid) {
+  const uint32_t sh = (off + q) & 1u;
+  const uint32_t a0 = min(off + n, ((off + q + 1u) & ~1u) - q);
+  const uint32_t a1 = max(a0, ((off + n + q) & ~1u) - q);
+  if (tid == 0) {
+    const uint32_t bytes = (a1 - a0) * 8u;
+    mbar_arrive_tx(bar, bytes);
+    if (bytes) bulk_g2s(P + (a0 - off + sh), X + a0, bytes, bar);
+  }
+  constexpr uint32_t kHead = NT > 32 ? 32u : 0u;
+  if (tid == kHead && a0 > off) P[sh] = __ldg(X + off);
+  if (tid == kHead + 1 && a1 < off + n && a1 >= a0) P[a1 - off + sh] = __ldg(X + a1);
 }
 
 // one part of more than kLeafRank keys, B[s, s + c): sorted by one warp
@@ -1081,81 +1110,81 @@ __device__ __noinline__ void leaf_big_part(uint64_t* B, uint64_t* S, uint32_t s,
   __syncwarp();
 }
 
-template <uint32_t NT, uint32_t KPT, uint32_t OVS>
+template <uint32_t NT, uint32_t KPT, uint32_t OVS, uint32_t KT>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
     k_leaf_sort(const uint2* __restrict__ list, const uint32_t* __restrict__ count,
-                const uint64_t* __restrict__ X, uint64_t* out, uint32_t kt, uint32_t* status) {
+                const uint64_t* __restrict__ X, uint64_t* out, uint32_t* status) {
   constexpr uint32_t CAP = NT * KPT, NW = NT / 32;
-  constexpr uint32_t LNT = NT == 32 ? 5 : NT == 64 ? 6 : NT == 128 ? 7 : NT == 256 ? 8
-                         : NT == 512 ? 9 : 10;
-  static_assert((1u << LNT) == NT, "NT must be a power of two, 32..1024");
+  static_assert(NT >= 32 && NT <= 1024 && (NT & (NT - 1)) == 0, "NT a power of two, 32..1024");
   static_assert(KPT >= 1 && (KPT & (KPT - 1)) == 0 && CAP <= 8192, "KPT a power of two");
   if (pcf_aborted(status)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ LeafShared<NT> sh;
   uint64_t* B = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* Pf = B + CAP;
-  uint32_t* Wp = reinterpret_cast<uint32_t*>(Pf + CAP);
+  uint32_t* Wp = reinterpret_cast<uint32_t*>(Pf + CAP + 2);
   uint32_t* H = Wp + CAP;
   uint32_t* big = H + (CAP << OVS);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(
+      smem_raw + (((size_t)CAP * 20 + 16 + ((size_t)CAP << OVS) * 4 +
+                   (((size_t)CAP / kLeafRank + 1) * 4 + 15)) & ~(size_t)15));
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t nitems = *count;
   const uint32_t G = gridDim.x;
   uint32_t li = blockIdx.x;
   if (li >= nitems) return;
+  if (tid == 0) mbar_init(bar);
+  __syncthreads();
   uint2 rec = list[li];
   uint2 rec1 = li + G < nitems ? list[li + G] : make_uint2(0u, 0u);
-#pragma unroll
-  for (uint32_t j = 0; j < KPT; ++j) {
-    const uint32_t i = tid + j * NT;
-    if (i < rec.y) cp_async8(Pf + i, X + rec.x + i);
-  }
-  cp_async_commit();
+  const uint32_t q = (uint32_t)(reinterpret_cast<uintptr_t>(X) >> 3) & 1u;
+  leaf_stage<NT>(Pf, bar, X, q, rec.x, rec.y <= CAP ? rec.y : 0u, tid);
+  uint32_t phase = 0;
   for (; li < nitems; li += G) {
     // a record larger than this class holds is an internal error (flagged,
     // nothing written for it)
     if (rec.y > CAP && tid == 0) atomicOr(status, STATUS_INTERNAL);
-    const uint32_t off = rec.x, n = rec.y <= CAP ? rec.y : 0u;
+    const uint32_t off = rec.x, n = rec.y <= CAP ? rec.y : 0u, shf = (off + q) & 1u;
     const uint2 rec2 = li + 2 * G < nitems ? list[li + 2 * G] : make_uint2(0u, 0u);
     const uint32_t m = (n > 1 ? 32u - __clz(n - 1) : 0u) + OVS;  // M = 2^m >= n parts
     const uint32_t M = 1u << m;
-    const uint32_t lr = m > LNT ? m - LNT : 0u;          // r = 2^lr parts per thread chunk
-    const uint32_t rmask = (1u << lr) - 1u;
-    auto hix = [&](uint32_t d) -> uint32_t { return ((d & rmask) << LNT) | (d >> lr); };
-    cp_async_wait_all();
-    __syncthreads();  // the bucket is staged in P (every thread's copies)
+    // the staged bucket: every thread waits on the barrier (bounded); a wait
+    // that gives up flags the sort and leaves (nothing further is staged)
+    const bool ok = mbar_wait(bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(status, STATUS_TIMEOUT);
+      // give the copy one more bounded wait before the shared memory is left
+      mbar_wait(bar, phase);
+      return;
+    }
+    phase ^= 1u;
     uint64_t k[KPT];
     uint64_t mn = ~0ull, mx = 0ull;
 #pragma unroll
     for (uint32_t j = 0; j < KPT; ++j) {
       const uint32_t i = tid + j * NT;
-      k[j] = i < n ? ord_of(Pf[i], kt) : 0ull;
+      k[j] = ord_of(Pf[(i < n ? i : 0u) + shf], KT);
       if (i < n) {
         mn = k[j] < mn ? k[j] : mn;
         mx = k[j] > mx ? k[j] : mx;
       }
     }
-    for (uint32_t d = tid; d < M; d += NT) H[d] = 0u;
-    if (tid == 0) sh.n_big = 0;
-#pragma unroll
-    for (int d = 16; d; d >>= 1) {
-      const uint64_t a = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mn, d);
-      const uint64_t b = (uint64_t)__shfl_xor_sync(~0u, (unsigned long long)mx, d);
-      mn = a < mn ? a : mn;
-      mx = b > mx ? b : mx;
+    if (M >= 4) {
+      for (uint32_t d = tid * 4; d < M; d += NT * 4)
+        *reinterpret_cast<uint4*>(H + d) = make_uint4(0u, 0u, 0u, 0u);
+    } else if (tid < M) {
+      H[tid] = 0u;
     }
+    if (tid == 0) sh.n_big = 0;
+    mn = warp_min_u64(mn);
+    mx = warp_max_u64(mx);
     if (lane == 0) {
       sh.mn[wid] = mn;
       sh.mx[wid] = mx;
     }
     __syncthreads();  // P is free again; H zeroed
     // stage the next bucket while this one is sorted
-#pragma unroll
-    for (uint32_t j = 0; j < KPT; ++j) {
-      const uint32_t i = tid + j * NT;
-      if (i < rec1.y) cp_async8(Pf + i, X + rec1.x + i);
-    }
-    cp_async_commit();
+    if (li + G < nitems) leaf_stage<NT>(Pf, bar, X, q, rec1.x, rec1.y <= CAP ? rec1.y : 0u, tid);
 #pragma unroll
     for (uint32_t w = 0; w < NW; ++w) {
       mn = sh.mn[w] < mn ? sh.mn[w] : mn;
@@ -1165,7 +1194,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
 #pragma unroll
       for (uint32_t j = 0; j < KPT; ++j) {
         const uint32_t i = tid + j * NT;
-        if (i < n && PCF_IN_KEYS(off + i, status)) out[off + i] = bits_of_ord(k[j], kt);
+        if (i < n && PCF_IN_KEYS(off + i, status)) out[off + i] = bits_of_ord(k[j], KT);
       }
     } else {
       const uint32_t nb = 64u - (uint32_t)__clzll((long long)(mx - mn));
@@ -1174,30 +1203,73 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
 #pragma unroll
       for (uint32_t j = 0; j < KPT; ++j) {
         const uint32_t i = tid + j * NT;
-        hx[j] = hix((uint32_t)((k[j] - mn) >> sft));
+        hx[j] = (uint32_t)((k[j] - mn) >> sft);
         rk[j] = i < n ? atomicAdd(&H[hx[j]], 1u) : 0u;
       }
       __syncthreads();
-      // exclusive scan: thread t owns parts [t r, t r + r), at H[c NT + t];
-      // each entry becomes start | count << 16 (both at most 8192)
+      // exclusive scan: thread t owns parts [t r, t r + r), r = M / NT (or
+      // one part for t < M when M < NT); each entry becomes
+      // start | count << 16 (both at most 8192)
       {
-        const uint32_t rr = 1u << lr;
-        const bool own = tid * rr < M;
+        const uint32_t r = M >= NT ? M / NT : 1u;
+        const bool own = tid * r < M;
+        uint32_t v[(KPT > 4 ? KPT : 4) << OVS];
         uint32_t sum = 0;
-        if (own)
-          for (uint32_t c = 0; c < rr; ++c) sum += H[(c << LNT) | tid];
-        const uint32_t inc = wscan(sum, lane);
+        if (r >= 4) {
+#pragma unroll
+          for (uint32_t c = 0; c < (KPT << OVS); c += 4) {
+            if (c < r) {
+              const uint4 h = *reinterpret_cast<const uint4*>(H + tid * r + c);
+              v[c] = h.x;
+              v[c + 1] = h.y;
+              v[c + 2] = h.z;
+              v[c + 3] = h.w;
+              sum += h.x + h.y + h.z + h.w;
+            }
+          }
+        } else {
+#pragma unroll
+          for (uint32_t c = 0; c < 4; ++c) {
+            v[c] = (own && c < r) ? H[tid * r + c] : 0u;
+            sum += v[c];
+          }
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t u = __shfl_up_sync(~0u, inc, d);
+          if (lane >= (uint32_t)d) inc += u;
+        }
         if (lane == 31) sh.wsum[wid] = inc;
         __syncthreads();
         uint32_t run = inc - sum;
 #pragma unroll
         for (uint32_t w = 0; w < NW; ++w) run += w < wid ? sh.wsum[w] : 0u;
-        if (own)
-          for (uint32_t c = 0; c < rr; ++c) {
-            const uint32_t v = H[(c << LNT) | tid];
-            H[(c << LNT) | tid] = run | (v << 16);
-            run += v;
+        if (r >= 4) {
+#pragma unroll
+          for (uint32_t c = 0; c < (KPT << OVS); c += 4) {
+            if (c < r) {
+              uint4 h;
+              h.x = run | (v[c] << 16);
+              run += v[c];
+              h.y = run | (v[c + 1] << 16);
+              run += v[c + 1];
+              h.z = run | (v[c + 2] << 16);
+              run += v[c + 2];
+              h.w = run | (v[c + 3] << 16);
+              run += v[c + 3];
+              *reinterpret_cast<uint4*>(H + tid * r + c) = h;
+            }
           }
+        } else if (own) {
+#pragma unroll
+          for (uint32_t c = 0; c < 4; ++c) {
+            if (c < r) {
+              H[tid * r + c] = run | (v[c] << 16);
+              run += v[c];
+            }
+          }
+        }
       }
       __syncthreads();
 #pragma unroll
@@ -1213,30 +1285,46 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
         }
       }
       __syncthreads();
-#pragma unroll
+      const uint32_t ml = (uint32_t)mn;
+#pragma unroll 2
       for (uint32_t j = 0; j < KPT; ++j) {
         const uint32_t p = tid + j * NT;
-        if (p < n) {
-          const uint64_t v = B[p];
-          const uint32_t sc = Wp[p];
-          const uint32_t s = sc & 0xFFFFu, c = sc >> 16;
-          uint32_t pos = p;
-          if (c > kLeafRank) {
-            if (p == s) big[atomicAdd(&sh.n_big, 1u)] = sc;
-            continue;
-          }
-          if (c > 1)
-            pos = s + (sft <= 32 ? rank_in_lo32(B, s, s + c, p, (uint32_t)v - (uint32_t)mn,
-                                                (uint32_t)mn)
-                                 : rank_in(B, s, s + c, p, v));
-          if (PCF_IN_KEYS(off + pos, status)) out[off + pos] = bits_of_ord(v, kt);
+        if (p >= n) break;
+        const uint64_t v = B[p];
+        const uint32_t sc = Wp[p];
+        const uint32_t s = sc & 0xFFFFu, c = sc >> 16;
+        uint32_t pos = p;
+        if (c > kLeafRank) {
+          if (p == s) big[atomicAdd(&sh.n_big, 1u)] = sc;
+          continue;
         }
+        if (c > 1) {
+          // rank among the part's keys (smaller, or equal and earlier)
+          uint32_t r = 0;
+          if (sft <= 32) {
+            const uint32_t* K32 = reinterpret_cast<const uint32_t*>(B);
+            const uint32_t vl = (uint32_t)v - ml;
+#pragma unroll 1
+            for (uint32_t t = s; t < s + c; ++t) {
+              const uint32_t ul = K32[2 * t] - ml;
+              r += (ul < vl || (ul == vl && t < p)) ? 1u : 0u;
+            }
+          } else {
+#pragma unroll 1
+            for (uint32_t t = s; t < s + c; ++t) {
+              const uint64_t u = B[t];
+              r += (u < v || (u == v && t < p)) ? 1u : 0u;
+            }
+          }
+          pos = s + r;
+        }
+        if (PCF_IN_KEYS(off + pos, status)) out[off + pos] = bits_of_ord(v, KT);
       }
       __syncthreads();
       const uint32_t nbig = sh.n_big;
       for (uint32_t b = wid; b < nbig; b += NW)
         leaf_big_part(B, reinterpret_cast<uint64_t*>(Wp), big[b] & 0xFFFFu, big[b] >> 16, out,
-                      off, kt, lane, status);
+                      off, KT, lane, status);
     }
     __syncthreads();  // B, H, W and the list are reused by the next bucket
     rec = rec1;
@@ -1328,26 +1416,33 @@ static cudaError_t launch_warp_model(const LaunchCfg& c, const BRec* br, const u
 
 // the block-local sort of one size class: NT threads, KPT keys each, parts
 // 2^(ceil(log2 n) + OVS)
-template <uint32_t NT, uint32_t KPT, uint32_t OVS = 0u>
-static cudaError_t launch_leaf_sort(const LaunchCfg& c, const uint2* list, const uint32_t* count,
-                                    const uint64_t* X, uint64_t* out) {
+template <uint32_t NT, uint32_t KPT, uint32_t OVS, uint32_t KT>
+static cudaError_t launch_leaf_sort_kt(const LaunchCfg& c, const uint2* list,
+                                       const uint32_t* count, const uint64_t* X, uint64_t* out) {
   const size_t smem = leaf_sort_smem(NT * KPT, OVS);
-  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT, OVS>);
+  cudaError_t e = allow_max_smem((const void*)k_leaf_sort<NT, KPT, OVS, KT>);
   if (e) return e;
   static int per_sm_cache[64] = {0};
   int dev = 0;
   if ((e = cudaGetDevice(&dev))) return e;
   int per_sm = dev >= 0 && dev < 64 ? per_sm_cache[dev] : 0;
   if (per_sm <= 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT, OVS>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leaf_sort<NT, KPT, OVS, KT>,
                                                       (int)NT, smem);
     if (e) return e;
     per_sm = per_sm > 0 ? per_sm : 1;
     if (dev >= 0 && dev < 64) per_sm_cache[dev] = per_sm;
   }
-  k_leaf_sort<NT, KPT, OVS><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT,
-                              smem, c.stream>>>(list, count, X, out, c.kt, c.status);
+  k_leaf_sort<NT, KPT, OVS, KT><<<(uint32_t)num_sms_of_current_device() * (uint32_t)per_sm, NT,
+                                  smem, c.stream>>>(list, count, X, out, c.status);
   return cudaGetLastError();
+}
+
+template <uint32_t NT, uint32_t KPT, uint32_t OVS = 0u>
+static cudaError_t launch_leaf_sort(const LaunchCfg& c, const uint2* list, const uint32_t* count,
+                                    const uint64_t* X, uint64_t* out) {
+  return c.kt == KEY_U64 ? launch_leaf_sort_kt<NT, KPT, OVS, KEY_U64>(c, list, count, X, out)
+                         : launch_leaf_sort_kt<NT, KPT, OVS, KEY_F64>(c, list, count, X, out);
 }
 
 uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs) {
