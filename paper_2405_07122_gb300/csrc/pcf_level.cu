@@ -1112,6 +1112,7 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
 }
 
 constexpr uint32_t kTiny = 16;  // buckets this small are sorted by one thread
+constexpr uint32_t kRunBucket = 64;  // runs of 32 leaf buckets this small sort as one
 constexpr uint32_t kStdLeafMax = 1024;
 
 template <bool PAIRS>
@@ -1187,10 +1188,26 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
       atomicAdd(&pcf_counters(status)->guard_keys, (unsigned long long)gk);
     }
   }
+  // A run of small leaf buckets (block-local leaf sort only): when this
+  // warp's 32 buckets belong to one bucketed (sub)array and each of them is
+  // a leaf of at most kRunBucket keys, they are listed as one leaf record of
+  // their total size.  Buckets are ordered (every key of bucket j precedes
+  // every key of bucket j + 1, Sec. 3.2), so the run sorted as one piece is
+  // the buckets sorted one after another.
+  bool run = false;
+  uint32_t run_n = 0;
+  if (leaf_lists) {
+    const uint32_t s0 = __shfl_sync(~0u, s, 0);
+    const bool small = in && s == s0 && segs[s].status == SEG_BUCKET && size <= kRunBucket &&
+                       size <= leaf_cap &&
+                       !(size >= segs[s].delta && size > min(leaf_cap, kStdLeafMax));
+    run_n = __reduce_add_sync(~0u, in ? size : 0u);
+    run = __all_sync(~0u, small) && run_n <= leaf_cap;
+  }
   // Standard-Sort (|c| >= delta, or |c| < tau inside the recursive call) of a
   // tiny bucket: insertion sort by this thread, X -> out
   const bool std_sort = v && (size >= sg->delta || size < tau);
-  if (std_sort && size <= kTiny) {
+  if (std_sort && size <= kTiny && !run) {
     const uint32_t t = threadIdx.x;
     for (uint32_t i = 0; i < size; ++i) {
       const uint64_t key = X[off + i];
@@ -1221,7 +1238,7 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     BRec r;
     r.off = (uint32_t)off;
     r.n = size;
-    r.kind = is_leaf ? (BK_LEAF | (std_sort ? BK_STD : 0u)) : 0u;
+    r.kind = is_leaf && !run ? (BK_LEAF | (std_sort ? BK_STD : 0u)) : 0u;
     r.depth = sg ? sg->depth + 1 : 0u;
     r.start = sg ? sg->start + (off - sg->off) : 0ull;
     r.seed = sg ? sg->seed : 0ull;
@@ -1230,9 +1247,14 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
   if (in) next_flag[B] = is_next ? 1u : 0u;
   const uint32_t i_leaf = warp_append(&lo->n_leaf, is_leaf);
   (void)i_leaf;
-  // the block-local sort's class lists, (offset, size) per leaf bucket
+  // the block-local sort's class lists, (offset, size) per leaf bucket, or
+  // one record per run (lane 0: the run's first offset and its size)
   if (leaf_lists) {
-    const uint32_t cls = is_leaf ? min(leaf_size_class(size), leaf_classes - 1) : kMaxLeafClasses;
+    const bool lane0 = (threadIdx.x & 31) == 0;
+    const uint32_t ln = run ? run_n : size;
+    const uint32_t cls = (run ? lane0 && run_n > 0 : is_leaf)
+                             ? min(leaf_size_class(ln), leaf_classes - 1)
+                             : kMaxLeafClasses;
 #pragma unroll
     for (uint32_t k = 0; k < kMaxLeafClasses; ++k) {
       const uint32_t bal = __ballot_sync(~0u, cls == k);
@@ -1243,7 +1265,7 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
       base = __shfl_sync(~0u, base, leader);
       if (cls == k)
         leaf_lists[(size_t)k * n_buckets + base + __popc(bal & lanemask_lt())] =
-            make_uint2((uint32_t)off, size);
+            make_uint2((uint32_t)off, ln);
     }
   }
   const uint32_t i_next = warp_append(&lo->n_next, is_next);
