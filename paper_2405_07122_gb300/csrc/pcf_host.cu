@@ -117,6 +117,7 @@ struct pcf_ctx {
   DevBuf leaf, next, fb, lout, status, misc, fb_items, fb_bases, fb_lohi, small_items;
   DevBuf segs_b, pcols, pbsums;  // the other level's plan, its count columns
   DevBuf olist;                  // on-chip buckets listed by size class
+  DevBuf mid;                    // k_mid's work list and its leaf records
   DevBuf jbuf;                   // bucket id of every key of a level
   DevBuf small_segs;             // range records of the on-chip arrays (level 0)
   DevBuf fb_cnt;                 // per-tile part counts of the three-way splits
@@ -729,7 +730,8 @@ uint64_t buffers_signature(const pcf_ctx* c) {
                         c->groups.p, c->gtiles.p, c->gcent.p, c->gtot.p, c->leaf.p, c->next.p,
                         c->fb.p, c->lout.p, c->status.p, c->misc.p, c->fb_items.p,
                         c->fb_bases.p, c->fb_lohi.p, c->small_items.p, c->segs_b.p, c->pcols.p,
-                        c->pbsums.p, c->olist.p, c->jbuf.p, c->small_segs.p, c->fb_cnt.p,
+                        c->pbsums.p, c->olist.p, c->mid.p, c->jbuf.p, c->small_segs.p,
+                        c->fb_cnt.p,
                         c->bcounts.p, c->bmax.p, c->ptab.p, c->pipe_keys.p, c->h_stage.p,
                         c->h_lout.p, c->h_status.p, c->h_items.p, c->h_stage_small.p, c->h_fb.p,
                         c->h_offs.p};
@@ -750,7 +752,7 @@ uint64_t workspace_held(const pcf_ctx* c) {
                           &c->tpool, &c->done, &c->cmat1, &c->cmat2, &c->sw, &c->groups,
                           &c->gtiles, &c->gcent, &c->gtot, &c->leaf, &c->next, &c->fb, &c->lout,
                           &c->status, &c->misc, &c->fb_items, &c->fb_bases, &c->fb_lohi,
-                          &c->small_items, &c->segs_b, &c->pcols, &c->pbsums, &c->olist,
+                          &c->small_items, &c->segs_b, &c->pcols, &c->pbsums, &c->olist, &c->mid,
                           &c->jbuf, &c->small_segs, &c->fb_cnt, &c->bcounts, &c->bmax, &c->ptab,
                           &c->pipe_keys};
   uint64_t b = 0;
@@ -774,6 +776,14 @@ uint64_t workspace_bound(const Policy& P, const pcf_tuning& tu, uint64_t n, uint
   const bool leaf_sort = !pairs && tu.leaf_mode == 1;
   const uint64_t olist_per = 8ull * (leaf_sort ? leaf_sort_classes(cap) : onchip_classes(cap));
   auto grow = [](uint64_t b) { return b + b / 4; };
+  // k_mid's work list and leaf records (counted with the class lists)
+  const bool mid = leaf_sort && P.model == MODEL_PCF && P.range_mode == RANGE_ARRAY;
+  auto mid_bytes = [&](uint64_t n_level) -> uint64_t {
+    if (!mid) return 0;
+    uint64_t at = ((n_level / ((uint64_t)cap + 1) + 1) * 4 + 15) / 16 * 2;
+    for (uint32_t q = 0; q < kMaxLeafClasses; ++q) at += mid_class_cap(q, n_level, cap);
+    return at * 8;
+  };
   enum { LEAF, NEXT, FB, TPOOL, SW, CMAT1, GROUPS, GTILES, GCENT, CMAT2, OLIST, PLAN, PLAN2,
          PCOLS, PBSUMS, NNEED };
   uint64_t need[NNEED] = {0};
@@ -796,7 +806,7 @@ uint64_t workspace_bound(const Policy& P, const pcf_tuning& tu, uint64_t n, uint
         max_items * sizeof(BRec), max_items * 4, max_items * sizeof(FbItem), pl.tpool * 4,
         ((scan_max + kScanTile - 1) / kScanTile + (pl.n_groups + kScanTile - 1) / kScanTile + 8) * 8,
         pl.cmat1 * 4, pl.n_groups * sizeof(Group), pl.n_groups * 4, pl.n_groups * 4,
-        pl.cmat2_bound * 4, pl.n_buckets * olist_per, plan_layout(rows).bytes,
+        pl.cmat2_bound * 4, pl.n_buckets * olist_per + mid_bytes(n_level), plan_layout(rows).bytes,
         plan_layout(s_max).bytes, (uint64_t)PC_NCOL * s_max * 4,
         (uint64_t)PC_NCOL * ((s_max + 2047) / 2048) * 4};
     for (int i = 0; i < NNEED; ++i) need[i] = std::max(need[i], v[i]);
@@ -860,6 +870,8 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
   lc.model = ctx->policy.model;
   lc.range_mode = ctx->policy.range_mode;
   lc.leaf_sort = !pairs && ctx->tuning.leaf_mode == 1;
+  const bool use_mid = lc.leaf_sort && ctx->policy.model == MODEL_PCF &&
+                       ctx->policy.range_mode == RANGE_ARRAY;
   CK(ensure(ctx->status, 64));
   lc.status = as<uint32_t>(ctx->status);
   CK(cudaMemsetAsync(lc.status, 0, 64, st));
@@ -1150,15 +1162,44 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     uint32_t* next_flag = as<uint32_t>(ctx->next);
     uint32_t* leaf_counts = (uint32_t*)((char*)ctx->misc.p + 128);
     CK(ensure(ctx->olist, (size_t)L.n_buckets * olist_per_bucket));
-    if (lc.leaf_sort) CK(cudaMemsetAsync(leaf_counts, 0, 4 * kMaxLeafClasses, st));
+    // mid-size next-level buckets: one Learned-Sort call per CTA (k_mid),
+    // keys-only block-local sorts under the default policy
+    const bool mid = use_mid;
+    uint32_t* mid_counts = (uint32_t*)((char*)ctx->misc.p + 160);  // per class
+    uint32_t* mid_count = (uint32_t*)((char*)ctx->misc.p + 192);
+    MidLists ml{};
+    uint32_t* mid_list = nullptr;
+    uint2* mid_lists = nullptr;
+    if (mid) {
+      const uint64_t n_mid_max = n_level / ((uint64_t)cap + 1) + 1;
+      uint64_t at = (n_mid_max * 4 + 15) / 16 * 2;  // u64 units after the work list
+      for (uint32_t q = 0; q < kMaxLeafClasses; ++q) {
+        ml.cap[q] = mid_class_cap(q, n_level, cap);
+        ml.base[q] = at;
+        at += ml.cap[q];
+      }
+      CK(ensure(ctx->mid, at * 8));
+      mid_list = as<uint32_t>(ctx->mid);
+      mid_lists = (uint2*)ctx->mid.p;
+    }
+    if (lc.leaf_sort) CK(cudaMemsetAsync(leaf_counts, 0, mid ? 68 : 4 * kMaxLeafClasses, st));
     CK(launch_buckets(lc, d_segs, S, L.n_buckets, L.dp.bb, as<Group>(ctx->groups),
                       as<uint32_t>(ctx->cmat1), as<uint32_t>(ctx->cmat2), L.two_pass, cap,
                       (uint32_t)ctx->policy.tau, X, Xv, out_k, out_v, as<BRec>(ctx->leaf),
                       next_flag, as<FbItem>(ctx->fb), d_lo, (uint32_t)max_items,
                       lc.leaf_sort ? as<uint2>(ctx->olist) : nullptr,
-                      lc.leaf_sort ? leaf_counts : nullptr, leaf_sort_classes(cap)));
+                      lc.leaf_sort ? leaf_counts : nullptr, leaf_sort_classes(cap), mid_list,
+                      mid_count));
     CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k, out_v,
                      ctx->policy, ptab, as<uint32_t>(ctx->olist), leaf_counts, lc.leaf_sort));
+    if (mid) {
+      // the mid (sub)arrays' buckets land in Y (free at their offsets)
+      uint64_t* Y = (X == tmp_k) ? out_k : tmp_k;
+      CK(launch_mid(lc, mid_list, mid_count, as<BRec>(ctx->leaf), X, Y, out_k, next_flag,
+                    mid_lists, ml, mid_counts, leaf_sort_classes(cap), cap, ctx->policy, d_lo));
+      CK(launch_onchip(lc, nullptr, 1u, cap, Y, nullptr, out_k, nullptr, ctx->policy, ptab,
+                       (uint32_t*)mid_lists, mid_counts, true, ml.base));
+    }
     tm.mark(6);
     // the next level's plan, built on the device into the other buffer; a
     // next-level (sub)array holds more than cap keys, which bounds its rows
@@ -1229,6 +1270,9 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
     // keys finished on chip (or copied as one value) this level: read and
     // written once
     ctx->stats.bytes_moved += (n_level - lo.plan.n_keys - level_fb_keys) * (pairs ? 24 : 16);
+    // keys bucketed by k_mid: read for the range, the bins and the append,
+    // written once (their leaf sort is counted above)
+    ctx->stats.bytes_moved += lo.mid_keys * 32;
     // the next level
     const PlanTotals& pt = lo.plan;
     LevelPlan N;

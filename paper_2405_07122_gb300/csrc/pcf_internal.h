@@ -145,6 +145,7 @@ struct LevelOut {
   uint64_t leaf_keys, next_keys, fb_keys;
   uint32_t max_fb_n;  // largest standard-sort bucket (sizes the merge passes)
   uint32_t leaf_cursor; // work counter of the leaf kernel
+  uint64_t mid_keys;  // keys finished by k_mid (their own Learned-Sort call on chip)
   PlanTotals plan;    // the next level's plan (device-built)
 };
 
@@ -347,7 +348,8 @@ cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint
                            uint64_t* out_k, uint32_t* out_v, BRec* brec, uint32_t* next_flag,
                            FbItem* fb, LevelOut* lo, uint32_t max_items,
                            uint2* leaf_lists = nullptr, uint32_t* leaf_counts = nullptr,
-                           uint32_t leaf_classes = 0);
+                           uint32_t leaf_classes = 0, uint32_t* mid_list = nullptr,
+                           uint32_t* mid_count = nullptr);
 // builds the next level's plan from the flagged buckets (next_flag[B] = 1
 // for a bucket of the next level; scanned in place), s_max rows at most;
 // n_flagged receives the number of (sub)arrays
@@ -379,6 +381,27 @@ OnchipGeo onchip_geometry(uint32_t capw, const Policy& P, bool pairs);
 // 8192 keys; onchip_classes(cap) of them are used below leaf_cap = cap.
 constexpr uint32_t kMaxClasses = 6;
 uint32_t onchip_classes(uint32_t leaf_cap);
+// A failure-guard bucket (|c| >= delta) is finished on chip only up to this
+// many keys (one warp runs its Standard-Sort); larger ones go to the
+// fallback, where the whole device sorts them.
+constexpr uint32_t kStdLeafMax = 1024;
+// Runs of 32 adjacent leaf buckets of at most this many keys each are
+// listed as one leaf record (buckets are ordered, so the run sorted as one
+// piece is the buckets sorted one after another).
+constexpr uint32_t kRunBucket = 64;
+// Mid-size (sub)arrays (leaf_cap, kMidCap]: one Learned-Sort call per CTA
+// (k_mid) instead of a further global level; kMidTab bounds beta + 1 and
+// gamma + 1 (kMidCap^(3/4) + 1 under the paper's policy).
+constexpr uint32_t kMidCap = 32768;
+constexpr uint32_t kMidTab = 2056;
+// upper bound on the leaf records k_mid lists for a level of n_level keys:
+// per class (q >= 1: records of more than 2^(q+5) keys; q = 0: at most one
+// record per bucket of the mid (sub)arrays, each more than leaf_cap keys)
+inline uint64_t mid_class_cap(uint32_t q, uint64_t n_level, uint32_t leaf_cap) {
+  if (q > 0) return (n_level >> (q + 5)) + 1;
+  const uint64_t g = (n_level / ((uint64_t)leaf_cap + 1) + 1) * kMidTab;
+  return (g < n_level ? g : n_level) + 1;
+}
 // The block-local sort's classes (0, 64], (64, 128], (128, 256], (256, 512],
 // ... up to leaf_cap: leaf_sort_classes(cap) of them, at most kMaxLeafClasses.
 constexpr uint32_t kMaxLeafClasses = 8;
@@ -386,6 +409,21 @@ uint32_t leaf_sort_classes(uint32_t leaf_cap);
 __device__ __forceinline__ uint32_t leaf_size_class(uint32_t n) {
   return n <= 64 ? 0u : (uint32_t)(32 - __clz((int)(n - 1))) - 6u;
 }
+// Mid-size buckets mid_list[0 .. *mid_count) (bucket indices into brec,
+// keys in X): each one Learned-Sort call by one CTA; its buckets appended
+// in Y and listed for the block-local sort (lists: class q at
+// class_base[q], counts[q]); next_flag[B] = 1 where the call leaves the
+// bucket to the next global level.  The default policy only (PCF model,
+// array range).
+struct MidLists {
+  uint64_t base[kMaxLeafClasses];
+  uint64_t cap[kMaxLeafClasses];
+};
+cudaError_t launch_mid(const LaunchCfg& c, const uint32_t* mid_list, const uint32_t* mid_count,
+                       const BRec* brec, const uint64_t* X, uint64_t* Y, uint64_t* out,
+                       uint32_t* next_flag, uint2* lists, const MidLists& ml,
+                       uint32_t* list_counts, uint32_t leaf_classes, uint32_t leaf_cap,
+                       const Policy& P, LevelOut* lo);
 // The largest bucket finished on chip: leaf_cap (key-value sorts at most
 // 1024), halved until the policy's slice fits one block's shared memory.
 uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs);
@@ -394,10 +432,12 @@ uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs);
 // for the block-local sort); counts: kMaxLeafClasses u32
 // prelisted: the block-local sort's class lists and counts were already
 // written (by k_buckets), so they are not built from the records again
+// class_base: the block-local sort's class lists at these record offsets
+// (prelisted lists only; nullptr: class q at q * nb)
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts,
-                          bool prelisted = false);
+                          bool prelisted = false, const uint64_t* class_base = nullptr);
 cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                             const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
                             uint64_t* ord_lohi);

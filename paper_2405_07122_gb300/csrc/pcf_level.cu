@@ -1112,8 +1112,6 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
 }
 
 constexpr uint32_t kTiny = 16;  // buckets this small are sorted by one thread
-constexpr uint32_t kRunBucket = 64;  // runs of 32 leaf buckets this small sort as one
-constexpr uint32_t kStdLeafMax = 1024;
 
 template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, uint64_t n_buckets,
@@ -1126,7 +1124,8 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
                                                  uint32_t* out_v, BRec* brec, uint32_t* next_flag,
                                                  FbItem* fb, LevelOut* lo, uint32_t max_items,
                                                  uint2* leaf_lists, uint32_t* leaf_counts,
-                                                 uint32_t leaf_classes, uint32_t* status) {
+                                                 uint32_t leaf_classes, uint32_t* mid_list,
+                                                 uint32_t* mid_count, uint32_t* status) {
   if (pcf_aborted(status)) return;
   // [kTiny][256] (transposed: thread t owns column t, so accesses are
   // conflict-free)
@@ -1244,7 +1243,14 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     r.seed = sg ? sg->seed : 0ull;
     brec[B] = r;
   }
-  if (in) next_flag[B] = is_next ? 1u : 0u;
+  // a next-level bucket of at most kMidCap keys goes to k_mid first (its
+  // flag stays clear unless k_mid leaves it to the next level)
+  const bool is_mid = is_next && mid_list && size <= kMidCap;
+  if (in) next_flag[B] = is_next && !is_mid ? 1u : 0u;
+  if (mid_list) {
+    const uint32_t i_mid = warp_append(mid_count, is_mid);
+    if (is_mid) mid_list[i_mid] = (uint32_t)B;
+  }
   const uint32_t i_leaf = warp_append(&lo->n_leaf, is_leaf);
   (void)i_leaf;
   // the block-local sort's class lists, (offset, size) per leaf bucket, or
@@ -1874,18 +1880,18 @@ cudaError_t launch_buckets(const LaunchCfg& c, const Seg* segs, uint32_t S, uint
                            const uint64_t* X, const uint32_t* Xv, uint64_t* out_k, uint32_t* out_v,
                            BRec* brec, uint32_t* next_flag, FbItem* fb, LevelOut* lo,
                            uint32_t max_items, uint2* leaf_lists, uint32_t* leaf_counts,
-                           uint32_t leaf_classes) {
+                           uint32_t leaf_classes, uint32_t* mid_list, uint32_t* mid_count) {
   if (!n_buckets) return cudaSuccess;
   if (c.pairs)
     k_buckets<true><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
         segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
         c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, nullptr, nullptr, 0,
-        c.status);
+        nullptr, nullptr, c.status);
   else
     k_buckets<false><<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(
         segs, S, n_buckets, bucket_base, groups, cmat1, cmat2, two_pass ? 1 : 0, leaf_cap, tau,
         c.kt, X, Xv, out_k, out_v, brec, next_flag, fb, lo, max_items, leaf_lists, leaf_counts,
-        leaf_classes, c.status);
+        leaf_classes, leaf_lists ? mid_list : nullptr, mid_count, c.status);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -1332,6 +1332,230 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mid-size (sub)arrays: one Learned-Sort call (Alg. 1, PCF model of Sec.
+// 3.3) on a bucket of leaf_cap < n <= kMidCap keys, by one CTA, in place of
+// a further global level.  The CTA takes the bucket's range (x_min, x_max),
+// builds the model, draws its alpha samples (R2, keyed like every other
+// call) and the table T[k] = floor(b_k gamma / alpha), computes every key's
+// bucket, counts the buckets and decides them as Alg. 1 does.  When every
+// new bucket finishes on chip (at most leaf_cap keys, and not a
+// failure-guard bucket for the standard sort) it appends each key to its
+// bucket in Y (the level's other key buffer, free at these offsets) and
+// lists the new buckets for the block-local leaf sort, runs of 32 small
+// ones as one record as k_buckets does.  Otherwise it leaves the bucket to
+// the next global level (its next-level flag set, nothing written), so
+// every decision stays Alg. 1's.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kMidThreads = 512;
+
+struct MidShared {
+  BinModel bm;
+  uint64_t mn[kMidThreads / 32], mx[kMidThreads / 32];
+  uint32_t wsum[kMidThreads / 32];
+  uint32_t flag;
+};
+
+// T [kMidTab] u32 (bin counts, then the bucket table) | C [kMidTab] u32
+// (bucket sizes, then starts, then cursors) | J [kMidCap] u16 (the bucket of
+// every key)
+__host__ __device__ constexpr size_t mid_smem_bytes() {
+  return (size_t)kMidTab * 4 * 2 + (size_t)kMidCap * 2;
+}
+
+// exclusive (EXCL) or inclusive scan of a[0..m) in place by the CTA; each
+// thread a contiguous run; returns the total
+template <bool EXCL>
+__device__ __forceinline__ uint32_t mid_scan(uint32_t* a, uint32_t m, MidShared& sh) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t per = (m + kMidThreads - 1) / kMidThreads;
+  const uint32_t i0 = min(m, tid * per), i1 = min(m, i0 + per);
+  uint32_t sum = 0;
+  for (uint32_t i = i0; i < i1; ++i) sum += a[i];
+  uint32_t inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t u = __shfl_up_sync(~0u, inc, d);
+    if (lane >= (uint32_t)d) inc += u;
+  }
+  if (lane == 31) sh.wsum[wid] = inc;
+  __syncthreads();
+  uint32_t run = inc - sum, tot = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < kMidThreads / 32; ++w) {
+    const uint32_t x = sh.wsum[w];
+    run += w < wid ? x : 0u;
+    tot += x;
+  }
+  for (uint32_t i = i0; i < i1; ++i) {
+    const uint32_t v = a[i];
+    run += v;
+    a[i] = EXCL ? run - v : run;
+  }
+  __syncthreads();
+  return tot;
+}
+
+template <uint32_t KT>
+__global__ void __launch_bounds__(kMidThreads, 2)
+    k_mid(const uint32_t* __restrict__ mid_list, const uint32_t* __restrict__ mid_count,
+          const BRec* __restrict__ brec, const uint64_t* __restrict__ X, uint64_t* Y,
+          uint64_t* out, uint32_t* next_flag, uint2* lists, MidLists ml,
+          uint32_t* list_counts, uint32_t leaf_classes, uint32_t leaf_cap, Policy P,
+          LevelOut* lo, uint32_t* status) {
+  if (pcf_aborted(status)) return;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ MidShared sh;
+  uint32_t* T = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* C = T + kMidTab;
+  uint16_t* J = reinterpret_cast<uint16_t*>(C + kMidTab);
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr uint32_t NW = kMidThreads / 32;
+  const uint32_t nitems = *mid_count;
+  for (uint32_t li = blockIdx.x; li < nitems; li += gridDim.x) {
+    const uint32_t B = mid_list[li];
+    const BRec r = brec[B];
+    const uint32_t n = r.n, off = r.off;
+    const Params pr = params_of(P, n);
+    // range
+    uint64_t mn = ~0ull, mx = 0ull;
+    for (uint32_t i = tid; i < n; i += kMidThreads) {
+      const uint64_t v = ord_of(__ldg(X + off + i), KT);
+      mn = v < mn ? v : mn;
+      mx = v > mx ? v : mx;
+    }
+    mn = warp_min_u64(mn);
+    mx = warp_max_u64(mx);
+    if (lane == 0) {
+      sh.mn[wid] = mn;
+      sh.mx[wid] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (uint32_t w = 1; w < NW; ++w) {
+        mn = sh.mn[w] < mn ? sh.mn[w] : mn;
+        mx = sh.mx[w] > mx ? sh.mx[w] : mx;
+      }
+      // one value: already sorted (1); a degenerate range or tables larger
+      // than this kernel holds: the next global level decides (2)
+      uint32_t f = 0;
+      if (n > kMidCap || pr.beta + 1 > kMidTab || pr.gamma + 1 > kMidTab) f = 2;
+      else if (mn == mx) f = 1;
+      else if (make_bin_model(KT, bits_of_ord(mn, KT), bits_of_ord(mx, KT), pr.beta, &sh.bm))
+        f = 2;
+      sh.flag = f;
+    }
+    for (uint32_t k = tid; k <= pr.beta && k < kMidTab; k += kMidThreads) T[k] = 0u;
+    for (uint32_t k = tid; k <= pr.gamma && k < kMidTab; k += kMidThreads) C[k] = 0u;
+    __syncthreads();
+    const uint32_t f = sh.flag;
+    if (f == 1) {
+      for (uint32_t i = tid; i < n; i += kMidThreads)
+        if (PCF_IN_KEYS(off + i, status)) out[off + i] = __ldg(X + off + i);
+      __syncthreads();
+      continue;
+    }
+    if (f == 2) {
+      if (tid == 0) next_flag[B] = 1u;
+      __syncthreads();
+      continue;
+    }
+    // samples (R2) counted per bin, then b_k and the bucket table
+    const BinModel& bm = sh.bm;
+    {
+      const uint64_t st = sample_state(r.seed, r.depth, r.start, n);
+      for (uint32_t j = tid; j < pr.alpha; j += kMidThreads) {
+        const uint64_t idx = sample_index(st, j, n);
+        atomicAdd(&T[bin_of(bm, __ldg(X + off + idx))], 1u);
+      }
+    }
+    __syncthreads();
+    mid_scan<false>(T, pr.beta + 1, sh);
+    for (uint32_t k = tid; k <= pr.beta; k += kMidThreads)
+      T[k] = bucket_of_count(T[k], pr.alpha, pr.gamma);
+    __syncthreads();
+    // every key's bucket, and the bucket sizes
+    for (uint32_t i = tid; i < n; i += kMidThreads) {
+      const uint32_t j = T[bin_of(bm, __ldg(X + off + i))];
+      J[i] = (uint16_t)j;
+      atomicAdd(&C[j], 1u);
+    }
+    __syncthreads();
+    // Alg. 1's decision for every bucket: all must finish on chip
+    bool bad = false;
+    for (uint32_t k = tid; k <= pr.gamma; k += kMidThreads) {
+      const uint32_t c = C[k];
+      bad |= c > leaf_cap || (c >= pr.delta && c > min(leaf_cap, kStdLeafMax));
+    }
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) next_flag[B] = 1u;
+      continue;
+    }
+    // decided here: the call's record (a bucketing, its failure-guard
+    // buckets), the buckets' leaf records (runs of 32 small ones as one)
+    {
+      uint32_t gb = 0, gk = 0;
+      for (uint32_t k = tid; k <= pr.gamma; k += kMidThreads) {
+        const uint32_t c = C[k];
+        if (c >= pr.delta && c > 0) {
+          ++gb;
+          gk += c;
+        }
+      }
+      gb = __reduce_add_sync(~0u, gb);
+      gk = __reduce_add_sync(~0u, gk);
+      if (lane == 0 && gb) {
+        atomicAdd(&pcf_counters(status)->guard_buckets, (unsigned long long)gb);
+        atomicAdd(&pcf_counters(status)->guard_keys, (unsigned long long)gk);
+      }
+      if (tid == 0) {
+        atomicAdd(&pcf_counters(status)->bucketings, 1ull);
+        atomicAdd((unsigned long long*)&lo->mid_keys, (unsigned long long)n);
+      }
+    }
+    // sizes -> starts (kept in T's place: the table is no longer needed)
+    for (uint32_t k = tid; k <= pr.gamma; k += kMidThreads) T[k] = C[k];
+    __syncthreads();
+    mid_scan<true>(T, pr.gamma + 1, sh);
+    // leaf records: warp w takes buckets [32 q, 32 q + 32) for q = w, w + NW, ...
+    for (uint32_t b0 = wid * 32; b0 <= pr.gamma; b0 += NW * 32) {
+      const uint32_t k = b0 + lane;
+      const bool in = k <= pr.gamma;
+      const uint32_t c = in ? C[k] : 0u, s = in ? T[k] : 0u;
+      const uint32_t run_n = __reduce_add_sync(~0u, c);
+      const bool run = __all_sync(~0u, !in || c <= kRunBucket) && run_n <= leaf_cap;
+      const bool lane0 = lane == 0;
+      const uint32_t ln = run ? run_n : c;
+      const uint32_t ls = run ? __shfl_sync(~0u, s, 0) : s;
+      const uint32_t cls = (run ? lane0 && run_n > 0 : c > 0)
+                               ? min(leaf_size_class(ln), leaf_classes - 1)
+                               : kMaxLeafClasses;
+#pragma unroll
+      for (uint32_t q = 0; q < kMaxLeafClasses; ++q) {
+        const uint32_t bal = __ballot_sync(~0u, cls == q);
+        if (!bal) continue;
+        const int leader = __ffs(bal) - 1;
+        uint32_t base = 0;
+        if ((int)lane == leader) base = atomicAdd(&list_counts[q], (uint32_t)__popc(bal));
+        base = __shfl_sync(~0u, base, leader);
+        const uint32_t at = base + __popc(bal & ((1u << lane) - 1u));
+        if (cls == q) {
+          if (at < ml.cap[q]) lists[ml.base[q] + at] = make_uint2(off + ls, ln);
+          else atomicOr(status, STATUS_INTERNAL);
+        }
+      }
+    }
+    // the keys appended to their buckets in Y (C as cursors from the starts)
+    for (uint32_t k = tid; k <= pr.gamma; k += kMidThreads) C[k] = T[k];
+    __syncthreads();
+    for (uint32_t i = tid; i < n; i += kMidThreads) {
+      const uint32_t p = atomicAdd(&C[J[i]], 1u);
+      if (PCF_IN(p, n, status) && PCF_IN_KEYS(off + p, status)) Y[off + p] = __ldg(X + off + i);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace onchip
 
 using namespace onchip;
@@ -1458,10 +1682,40 @@ uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs) {
   return cap;
 }
 
+template <uint32_t KT>
+static cudaError_t launch_mid_kt(const LaunchCfg& c, const uint32_t* mid_list,
+                                 const uint32_t* mid_count, const BRec* brec, const uint64_t* X,
+                                 uint64_t* Y, uint64_t* out, uint32_t* next_flag, uint2* lists,
+                                 const MidLists& ml, uint32_t* list_counts, uint32_t leaf_classes,
+                                 uint32_t leaf_cap, const Policy& P, LevelOut* lo) {
+  constexpr size_t smem = mid_smem_bytes();
+  cudaError_t e = allow_max_smem((const void*)k_mid<KT>);
+  if (e) return e;
+  k_mid<KT><<<(uint32_t)num_sms_of_current_device() * 2u, kMidThreads, smem, c.stream>>>(
+      mid_list, mid_count, brec, X, Y, out, next_flag, lists, ml, list_counts, leaf_classes,
+      leaf_cap, P, lo, c.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mid(const LaunchCfg& c, const uint32_t* mid_list, const uint32_t* mid_count,
+                       const BRec* brec, const uint64_t* X, uint64_t* Y, uint64_t* out,
+                       uint32_t* next_flag, uint2* lists, const MidLists& ml,
+                       uint32_t* list_counts, uint32_t leaf_classes, uint32_t leaf_cap,
+                       const Policy& P, LevelOut* lo) {
+  cudaError_t e =
+      c.kt == KEY_U64
+          ? launch_mid_kt<KEY_U64>(c, mid_list, mid_count, brec, X, Y, out, next_flag, lists, ml,
+                                   list_counts, leaf_classes, leaf_cap, P, lo)
+          : launch_mid_kt<KEY_F64>(c, mid_list, mid_count, brec, X, Y, out, next_flag, lists, ml,
+                                   list_counts, leaf_classes, leaf_cap, P, lo);
+  count_launch(c);
+  return e;
+}
+
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts,
-                          bool prelisted) {
+                          bool prelisted, const uint64_t* class_base) {
   if (!nb) return cudaSuccess;
   // size classes (0, 256], (256, 512], (512, 1024], ... clipped to leaf_cap
   const bool recs = c.leaf_sort && !c.pairs;
@@ -1479,7 +1733,8 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
     // the whole bucket by the block-local Standard-Sort: a warp for up to
     // 256 keys (2, 4 or 8 per lane), then NT = capw / 8 threads
     for (uint32_t cls = 0, capw = 64; cls < ncls; ++cls, capw *= 2) {
-      const uint2* rl = reinterpret_cast<const uint2*>(lists) + (size_t)cls * nb;
+      const uint2* rl = reinterpret_cast<const uint2*>(lists) +
+                        (class_base ? class_base[cls] : (size_t)cls * nb);
       const uint32_t* cnt = counts + cls;
       switch (capw) {
         case 64: e = launch_leaf_sort<32, 2>(c, rl, cnt, X, out); break;

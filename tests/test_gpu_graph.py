@@ -108,9 +108,13 @@ def test_new_data_other_plan_sorts_again(P):
     n = 2**22
     offs = _offsets([n])
     xu = W.f64_keys("uniform", n, 3)
-    xl = W.f64_keys("lognormal", n, 4)
-    # precondition: LogNormal keys take a second global level (its densest
-    # level-0 buckets exceed 2048 keys), Uniform none
+    # a dense cluster of 50000 distinct keys inside one level-0 bin: a bucket
+    # larger than one CTA's Learned-Sort call takes (kMidCap = 32768 keys),
+    # below delta (92,681), so it takes a second global level
+    xl = W.f64_keys("uniform", n, 4)
+    rng = np.random.default_rng(4)
+    xl[rng.choice(n, 50000, replace=False)] = 0.5 + rng.random(50000) * 1e-9
+    # precondition: these keys take a second global level, Uniform none
     ctx = P.Context(0, tuning=dict(leaf_cap=2048))
     tmp = torch.empty_like(_dev(xl))
     ctx.sort_keys(_dev(xl), tmp, key_type="f64")
