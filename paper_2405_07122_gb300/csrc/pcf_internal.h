@@ -141,8 +141,8 @@ struct LevelOut {
   uint32_t n_leaf;
   uint32_t n_next;
   uint32_t n_fb;
-  uint32_t pad;
-  uint64_t leaf_keys, next_keys, fb_keys;
+  uint32_t n_flag;    // buckets flagged for the next global level
+  uint64_t flag_n;    // length of the flag scan: the buckets when any is flagged, else 0
   uint32_t max_fb_n;  // largest standard-sort bucket (sizes the merge passes)
   uint32_t leaf_cursor; // work counter of the leaf kernel
   uint64_t mid_keys;  // keys finished by k_mid (their own Learned-Sort call on chip)
@@ -382,9 +382,14 @@ OnchipGeo onchip_geometry(uint32_t capw, const Policy& P, bool pairs);
 constexpr uint32_t kMaxClasses = 6;
 uint32_t onchip_classes(uint32_t leaf_cap);
 // A failure-guard bucket (|c| >= delta) is finished on chip only up to this
-// many keys (one warp runs its Standard-Sort); larger ones go to the
-// fallback, where the whole device sorts them.
+// many keys when one warp runs its Standard-Sort (the Learned-Sort steps on
+// chip); larger ones go to the fallback, where the whole device sorts them.
+// The block-local leaf sort takes failure-guard buckets up to leaf_cap
+// (Standard-Sort is any sort, Sec. 3.1).
 constexpr uint32_t kStdLeafMax = 1024;
+__host__ __device__ inline uint32_t guard_leaf_max(uint32_t leaf_cap, bool block_local) {
+  return block_local ? leaf_cap : (leaf_cap < kStdLeafMax ? leaf_cap : kStdLeafMax);
+}
 // Runs of 32 adjacent leaf buckets of at most this many keys each are
 // listed as one leaf record (buckets are ordered, so the run sorted as one
 // piece is the buckets sorted one after another).

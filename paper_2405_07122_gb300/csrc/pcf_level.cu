@@ -1199,7 +1199,7 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     const uint32_t s0 = __shfl_sync(~0u, s, 0);
     const bool small = in && s == s0 && segs[s].status == SEG_BUCKET && size <= kRunBucket &&
                        size <= leaf_cap &&
-                       !(size >= segs[s].delta && size > min(leaf_cap, kStdLeafMax));
+                       !(size >= segs[s].delta && size > guard_leaf_max(leaf_cap, true));
     run_n = __reduce_add_sync(~0u, in ? size : 0u);
     run = __all_sync(~0u, small) && run_n <= leaf_cap;
   }
@@ -1228,9 +1228,11 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     }
     v = false;
   }
-  // a failure-guard bucket is sorted on chip only up to kStdLeafMax keys
-  // (there one warp runs the Standard-Sort); larger ones go to the fallback
-  const bool is_fb = v && size >= sg->delta && size > min(leaf_cap, kStdLeafMax);
+  // a failure-guard bucket is sorted on chip only up to guard_leaf_max keys
+  // (leaf_cap for the block-local sort, else kStdLeafMax: one warp runs the
+  // Standard-Sort); larger ones go to the fallback
+  const bool is_fb =
+      v && size >= sg->delta && size > guard_leaf_max(leaf_cap, leaf_lists != nullptr);
   const bool is_leaf = v && !is_fb && size <= leaf_cap;
   const bool is_next = v && !is_fb && !is_leaf;
   if (in) {
@@ -1251,6 +1253,7 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
     const uint32_t i_mid = warp_append(mid_count, is_mid);
     if (is_mid) mid_list[i_mid] = (uint32_t)B;
   }
+  warp_append(&lo->n_flag, is_next && !is_mid);
   const uint32_t i_leaf = warp_append(&lo->n_leaf, is_leaf);
   (void)i_leaf;
   // the block-local sort's class lists, (offset, size) per leaf bucket, or
@@ -1298,13 +1301,20 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t bits_of_dev(uint32_t v) { return v ? 32u - __clz(v) : 0u; }
 
+__global__ void k_plan_gate(LevelOut* lo, uint64_t n_buckets, uint64_t* n_flagged,
+                            const uint32_t* gate) {
+  if (pcf_aborted(gate)) return;
+  lo->flag_n = lo->n_flag ? n_buckets : 0ull;
+  *n_flagged = 0ull;
+}
+
 __global__ void k_next_segs(const BRec* __restrict__ brec, const uint32_t* __restrict__ pos,
                             const uint64_t* __restrict__ n_flagged, uint64_t n_buckets, Policy P,
                             uint32_t dbits, uint32_t tile_keys, Seg* nsegs, uint32_t* cols,
                             uint32_t s_max, LevelOut* lo, uint32_t* status) {
   if (pcf_aborted(status)) return;
   const uint64_t B = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (B >= n_buckets) return;
+  if (B >= n_buckets || *n_flagged == 0) return;
   const uint32_t s = pos[B];
   const uint32_t s_end = B + 1 < n_buckets ? pos[B + 1] : (uint32_t)*n_flagged;
   if (s_end == s) return;
@@ -1921,8 +1931,12 @@ cudaError_t launch_plan_next(const LaunchCfg& c, const BRec* brec, uint32_t* nex
                              uint32_t* block_sums, LevelOut* lo, uint64_t* sw,
                              uint32_t* tile_counter, uint64_t spin_limit, uint64_t* n_flagged) {
   if (!n_buckets) return cudaSuccess;
-  cudaError_t e = launch_scan(c, next_flag, n_buckets, nullptr, sw, tile_counter, 0xFFFFFFFFu,
-                              spin_limit, n_flagged);
+  // no bucket flagged (every one finished this level): the flag scan takes
+  // no tiles and the next level's plan stays empty
+  k_plan_gate<<<1, 1, 0, c.stream>>>(lo, n_buckets, n_flagged, c.status);
+  count_launch(c);
+  cudaError_t e = launch_scan(c, next_flag, n_buckets, &lo->flag_n, sw, tile_counter,
+                              0xFFFFFFFFu, spin_limit, n_flagged);
   if (e) return e;
   k_next_segs<<<cdiv(n_buckets, 256), 256, 0, c.stream>>>(brec, next_flag, n_flagged, n_buckets,
                                                           P, dbits, tile_keys, out.segs, cols,

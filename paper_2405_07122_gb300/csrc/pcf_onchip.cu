@@ -1456,7 +1456,10 @@ __global__ void __launch_bounds__(kMidThreads, 2)
       continue;
     }
     if (f == 2) {
-      if (tid == 0) next_flag[B] = 1u;
+      if (tid == 0) {
+        next_flag[B] = 1u;
+        atomicAdd(&lo->n_flag, 1u);
+      }
       __syncthreads();
       continue;
     }
@@ -1485,10 +1488,13 @@ __global__ void __launch_bounds__(kMidThreads, 2)
     bool bad = false;
     for (uint32_t k = tid; k <= pr.gamma; k += kMidThreads) {
       const uint32_t c = C[k];
-      bad |= c > leaf_cap || (c >= pr.delta && c > min(leaf_cap, kStdLeafMax));
+      bad |= c > leaf_cap || (c >= pr.delta && c > guard_leaf_max(leaf_cap, true));
     }
     if (__syncthreads_or(bad)) {
-      if (tid == 0) next_flag[B] = 1u;
+      if (tid == 0) {
+        next_flag[B] = 1u;
+        atomicAdd(&lo->n_flag, 1u);
+      }
       continue;
     }
     // decided here: the call's record (a bucketing, its failure-guard
