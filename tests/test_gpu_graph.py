@@ -104,6 +104,33 @@ def test_new_data_same_plan_replays(P, ctx):
     g.close()
 
 
+def test_new_data_mixed_batch_replays(P):
+    # arrays of five distributions whose densest buckets exceed leaf_cap
+    # (2048 here, as the autotuner picks for the batched workload): their
+    # Learned-Sort calls run in k_mid within the level, so the plan (one
+    # global level, no standard-sort item) depends on the lengths only, and
+    # fresh keys of the same lengths replay
+    lens = [5000, 2**17, 70001, 2**18 + 3, 9000, 2**16, 300000, 2**12]
+    offs = _offsets(lens)
+    x0 = _mixed(3, lens)
+    ctx = P.Context(0, tuning=dict(leaf_cap=2048))
+    tmp = torch.empty(int(offs[-1]), dtype=torch.float64, device="cuda")
+    ctx.sort_segmented(_dev(x0), offs, keys_out=tmp, key_type="f64")
+    assert ctx.last_stats()["levels"] == 1 and ctx.last_stats()["fallback_keys"] == 0
+    t = _dev(x0)
+    o = torch.empty_like(t)
+    g = P.SortGraph(ctx, t, offs, o, key_type="f64", seed=1)
+    for rep in range(3):
+        x = _mixed(40 + rep, lens)
+        t.copy_(_dev(x))
+        o.zero_()
+        assert g.launch() is True
+        torch.cuda.synchronize()
+        _check(o, x, offs, 1)
+    g.close()
+    ctx.close()
+
+
 def test_new_data_other_plan_sorts_again(P):
     n = 2**22
     offs = _offsets([n])
