@@ -1235,7 +1235,9 @@ __global__ void __launch_bounds__(256) k_buckets(const Seg* segs, uint32_t S, ui
       v && size >= sg->delta && size > guard_leaf_max(leaf_cap, leaf_lists != nullptr);
   const bool is_leaf = v && !is_fb && size <= leaf_cap;
   const bool is_next = v && !is_fb && !is_leaf;
-  if (in) {
+  // the records are read for next-level buckets (the planner, k_mid) and,
+  // without the block-local sort's lists, for the on-chip kernels' lists
+  if (in && (is_next || !leaf_lists)) {
     BRec r;
     r.off = (uint32_t)off;
     r.n = size;
