@@ -1339,9 +1339,10 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 1024 / NT)
 // builds the model, draws its alpha samples (R2, keyed like every other
 // call) and the table T[k] = floor(b_k gamma / alpha), computes every key's
 // bucket, counts the buckets and decides them as Alg. 1 does.  When every
-// new bucket finishes on chip (at most leaf_cap keys, and not a
-// failure-guard bucket for the standard sort) it appends each key to its
-// bucket in Y (the level's other key buffer, free at these offsets) and
+// new bucket finishes on chip (at most leaf_cap keys: the block-local leaf
+// sort, which also serves as the Standard-Sort of a failure-guard bucket)
+// it appends each key to its bucket in Y (the level's other key buffer,
+// free at these offsets) and
 // lists the new buckets for the block-local leaf sort, runs of 32 small
 // ones as one record as k_buckets does.  Otherwise it leaves the bucket to
 // the next global level (its next-level flag set, nothing written), so
