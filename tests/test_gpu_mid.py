@@ -132,3 +132,20 @@ def test_mid_u64_keys(P):
     ref, _ = oracle.sort(x, seed=5)
     assert np.array_equal(got, ref)
     ctx.close()
+
+
+@pytest.mark.parametrize("start", [1, 3])
+def test_mid_calls_with_buffers_at_8_byte_offsets(P, start):
+    # input and output 8 bytes past a 16-byte boundary: the mid calls read
+    # one buffer and append into the other, and their buckets are staged for
+    # the leaf sort from a buffer at either alignment
+    x = W.f64_keys("lognormal", (1 << 21) + 5, 16 + start)
+    t = _dev(x)
+    src = t[start:]
+    out = torch.empty(src.numel() + 1, dtype=torch.float64, device="cuda")[1:]
+    ctx = P.Context(0, tuning=dict(leaf_cap=2048))
+    ctx.sort_keys(src, out, key_type="f64", seed=2)
+    torch.cuda.synchronize()
+    ref, _ = oracle.sort(x[start:], seed=2)
+    assert np.array_equal(_bits(out.cpu().numpy()), _bits(ref))
+    ctx.close()
