@@ -1420,6 +1420,7 @@ __global__ void __launch_bounds__(kMidThreads, 2)
     const Params pr = params_of(P, n);
     // range
     uint64_t mn = ~0ull, mx = 0ull;
+#pragma unroll 4
     for (uint32_t i = tid; i < n; i += kMidThreads) {
       const uint64_t v = ord_of(__ldg(X + off + i), KT);
       mn = v < mn ? v : mn;
@@ -1478,11 +1479,37 @@ __global__ void __launch_bounds__(kMidThreads, 2)
     for (uint32_t k = tid; k <= pr.beta; k += kMidThreads)
       T[k] = bucket_of_count(T[k], pr.alpha, pr.gamma);
     __syncthreads();
-    // every key's bucket, and the bucket sizes
-    for (uint32_t i = tid; i < n; i += kMidThreads) {
-      const uint32_t j = T[bin_of(bm, __ldg(X + off + i))];
-      J[i] = (uint16_t)j;
-      atomicAdd(&C[j], 1u);
+    // every key's bucket, and the bucket sizes: four keys per thread and
+    // step, the fast bins first and the exact sequence only for the keys
+    // they leave undecided (as k_hist1 does)
+    for (uint32_t i0 = tid; i0 < n; i0 += 4 * kMidThreads) {
+      uint64_t x[4];
+      uint32_t bn[4], amb = 0;
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t i = i0 + u * kMidThreads;
+        x[u] = i < n ? __ldg(X + off + i) : bm.lo_bits;
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        bool a;
+        bn[u] = bin_fast(bm, x[u], a);
+        amb |= (uint32_t)a << u;
+      }
+      if (amb) {
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u)
+          if ((amb >> u) & 1u) bn[u] = bin_exact_of(bm, x[u]);
+      }
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t i = i0 + u * kMidThreads;
+        if (i < n) {
+          const uint32_t j = T[bn[u]];
+          J[i] = (uint16_t)j;
+          atomicAdd(&C[j], 1u);
+        }
+      }
     }
     __syncthreads();
     // Alg. 1's decision for every bucket: all must finish on chip
@@ -1555,6 +1582,7 @@ __global__ void __launch_bounds__(kMidThreads, 2)
     // the keys appended to their buckets in Y (C as cursors from the starts)
     for (uint32_t k = tid; k <= pr.gamma; k += kMidThreads) C[k] = T[k];
     __syncthreads();
+#pragma unroll 4
     for (uint32_t i = tid; i < n; i += kMidThreads) {
       const uint32_t p = atomicAdd(&C[J[i]], 1u);
       if (PCF_IN(p, n, status) && PCF_IN_KEYS(off + p, status)) Y[off + p] = __ldg(X + off + i);
