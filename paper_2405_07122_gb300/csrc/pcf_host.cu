@@ -44,6 +44,30 @@ struct HostBuf {  // pinned staging
   }
 };
 
+// A side stream that runs beside the caller's within one level (the mid-size
+// Learned-Sort calls and their leaf sort, beside the level's own leaf sort:
+// disjoint keys), forked and joined by events (created on first use, on the
+// context's device; a capture takes the side stream into the graph).
+struct SideStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool ready = false;
+  cudaError_t init() {
+    if (ready) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    ready = !e;
+    return e;
+  }
+  ~SideStream() {
+    if (!ready) return;
+    cudaStreamDestroy(st);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+  }
+};
+
 // Copy streams and events of the pipelined host-buffer entry point (created
 // on first use, on the context's device).
 constexpr int kPipeSlots = 3;
@@ -132,6 +156,7 @@ struct pcf_ctx {
   ParamCache pcache;
   DevBuf pipe_keys;  // kPipeSlots arrays of the pipelined host entry point
   CopyPipe pipe;
+  SideStream side;   // the mid calls beside the level's leaf sort
 };
 
 cudaError_t pcf::allow_max_smem(const void* kernel) {
@@ -850,6 +875,14 @@ void take_counters(pcf_ctx* ctx) {
 // arrays; keys flow src -> tmp (pass 1) -> out (pass 2); leaf buckets are
 // finished in place in out; fallback buckets are merge-sorted in out.
 // mode / rec / rp: see SortRecord and Replay.
+// Waits for every piece of a sort still in flight: the caller's stream and
+// the side stream (a call that failed between the fork and the join leaves
+// work on both).
+void drain(pcf_ctx* ctx, cudaStream_t st) {
+  cudaStreamSynchronize(st);
+  if (ctx->side.ready) cudaStreamSynchronize(ctx->side.st);
+}
+
 pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, uint64_t* out_k,
                     uint32_t* out_v, const std::vector<InSeg>& user, uint32_t kt, bool pairs,
                     cudaStream_t st, uint32_t scan_withhold = 0xFFFFFFFFu,
@@ -1190,15 +1223,30 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                       lc.leaf_sort ? as<uint2>(ctx->olist) : nullptr,
                       lc.leaf_sort ? leaf_counts : nullptr, leaf_sort_classes(cap), mid_list,
                       mid_count));
-    CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k, out_v,
-                     ctx->policy, ptab, as<uint32_t>(ctx->olist), leaf_counts, lc.leaf_sort));
     if (mid) {
-      // the mid (sub)arrays' buckets land in Y (free at their offsets)
+      // the mid (sub)arrays' buckets land in Y (free at their offsets); the
+      // mid calls and their leaf sort run on the side stream beside the
+      // level's leaf sort (they touch other keys), joined before the
+      // next level's planning reads their flags
       uint64_t* Y = (X == tmp_k) ? out_k : tmp_k;
-      CK(launch_mid(lc, mid_list, mid_count, as<BRec>(ctx->leaf), X, Y, out_k, next_flag,
+      CK(ctx->side.init());
+      LaunchCfg ls = lc;
+      ls.stream = ctx->side.st;
+      CK(cudaEventRecord(ctx->side.fork, st));
+      CK(cudaStreamWaitEvent(ls.stream, ctx->side.fork, 0));
+      CK(launch_mid(ls, mid_list, mid_count, as<BRec>(ctx->leaf), X, Y, out_k, next_flag,
                     mid_lists, ml, mid_counts, leaf_sort_classes(cap), cap, ctx->policy, d_lo));
-      CK(launch_onchip(lc, nullptr, 1u, cap, Y, nullptr, out_k, nullptr, ctx->policy, ptab,
+      CK(launch_onchip(ls, nullptr, 1u, cap, Y, nullptr, out_k, nullptr, ctx->policy, ptab,
                        (uint32_t*)mid_lists, mid_counts, true, ml.base));
+      CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k,
+                       out_v, ctx->policy, ptab, as<uint32_t>(ctx->olist), leaf_counts,
+                       lc.leaf_sort));
+      CK(cudaEventRecord(ctx->side.join, ls.stream));
+      CK(cudaStreamWaitEvent(st, ctx->side.join, 0));
+    } else {
+      CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k,
+                       out_v, ctx->policy, ptab, as<uint32_t>(ctx->olist), leaf_counts,
+                       lc.leaf_sort));
     }
     tm.mark(6);
     // the next level's plan, built on the device into the other buffer; a
@@ -1389,7 +1437,7 @@ pcf_status graph_build(pcf_graph* g, cudaStream_t st) {
   pcf_status r = run_sort(ctx, g->in_k, g->in_v, g->out_k, g->out_v, g->segs, g->kt, g->pairs, st,
                           0xFFFFFFFFu, kSpinLimit, RUN_RECORD, &nrec);
   if (r != PCF_OK) {
-    cudaStreamSynchronize(st);
+    drain(ctx, st);
     return r;
   }
   ++g->eager_runs;
@@ -1613,7 +1661,7 @@ static pcf_status sort_common(pcf_ctx* ctx, const void* kin, const uint32_t* vin
   const pcf_status r = run_sort(ctx, (const uint64_t*)kin, vin, (uint64_t*)kout, vout, segs,
                                (uint32_t)kt, pairs, (cudaStream_t)stream);
   // a call that fails part-way returns with none of its work in flight
-  if (r != PCF_OK) cudaStreamSynchronize((cudaStream_t)stream);
+  if (r != PCF_OK) drain(ctx, (cudaStream_t)stream);
   ctx->last_status = r;
   return r;
 }
