@@ -44,27 +44,31 @@ struct HostBuf {  // pinned staging
   }
 };
 
-// A side stream that runs beside the caller's within one level (the mid-size
-// Learned-Sort calls and their leaf sort, beside the level's own leaf sort:
-// disjoint keys), forked and joined by events (created on first use, on the
-// context's device; a capture takes the side stream into the graph).
+// Side streams that run beside the caller's within one level (the mid-size
+// Learned-Sort calls and their leaf sort; the level's leaf classes above 512
+// keys), all on disjoint keys, forked and joined by events (created on first
+// use, on the context's device; a capture takes them into the graph).
 struct SideStream {
-  cudaStream_t st = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t st = nullptr, st2 = nullptr;  // the mid calls; the larger leaf classes
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
   bool ready = false;
   cudaError_t init() {
     if (ready) return cudaSuccess;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
     if (!e) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     if (!e) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&join2, cudaEventDisableTiming);
     ready = !e;
     return e;
   }
   ~SideStream() {
     if (!ready) return;
     cudaStreamDestroy(st);
+    cudaStreamDestroy(st2);
     cudaEventDestroy(fork);
     cudaEventDestroy(join);
+    cudaEventDestroy(join2);
   }
 };
 
@@ -880,7 +884,10 @@ void take_counters(pcf_ctx* ctx) {
 // work on both).
 void drain(pcf_ctx* ctx, cudaStream_t st) {
   cudaStreamSynchronize(st);
-  if (ctx->side.ready) cudaStreamSynchronize(ctx->side.st);
+  if (ctx->side.ready) {
+    cudaStreamSynchronize(ctx->side.st);
+    cudaStreamSynchronize(ctx->side.st2);
+  }
 }
 
 pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, uint64_t* out_k,
@@ -1238,11 +1245,18 @@ pcf_status run_sort(pcf_ctx* ctx, const uint64_t* in_k, const uint32_t* in_v, ui
                     mid_lists, ml, mid_counts, leaf_sort_classes(cap), cap, ctx->policy, d_lo));
       CK(launch_onchip(ls, nullptr, 1u, cap, Y, nullptr, out_k, nullptr, ctx->policy, ptab,
                        (uint32_t*)mid_lists, mid_counts, true, ml.base));
+      // the level's classes above 512 keys on a second side stream, so that
+      // the classes' launches overlap one another's tails
+      CK(cudaStreamWaitEvent(ctx->side.st2, ctx->side.fork, 0));
+      cudaStream_t cls_st[kMaxLeafClasses];
+      for (uint32_t q = 0; q < kMaxLeafClasses; ++q) cls_st[q] = q < 4 ? st : ctx->side.st2;
       CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k,
                        out_v, ctx->policy, ptab, as<uint32_t>(ctx->olist), leaf_counts,
-                       lc.leaf_sort));
+                       lc.leaf_sort, nullptr, cls_st));
       CK(cudaEventRecord(ctx->side.join, ls.stream));
+      CK(cudaEventRecord(ctx->side.join2, ctx->side.st2));
       CK(cudaStreamWaitEvent(st, ctx->side.join, 0));
+      CK(cudaStreamWaitEvent(st, ctx->side.join2, 0));
     } else {
       CK(launch_onchip(lc, as<BRec>(ctx->leaf), (uint32_t)L.n_buckets, cap, X, Xv, out_k,
                        out_v, ctx->policy, ptab, as<uint32_t>(ctx->olist), leaf_counts,

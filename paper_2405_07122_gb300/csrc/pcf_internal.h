@@ -438,11 +438,13 @@ uint32_t onchip_cap(uint32_t leaf_cap, const Policy& P, bool pairs);
 // prelisted: the block-local sort's class lists and counts were already
 // written (by k_buckets), so they are not built from the records again
 // class_base: the block-local sort's class lists at these record offsets
-// (prelisted lists only; nullptr: class q at q * nb)
+// (prelisted lists only; nullptr: class q at q * nb); class_stream: the
+// stream of each class's launch (block-local sort; nullptr: c.stream)
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts,
-                          bool prelisted = false, const uint64_t* class_base = nullptr);
+                          bool prelisted = false, const uint64_t* class_base = nullptr,
+                          const cudaStream_t* class_stream = nullptr);
 cudaError_t launch_fb_range(const LaunchCfg& c, const FbItem* items, uint32_t n_items,
                             const uint32_t* tile_base, uint32_t n_tiles, const uint64_t* keys,
                             uint64_t* ord_lohi);

@@ -1750,7 +1750,8 @@ cudaError_t launch_mid(const LaunchCfg& c, const uint32_t* mid_list, const uint3
 cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint32_t leaf_cap,
                           const uint64_t* X, const uint32_t* Xv, uint64_t* out, uint32_t* out_v,
                           Policy P, const uint16_t* ptab, uint32_t* lists, uint32_t* counts,
-                          bool prelisted, const uint64_t* class_base) {
+                          bool prelisted, const uint64_t* class_base,
+                          const cudaStream_t* class_stream) {
   if (!nb) return cudaSuccess;
   // size classes (0, 256], (256, 512], (512, 1024], ... clipped to leaf_cap
   const bool recs = c.leaf_sort && !c.pairs;
@@ -1771,15 +1772,17 @@ cudaError_t launch_onchip(const LaunchCfg& c, const BRec* br, uint32_t nb, uint3
       const uint2* rl = reinterpret_cast<const uint2*>(lists) +
                         (class_base ? class_base[cls] : (size_t)cls * nb);
       const uint32_t* cnt = counts + cls;
+      LaunchCfg cc = c;
+      if (class_stream) cc.stream = class_stream[cls];
       switch (capw) {
-        case 64: e = launch_leaf_sort<32, 2>(c, rl, cnt, X, out); break;
-        case 128: e = launch_leaf_sort<32, 4>(c, rl, cnt, X, out); break;
-        case 256: e = launch_leaf_sort<32, 8>(c, rl, cnt, X, out); break;
-        case 512: e = launch_leaf_sort<64, 8>(c, rl, cnt, X, out); break;
-        case 1024: e = launch_leaf_sort<128, 8>(c, rl, cnt, X, out); break;
-        case 2048: e = launch_leaf_sort<256, 8>(c, rl, cnt, X, out); break;
-        case 4096: e = launch_leaf_sort<512, 8>(c, rl, cnt, X, out); break;
-        default: e = launch_leaf_sort<1024, 8>(c, rl, cnt, X, out); break;
+        case 64: e = launch_leaf_sort<32, 2>(cc, rl, cnt, X, out); break;
+        case 128: e = launch_leaf_sort<32, 4>(cc, rl, cnt, X, out); break;
+        case 256: e = launch_leaf_sort<32, 8>(cc, rl, cnt, X, out); break;
+        case 512: e = launch_leaf_sort<64, 8>(cc, rl, cnt, X, out); break;
+        case 1024: e = launch_leaf_sort<128, 8>(cc, rl, cnt, X, out); break;
+        case 2048: e = launch_leaf_sort<256, 8>(cc, rl, cnt, X, out); break;
+        case 4096: e = launch_leaf_sort<512, 8>(cc, rl, cnt, X, out); break;
+        default: e = launch_leaf_sort<1024, 8>(cc, rl, cnt, X, out); break;
       }
       if (e) return e;
       count_launch(c);
