@@ -3,9 +3,14 @@
 Workload (one step): sort four arrays of n = 10^8 float64 keys, one per
 distribution (Normal(0,1), LogNormal(0,1), Exponential(1), a 5-Gaussian
 mixture), keys only, through pcf_sort_keys (pristine device input ->
-device output; inputs are 800 MB each, larger than the 129 MB L2).
+device output; inputs are 800 MB each, larger than the 129 MB L2).  The
+four independent sorts are issued by --sort-threads host threads (default
+4, one per array), each with its own context and stream, so one
+array's on-chip finish (instruction-bound) overlaps another's global
+passes (memory-bound); every sort is the whole algorithm on its array.
 
   value        sorted Gkeys/s over the K timed steps (device-resident inputs)
+  sequential   the same steps from one thread on one stream, for comparison
   e2e          the same through pcf_sort_keys_host_batch: the step's four
                arrays from pinned host buffers -> device -> sort -> host,
                every copy inside the timed region (the library overlaps
@@ -29,6 +34,7 @@ import os
 import subprocess
 import sys
 import threading
+from concurrent.futures import ThreadPoolExecutor
 import time
 
 import numpy as np
@@ -218,6 +224,9 @@ def main():
                     help="plain: the default 4 x 10^8 f64 line; the others are the "
                          "secondary configurations")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--sort-threads", type=int, default=4, choices=[1, 2, 4],
+                    help="plain workload: host threads issuing the step's four sorts, "
+                         "one context and stream each (1: one thread, one stream)")
     ap.add_argument("--leaf-mode", type=int, default=0, choices=[0, 1, 2],
                     help="on-chip finish of keys-only sorts: 1 block-local sort, 2 Learned-Sort "
                          "steps in shared memory, 0 the library default (1)")
@@ -248,32 +257,83 @@ def main():
     host_keys = [W.f64_keys(d, n, seed) for d, seed in DISTS]
     ins = [torch.from_numpy(x).to(dev) for x in host_keys]
     outs = [torch.empty_like(t) for t in ins]
-    ctx = pcfsort.Context(local)
-    if args.model != "pcf" or args.range != "array":
-        ctx.set_policy(model=args.model, range_mode=args.range)
-    if args.leaf_mode:
-        ctx.set_tuning(leaf_mode=args.leaf_mode)
-    ctx.reserve(n)
-    # the sorts' own stream (created non-blocking by torch): on the legacy
+    T = args.sort_threads
+    ctxs = [pcfsort.Context(local) for _ in range(T)]
+    for c in ctxs:
+        if args.model != "pcf" or args.range != "array":
+            c.set_policy(model=args.model, range_mode=args.range)
+        if args.leaf_mode:
+            c.set_tuning(leaf_mode=args.leaf_mode)
+        c.reserve(n)
+    ctx = ctxs[0]
+    # the sorts' own streams (created non-blocking by torch): on the legacy
     # default stream every launch would also order against other streams
-    stream = torch.cuda.Stream(dev)
+    streams = [torch.cuda.Stream(dev) for _ in range(T)]
+    stream = streams[0]
 
-    def step(timing=False):
+    def sort_some(t, timing):
+        # thread t: arrays t, t + T, ... on context t and stream t; a sort
+        # call returns when its sort is complete on the device
+        torch.cuda.set_device(local)
         st = {k: 0.0 for k in pcfsort.STAGES}
         launches, moved = 0, 0
-        for t, o in zip(ins, outs):
-            ctx.sort_keys(t, o, key_type="f64", seed=0, stream=stream)
-            s = ctx.last_stats()
+        for i in range(t, 4, T):
+            ctxs[t].sort_keys(ins[i], outs[i], key_type="f64", seed=0, stream=streams[t])
+            s = ctxs[t].last_stats()
             launches += s["kernel_launches"]
             moved += s["bytes_moved"]
             if timing:
-                for k, v in ctx.stage_ms().items():
+                for k, v in ctxs[t].stage_ms().items():
                     st[k] += v
         return st, launches, moved
 
+    pool = ThreadPoolExecutor(max_workers=T) if T > 1 else None
+
+    def step(timing=False, concurrent=True):
+        if not concurrent or pool is None:
+            # one thread, one stream: context 0 sorts all four arrays
+            st = {k: 0.0 for k in pcfsort.STAGES}
+            launches, moved = 0, 0
+            for i in range(4):
+                ctx.sort_keys(ins[i], outs[i], key_type="f64", seed=0, stream=stream)
+                s = ctx.last_stats()
+                launches += s["kernel_launches"]
+                moved += s["bytes_moved"]
+                if timing:
+                    for k, v in ctx.stage_ms().items():
+                        st[k] += v
+            return st, launches, moved
+        parts = list(pool.map(lambda t: sort_some(t, timing), range(T)))
+        st = {k: sum(p[0][k] for p in parts) for k in pcfsort.STAGES}
+        return st, sum(p[1] for p in parts), sum(p[2] for p in parts)
+
+    def timed_steps(k, concurrent):
+        # device time from an event on stream 0 (which the other streams wait
+        # on) to one recorded there after the other streams' last work
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s2 in streams[1:]:
+            s2.wait_event(e0)
+        launches, moved = 0, 0
+        for _ in range(k):
+            _, nl, mv = step(concurrent=concurrent)
+            launches += nl
+            moved += mv
+        for s2 in streams[1:]:
+            ev = torch.cuda.Event()
+            ev.record(s2)
+            stream.wait_event(ev)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), launches, moved
+
     for _ in range(args.warmup):
+        if T > 1:
+            step(concurrent=False)
         step()
-    # correctness guard on the timed configuration (full check is in tests)
+    # correctness guard on the timed configuration (full check is in tests):
+    # the outputs of the last warm-up step, taken in the timed form
     for o in outs:
         b = o.view(torch.int64)
         low63 = torch.tensor(2**63 - 1, dtype=torch.int64, device=dev)
@@ -283,28 +343,30 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches, moved = 0, 0
     with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            _, nl, mv = step()
-            launches += nl
-            moved += mv
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        ms_dev, launches, moved = timed_steps(args.steps, concurrent=True)
+    ms = max_over_ranks(ms_dev, dist, dev)
     if dist:
         dist.barrier()
     keys_per_step = 4 * n * world
     value = job_value(4 * n, world, args.steps, ms)
+    # the one-thread, one-stream form of the same steps (untimed by the
+    # contract, reported beside the value)
+    if T > 1:
+        if dist:
+            dist.barrier()
+        ms_seq = max_over_ranks(timed_steps(args.steps, concurrent=False)[0], dist, dev)
+        sequential = {"value": job_value(4 * n, world, args.steps, ms_seq), "unit": "Gkeys/s",
+                      "ms_per_step": ms_seq / args.steps,
+                      "how": "the same steps from one host thread on one stream"}
+    else:
+        sequential = None
     # stage breakdown (CUDA events on the sort's stream), untimed steps
     ctx.enable_timing(True)
     t_steps = 2
     stages = {k: 0.0 for k in pcfsort.STAGES}
     for _ in range(t_steps):
-        st, _, _ = step(timing=True)
+        st, _, _ = step(timing=True, concurrent=False)
         for k in stages:
             stages[k] += st[k]
     ctx.enable_timing(False)
@@ -381,6 +443,12 @@ def main():
         "stage_ms_per_array": {k: v / (t_steps * 4) for k, v in stages.items()},
         "clocks": clk.summary(),
     }
+    line["config"]["sort_threads"] = T
+    line["config"]["streams"] = ("%d host threads, one context and stream each, arrays "
+                                 "round-robin; stage times from one-stream steps" % T
+                                 if T > 1 else "one host thread, one stream")
+    if sequential:
+        line["sequential"] = sequential
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, total, secs = cpu_oracle_gkeys(host_keys, args.model, args.range)
         line["cpu_baseline"] = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
@@ -388,7 +456,10 @@ def main():
                                           % (CPU_SAMPLE_N, total, secs)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if pool is not None:
+        pool.shutdown()
+    for c in ctxs:
+        c.close()
     if dist:
         dist.destroy_process_group()
     return 0
