@@ -466,7 +466,7 @@ def main():
 
 
 # ---------------------------------------------------------------------------
-# secondary configurations (not the driver's default line)
+# secondary configurations (not the default line)
 # ---------------------------------------------------------------------------
 def secondary_roofline(torch, ctx, run, n_global, n_total, peak, peak_kind):
     """Stage times of one more run (CUDA events on the sort's stream) and the
